@@ -1,0 +1,175 @@
+/*
+ * tsim.h -- C ABI of the GB300 per-shot sampler for noisy Clifford+T circuits.
+ *
+ * The library implements the compile-once / sample-many pipeline of Tsim
+ * (Haenel, Luo, Zhao, "Tsim: Fast Universal Simulator for Quantum Error
+ * Correction", arXiv 2604.01059):
+ *
+ *   tsim_compile   Sec. "Simulation pipeline" and Appendices "Pauli noise
+ *                  channels", "Channel reduction", "Stabilizer decompositions",
+ *                  "Parameterized evaluation of Clifford ZX diagrams": the
+ *                  circuit becomes a doubled, parameterised diagram, Clifford
+ *                  rewriting separates detectors (Eq. detector_sampling,
+ *                  f = T e mod 2) from the observable part, and every marginal
+ *                  of Algorithm 1 becomes a sum of stabilizer terms
+ *                  P = sum_t c^t prod_k h(alpha_k^t, beta_k^t; a_k, b_k)
+ *                  (Eqs. parities, phase_pair, scalar_product).
+ *   tsim_sample    Sec. "Complexity", paragraph "Sampling", Eq. detector_sampling
+ *                  and Algorithm 1: per shot, sample error mechanisms, compute
+ *                  f, evaluate the marginals exactly and draw the outputs; on
+ *                  one GPU, in hand-written sm_103a kernels.
+ *
+ * Conventions for every entry point:
+ *   - Status codes only; no C++ exception crosses this boundary.  On failure
+ *     tsim_last_error() returns a thread-local message.
+ *   - Programs are opaque, owned by the library, freed with tsim_program_free.
+ *   - Device buffers are caller-owned (e.g. torch tensors); the library never
+ *     frees them.  Host buffers likewise.
+ *   - Records are row-major [shot][word] uint64, record bit b of a row is bit
+ *     (b & 63) of word (b >> 6); unused high bits are zero.
+ *   - Output is a pure function of (program, seed, global shot index): the
+ *     Philox4x32-10 counter of shot s is (s lo, s hi, stream, block) with key
+ *     (seed lo, seed hi); stream 0 drives noise channel c (word c%4 of block
+ *     c/4), stream 1 drives autoregressive output i (word i%4 of block i/4).
+ */
+#ifndef TSIM_H
+#define TSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TSIM_OK = 0,
+  TSIM_ERR_PARSE = 1,            /* malformed circuit or program text */
+  TSIM_ERR_UNSUPPORTED_GATE = 2, /* instruction outside the supported set */
+  TSIM_ERR_CHI_BUDGET = 3,       /* stabilizer terms exceed chi_budget */
+  TSIM_ERR_OVERFLOW_BOUND = 4,   /* exact accumulation would not fit the kernel's integers */
+  TSIM_ERR_CUDA = 5,             /* a CUDA call failed (message names it) */
+  TSIM_ERR_OOM = 6,              /* host or device allocation failed */
+  TSIM_ERR_ARG = 7,              /* invalid argument (NULL, size, mode mismatch) */
+  TSIM_ERR_ZERO_PROB = 8,        /* a sampled prefix had P_prev = 0 (compiler bug guard) */
+  TSIM_ERR_TIMEOUT = 9,          /* a bounded device wait gave up */
+  TSIM_ERR_INTERNAL = 10         /* internal invariant violated */
+} tsim_status;
+
+typedef struct tsim_program tsim_program;
+
+enum { TSIM_MODE_DETECTORS = 0, TSIM_MODE_MEASUREMENTS = 1 };
+enum { TSIM_DECOMP_HEURISTIC = 0, TSIM_DECOMP_LEARNED = 1, TSIM_DECOMP_SINGLE_T = 2 };
+
+typedef struct {
+  int mode;              /* TSIM_MODE_DETECTORS: records are detector + observable bits
+                            (Sec. "Sampling detectors and observables"); TSIM_MODE_MEASUREMENTS:
+                            records are the measurement outcomes (plus detectors /
+                            observables computed from them by Eq. xor). */
+  int decomp;            /* stabilizer decomposition policy (Appendix "Stabilizer
+                            decompositions"): HEURISTIC = pairs of non-Clifford
+                            vertices in ascending order (2 terms per pair, alpha = 0.5),
+                            SINGLE_T = one T-state cut at a time, LEARNED = order scored
+                            by the cut-order network, heuristic as fallback. */
+  uint64_t chi_budget;   /* maximum stabilizer terms per marginal; 0 = 1<<20 */
+  int channel_reduction; /* 1 = apply the four steps of Appendix "Channel reduction" */
+} tsim_compile_opts;
+
+typedef struct {
+  int mode;
+  int num_qubits;
+  int num_measurements;   /* N_m */
+  int num_detectors;      /* N_d */
+  int num_observables;    /* N_o */
+  int num_error_bits;     /* raw error bits e (Appendix "Pauli noise channels") */
+  int num_channels;       /* reduced noise channels sampled per shot */
+  int num_f;              /* f variables after GF(2) elimination (Eq. detector_sampling) */
+  int num_random;         /* outputs drawn by Algorithm 1 */
+  int num_outputs;        /* all outputs in autoregressive order */
+  int num_chains;         /* independent autoregressive chains (connected components) */
+  int num_tables;         /* marginal tables (chain normalisations included) */
+  int x_words;            /* 64-bit words of the per-shot vector X = (f, random outputs) */
+  uint64_t total_terms;   /* sum over tables of stabilizer terms chi_j */
+  uint64_t max_terms;     /* largest chi_j */
+  int max_factors;        /* largest number of factors m in one term */
+  int meas_words, det_words, obs_words; /* record row widths in uint64 words */
+} tsim_program_info_t;
+
+/* Compile a Stim-format circuit (text, len bytes; the Clifford+T subset: I X Y Z
+ * H S S_DAG SQRT_X SQRT_X_DAG T T_DAG CX CY CZ SWAP (and CX/CY/CZ with a rec[-k]
+ * control), R RX M MX MR MRX (optional flip probability), X_ERROR Y_ERROR
+ * Z_ERROR DEPOLARIZE1 DEPOLARIZE2 PAULI_CHANNEL_1 PAULI_CHANNEL_2, DETECTOR,
+ * OBSERVABLE_INCLUDE, REPEAT, TICK, QUBIT_COORDS, SHIFT_COORDS) into a program.
+ * opts may be NULL (detector mode, heuristic, default budget, reduction on).
+ * On success *out owns a new program. */
+tsim_status tsim_compile(const char* text, size_t len, const tsim_compile_opts* opts,
+                         tsim_program** out);
+
+/* Fill *out with the program's sizes (used to size the record buffers). */
+tsim_status tsim_program_info(const tsim_program* prog, tsim_program_info_t* out);
+
+/* Number of stabilizer terms of marginal table t (0 <= t < num_tables). */
+tsim_status tsim_program_table_terms(const tsim_program* prog, int t, uint64_t* terms);
+
+/* Sample shots [shot_offset, shot_offset + shots) on the current CUDA device,
+ * asynchronously on cuda_stream (a cudaStream_t; NULL = legacy default stream).
+ * Outputs are DEVICE pointers, caller-owned, each may be NULL when not wanted:
+ *   d_meas   [shots][meas_words]  measurement records (measurement mode only,
+ *                                 must be NULL in detector mode -> TSIM_ERR_ARG)
+ *   d_det    [shots][det_words]   detector bits
+ *   d_obs    [shots][obs_words]   observable bits
+ *   d_accept [shots]              1 iff every detector bit of the shot is 0
+ * The first call for a program uploads its tables (synchronously).  Errors
+ * detected on the device are reported by the next tsim_sync/tsim_sample. */
+tsim_status tsim_sample(const tsim_program* prog, uint64_t shots, uint64_t seed,
+                        uint64_t shot_offset, uint64_t* d_meas, uint64_t* d_det,
+                        uint64_t* d_obs, uint8_t* d_accept, void* cuda_stream);
+
+/* End-to-end variant with HOST buffers (same layout as tsim_sample): allocates
+ * device staging buffers, samples, copies records back, synchronises. */
+tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t seed,
+                             uint64_t shot_offset, uint64_t* h_meas, uint64_t* h_det,
+                             uint64_t* h_obs, uint8_t* h_accept, void* cuda_stream);
+
+/* Batched launch: n programs, each with its own shots / seed / offset and its
+ * own output pointers (arrays of n device pointers; entries may be NULL), in
+ * one persistent-kernel launch over (program, shot-block) work items. */
+tsim_status tsim_sample_batch(const tsim_program* const* progs, int n, const uint64_t* shots,
+                              const uint64_t* seeds, const uint64_t* shot_offsets,
+                              uint64_t* const* d_meas, uint64_t* const* d_det,
+                              uint64_t* const* d_obs, uint8_t* const* d_accept,
+                              void* cuda_stream);
+
+/* Wait for cuda_stream and report any device-side error status. */
+tsim_status tsim_sync(void* cuda_stream);
+
+/* Exact value of marginal table t at the per-shot vector X (x_words uint64,
+ * host memory): P = sum_t c^t prod_k h(...) returned as
+ * (c0 + c1 w + c2 w^2 + c3 w^3) * sqrt2^(*sqrt2_exp), w = e^{i pi/4}.
+ * Used to validate compiled marginals against exact probabilities
+ * (Appendix "Validation"). */
+tsim_status tsim_eval_table(const tsim_program* prog, int t, const uint64_t* x,
+                            int64_t out_zw[4], int32_t* sqrt2_exp);
+
+/* Map raw error bits e (num_error_bits bytes, 0/1) to X = (T e) in the
+ * program's X layout (x_words words), Eq. detector_sampling. */
+tsim_status tsim_raw_to_x(const tsim_program* prog, const uint8_t* e, uint64_t* x);
+
+/* Serialise / restore a program (text format documented in the program
+ * writer; both directions are exact). */
+tsim_status tsim_program_save(const tsim_program* prog, const char* path);
+tsim_status tsim_program_load(const char* path, tsim_program** out);
+
+void tsim_program_free(tsim_program* prog);
+
+/* Thread-local description of the last failure on this thread. */
+const char* tsim_last_error(void);
+
+/* Self-check of the compiler's rewrite rules against brute-force summation on
+ * random small parameterised graphs (no GPU).  Returns TSIM_OK when all pass. */
+tsim_status tsim_selftest_rules(uint64_t seed, int iterations);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSIM_H */

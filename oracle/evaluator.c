@@ -227,8 +227,8 @@ struct oracle_prog {
   int n_chains; int* chain_norm;
   int n_ch; channel* ch;
   int n_tab; table* tab;
-  int* detmap_n; int** detmap;
-  int* obsmap_n; int** obsmap;
+  int n_detmap; int* detmap_n; int** detmap;
+  int n_obsmap; int* obsmap_n; int** obsmap;
 };
 
 static int read_hex_words(FILE* f, int W, uint64_t* dst) {
@@ -321,6 +321,7 @@ struct oracle_prog* oracle_load(const char* path) {
   if (expect(f, "detmap")) goto bad;
   int nd;
   if (fscanf(f, "%d", &nd) != 1) goto bad;
+  p->n_detmap = nd;
   p->detmap_n = calloc((size_t)nd + 1, sizeof(int));
   p->detmap = calloc((size_t)nd + 1, sizeof(int*));
   for (int d = 0; d < nd; ++d) {
@@ -332,6 +333,7 @@ struct oracle_prog* oracle_load(const char* path) {
   if (expect(f, "obsmap")) goto bad;
   int no;
   if (fscanf(f, "%d", &no) != 1) goto bad;
+  p->n_obsmap = no;
   p->obsmap_n = calloc((size_t)no + 1, sizeof(int));
   p->obsmap = calloc((size_t)no + 1, sizeof(int*));
   for (int d = 0; d < no; ++d) {
@@ -367,8 +369,8 @@ void oracle_free(struct oracle_prog* p) {
     free(tb->t);
   }
   free(p->tab);
-  if (p->detmap) for (int d = 0; d < p->ndet; ++d) free(p->detmap[d]);
-  if (p->obsmap) for (int d = 0; d < p->nobs; ++d) free(p->obsmap[d]);
+  if (p->detmap) for (int d = 0; d < p->n_detmap; ++d) free(p->detmap[d]);
+  if (p->obsmap) for (int d = 0; d < p->n_obsmap; ++d) free(p->obsmap[d]);
   free(p->detmap); free(p->detmap_n); free(p->obsmap); free(p->obsmap_n);
   free(p);
 }

@@ -1,0 +1,233 @@
+"""GB300-native per-shot sampler for noisy Clifford+T circuits (Tsim's method).
+
+Thin ctypes binding of the C ABI declared in ``include/tsim.h``: argument
+marshalling only.  Every step of compilation runs in the native library and
+every step of sampling runs in its sm_103a kernels; there is no Python or CPU
+fallback -- if the native library is missing, importing the binding raises.
+PyTorch is used only for device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from .build import LIB, build as _build
+
+__all__ = [
+    "TsimError", "Program", "tsim_compile", "tsim_program_info", "tsim_program_table_terms",
+    "tsim_sample", "tsim_sample_host", "tsim_sample_batch", "tsim_sync", "tsim_eval_table",
+    "tsim_raw_to_x", "tsim_program_save", "tsim_program_load", "tsim_program_free",
+    "tsim_last_error", "tsim_selftest_rules", "load_library",
+    "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T",
+]
+
+MODE_DETECTORS, MODE_MEASUREMENTS = 0, 1
+DECOMP_HEURISTIC, DECOMP_LEARNED, DECOMP_SINGLE_T = 0, 1, 2
+
+STATUS = {0: "TSIM_OK", 1: "TSIM_ERR_PARSE", 2: "TSIM_ERR_UNSUPPORTED_GATE", 3: "TSIM_ERR_CHI_BUDGET",
+          4: "TSIM_ERR_OVERFLOW_BOUND", 5: "TSIM_ERR_CUDA", 6: "TSIM_ERR_OOM", 7: "TSIM_ERR_ARG",
+          8: "TSIM_ERR_ZERO_PROB", 9: "TSIM_ERR_TIMEOUT", 10: "TSIM_ERR_INTERNAL"}
+
+
+class TsimError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class CompileOpts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("decomp", ctypes.c_int), ("chi_budget", ctypes.c_uint64),
+                ("channel_reduction", ctypes.c_int)]
+
+
+class ProgramInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in (
+        "mode", "num_qubits", "num_measurements", "num_detectors", "num_observables",
+        "num_error_bits", "num_channels", "num_f", "num_random", "num_outputs", "num_chains",
+        "num_tables", "x_words")] + [
+        ("total_terms", ctypes.c_uint64), ("max_terms", ctypes.c_uint64), ("max_factors", ctypes.c_int),
+        ("meas_words", ctypes.c_int), ("det_words", ctypes.c_int), ("obs_words", ctypes.c_int)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load the native library (building it in-tree if it is absent or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build() if not os.environ.get("TSIM_NO_BUILD") else LIB
+    if not os.path.exists(path):
+        raise ImportError(f"native library {path} is missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, u64, i32, i64 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_int64
+    pp = ctypes.POINTER(vp)
+    L.tsim_compile.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(CompileOpts), pp]
+    L.tsim_program_info.argtypes = [vp, ctypes.POINTER(ProgramInfo)]
+    L.tsim_program_table_terms.argtypes = [vp, i32, ctypes.POINTER(u64)]
+    L.tsim_sample.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp, vp]
+    L.tsim_sample_host.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp, vp]
+    L.tsim_sample_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                    ctypes.POINTER(u64), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.tsim_sync.argtypes = [vp]
+    L.tsim_eval_table.argtypes = [vp, i32, ctypes.POINTER(u64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)]
+    L.tsim_raw_to_x.argtypes = [vp, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(u64)]
+    L.tsim_program_save.argtypes = [vp, ctypes.c_char_p]
+    L.tsim_program_load.argtypes = [ctypes.c_char_p, pp]
+    L.tsim_program_free.argtypes = [vp]
+    L.tsim_program_free.restype = None
+    L.tsim_last_error.restype = ctypes.c_char_p
+    L.tsim_selftest_rules.argtypes = [u64, i32]
+    for n in ("tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_sample",
+              "tsim_sample_host", "tsim_sample_batch", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
+              "tsim_program_save", "tsim_program_load", "tsim_selftest_rules"):
+        getattr(L, n).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise TsimError(rc, load_library().tsim_last_error().decode(errors="replace"))
+
+
+def tsim_last_error() -> str:
+    return load_library().tsim_last_error().decode(errors="replace")
+
+
+def tsim_compile(text: str, mode=MODE_DETECTORS, decomp=DECOMP_HEURISTIC, chi_budget=0, channel_reduction=True):
+    """Compile a Stim-format circuit; returns an opaque program handle (int)."""
+    L = load_library()
+    b = text.encode()
+    opts = CompileOpts(mode, decomp, chi_budget, 1 if channel_reduction else 0)
+    h = ctypes.c_void_p()
+    _check(L.tsim_compile(b, len(b), ctypes.byref(opts), ctypes.byref(h)))
+    return h.value
+
+
+def tsim_program_info(h) -> dict:
+    info = ProgramInfo()
+    _check(load_library().tsim_program_info(h, ctypes.byref(info)))
+    return info.as_dict()
+
+
+def tsim_program_table_terms(h, t) -> int:
+    n = ctypes.c_uint64()
+    _check(load_library().tsim_program_table_terms(h, t, ctypes.byref(n)))
+    return n.value
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def tsim_sample(h, shots, seed, shot_offset=0, meas=None, det=None, obs=None, accept=None, stream=None):
+    """Launch sampling into caller-owned device tensors (asynchronous on `stream`)."""
+    s = stream if isinstance(stream, (int, type(None))) else stream.cuda_stream
+    _check(load_library().tsim_sample(h, shots, seed, shot_offset, _ptr(meas), _ptr(det), _ptr(obs),
+                                      _ptr(accept), s))
+
+
+def tsim_sample_host(h, shots, seed, shot_offset=0, meas=None, det=None, obs=None, accept=None, stream=None):
+    """Sample into host numpy arrays (copies inside, synchronous)."""
+    s = stream if isinstance(stream, (int, type(None))) else stream.cuda_stream
+    p = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+    _check(load_library().tsim_sample_host(h, shots, seed, shot_offset, p(meas), p(det), p(obs), p(accept), s))
+
+
+def tsim_sample_batch(hs, shots, seeds, shot_offsets=None, meas=None, det=None, obs=None, accept=None,
+                      stream=None):
+    n = len(hs)
+    vp, u64 = ctypes.c_void_p, ctypes.c_uint64
+    arr = lambda xs, T: (T * n)(*xs)  # noqa: E731
+    ptrs = lambda ts: None if ts is None else arr([_ptr(t) for t in ts], vp)  # noqa: E731
+    s = stream if isinstance(stream, (int, type(None))) else stream.cuda_stream
+    _check(load_library().tsim_sample_batch(arr(hs, vp), n, arr(shots, u64), arr(seeds, u64),
+                                            arr(shot_offsets or [0] * n, u64), ptrs(meas), ptrs(det),
+                                            ptrs(obs), ptrs(accept), s))
+
+
+def tsim_sync(stream=None):
+    s = stream if isinstance(stream, (int, type(None))) else stream.cuda_stream
+    _check(load_library().tsim_sync(s))
+
+
+def tsim_eval_table(h, t, xwords):
+    """Exact table value: ((c0, c1, c2, c3), k) meaning (sum c_i w^i) * sqrt2^k."""
+    n = len(xwords)
+    x = (ctypes.c_uint64 * n)(*[int(v) & 0xFFFFFFFFFFFFFFFF for v in xwords])
+    out = (ctypes.c_int64 * 4)()
+    k = ctypes.c_int32()
+    _check(load_library().tsim_eval_table(h, t, x, out, ctypes.byref(k)))
+    return tuple(out), k.value
+
+
+def tsim_raw_to_x(h, e_bits, x_words):
+    e = (ctypes.c_uint8 * max(1, len(e_bits)))(*e_bits)
+    x = (ctypes.c_uint64 * x_words)()
+    _check(load_library().tsim_raw_to_x(h, e, x))
+    return list(x)
+
+
+def tsim_program_save(h, path):
+    _check(load_library().tsim_program_save(h, os.fsencode(path)))
+
+
+def tsim_program_load(path):
+    h = ctypes.c_void_p()
+    _check(load_library().tsim_program_load(os.fsencode(path), ctypes.byref(h)))
+    return h.value
+
+
+def tsim_program_free(h):
+    load_library().tsim_program_free(h)
+
+
+def tsim_selftest_rules(seed=0, iterations=200):
+    _check(load_library().tsim_selftest_rules(seed, iterations))
+
+
+class Program:
+    """Owning wrapper around a compiled program handle."""
+
+    def __init__(self, text=None, *, handle=None, **opts):
+        self.h = handle if handle is not None else tsim_compile(text, **opts)
+        self.info = tsim_program_info(self.h)
+
+    @classmethod
+    def load(cls, path):
+        return cls(handle=tsim_program_load(path))
+
+    def save(self, path):
+        tsim_program_save(self.h, path)
+
+    def table_terms(self):
+        return [tsim_program_table_terms(self.h, t) for t in range(self.info["num_tables"])]
+
+    def sample_torch(self, shots, seed, shot_offset=0, stream=None, device="cuda"):
+        """Allocate torch output tensors on `device` and launch sampling."""
+        import torch
+        i = self.info
+        meas = torch.empty((shots, i["meas_words"]), dtype=torch.int64, device=device) \
+            if i["mode"] == MODE_MEASUREMENTS and i["meas_words"] else None
+        det = torch.empty((shots, max(i["det_words"], 1)), dtype=torch.int64, device=device)
+        obs = torch.empty((shots, max(i["obs_words"], 1)), dtype=torch.int64, device=device)
+        acc = torch.empty((shots,), dtype=torch.uint8, device=device)
+        tsim_sample(self.h, shots, seed, shot_offset, meas, det if i["det_words"] else None,
+                    obs if i["obs_words"] else None, acc, stream)
+        return {"meas": meas, "det": det[:, :i["det_words"]], "obs": obs[:, :i["obs_words"]], "accept": acc}
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            try:
+                tsim_program_free(h)
+            except Exception:
+                pass
+            self.h = None

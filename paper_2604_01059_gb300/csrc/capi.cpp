@@ -1,0 +1,298 @@
+// extern "C" boundary: argument checks, exception -> status conversion.
+#include <cstring>
+#include <random>
+#include <string>
+
+#include "circuit.h"
+#include "device.h"
+#include "program.h"
+#include "zx.h"
+
+#include <cuda_runtime.h>
+
+struct tsim_program {
+  tsim::Program* p;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class F>
+tsim_status guard(F&& f) {
+  try {
+    f();
+    return TSIM_OK;
+  } catch (const tsim::Error& e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return TSIM_ERR_OOM;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return TSIM_ERR_INTERNAL;
+  }
+}
+
+const tsim::Program& prog_of(const tsim_program* p) {
+  if (!p || !p->p) tsim::fail(TSIM_ERR_ARG, "NULL program");
+  return *p->p;
+}
+
+}  // namespace
+
+tsim::Program::~Program() { tsim::device_release(dev); }
+
+extern "C" {
+
+const char* tsim_last_error(void) { return g_last_error.c_str(); }
+
+tsim_status tsim_compile(const char* text, size_t len, const tsim_compile_opts* opts, tsim_program** out) {
+  return guard([&] {
+    if (!text || !out) tsim::fail(TSIM_ERR_ARG, "NULL argument");
+    tsim_compile_opts o{};
+    o.mode = TSIM_MODE_DETECTORS;
+    o.decomp = TSIM_DECOMP_HEURISTIC;
+    o.chi_budget = 0;
+    o.channel_reduction = 1;
+    if (opts) o = *opts;
+    if (o.mode != TSIM_MODE_DETECTORS && o.mode != TSIM_MODE_MEASUREMENTS) tsim::fail(TSIM_ERR_ARG, "bad mode");
+    if (o.decomp < 0 || o.decomp > 2) tsim::fail(TSIM_ERR_ARG, "bad decomposition policy");
+    tsim::Program* p = tsim::compile_program(std::string(text, len), o);
+    *out = new tsim_program{p};
+  });
+}
+
+tsim_status tsim_program_info(const tsim_program* prog, tsim_program_info_t* out) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!out) tsim::fail(TSIM_ERR_ARG, "NULL info");
+    std::memset(out, 0, sizeof *out);
+    out->mode = p.mode;
+    out->num_qubits = p.nq;
+    out->num_measurements = p.nmeas;
+    out->num_detectors = p.ndet;
+    out->num_observables = p.nobs;
+    out->num_error_bits = p.E;
+    out->num_channels = (int)p.channels.size();
+    out->num_f = p.nf;
+    out->num_random = p.nr;
+    out->num_outputs = (int)p.outputs.size();
+    out->num_chains = (int)p.chain_norm.size();
+    out->num_tables = (int)p.tables.size();
+    out->x_words = p.W;
+    for (const auto& t : p.tables) {
+      out->total_terms += t.terms.size();
+      out->max_terms = std::max<uint64_t>(out->max_terms, t.terms.size());
+      for (const auto& tm : t.terms) out->max_factors = std::max(out->max_factors, (int)tm.f.size());
+    }
+    out->meas_words = (p.nmeas + 63) / 64;
+    out->det_words = (p.ndet + 63) / 64;
+    out->obs_words = (p.nobs + 63) / 64;
+  });
+}
+
+tsim_status tsim_program_table_terms(const tsim_program* prog, int t, uint64_t* terms) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!terms || t < 0 || t >= (int)p.tables.size()) tsim::fail(TSIM_ERR_ARG, "bad table index");
+    *terms = p.tables[(size_t)t].terms.size();
+  });
+}
+
+tsim_status tsim_sample(const tsim_program* prog, uint64_t shots, uint64_t seed, uint64_t shot_offset,
+                        uint64_t* d_meas, uint64_t* d_det, uint64_t* d_obs, uint8_t* d_accept,
+                        void* cuda_stream) {
+  return guard([&] {
+    tsim::SampleArgs a;
+    a.shots = shots;
+    a.seed = seed;
+    a.shot_offset = shot_offset;
+    a.meas = d_meas;
+    a.det = d_det;
+    a.obs = d_obs;
+    a.accept = d_accept;
+    tsim::device_sample(prog_of(prog), a, cuda_stream);
+  });
+}
+
+tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t seed, uint64_t shot_offset,
+                             uint64_t* h_meas, uint64_t* h_det, uint64_t* h_obs, uint8_t* h_accept,
+                             void* cuda_stream) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (p.mode == TSIM_MODE_DETECTORS && h_meas) tsim::fail(TSIM_ERR_ARG, "measurement records requested from a detector-mode program");
+    size_t mw = (size_t)(p.nmeas + 63) / 64, dw = (size_t)(p.ndet + 63) / 64, ow = (size_t)(p.nobs + 63) / 64;
+    size_t bm = h_meas ? shots * mw * 8 : 0, bd = h_det ? shots * dw * 8 : 0;
+    size_t bo = h_obs ? shots * ow * 8 : 0, ba = h_accept ? shots : 0;
+    unsigned char* d = nullptr;
+    size_t tot = bm + bd + bo + ba + 64;
+    cudaError_t e = cudaMalloc(&d, tot);
+    if (e != cudaSuccess) tsim::fail(TSIM_ERR_OOM, std::string("cudaMalloc staging: ") + cudaGetErrorString(e));
+    struct Free { unsigned char* d; ~Free() { cudaFree(d); } } fr{d};
+    tsim::SampleArgs a;
+    a.shots = shots;
+    a.seed = seed;
+    a.shot_offset = shot_offset;
+    a.meas = h_meas ? (uint64_t*)d : nullptr;
+    a.det = h_det ? (uint64_t*)(d + bm) : nullptr;
+    a.obs = h_obs ? (uint64_t*)(d + bm + bd) : nullptr;
+    a.accept = h_accept ? (uint8_t*)(d + bm + bd + bo) : nullptr;
+    tsim::device_sample(p, a, cuda_stream);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    auto cp = [&](void* dst, const void* src, size_t n) {
+      if (!n) return;
+      cudaError_t ce = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
+      if (ce != cudaSuccess) tsim::fail(TSIM_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(ce));
+    };
+    cp(h_meas, a.meas, bm);
+    cp(h_det, a.det, bd);
+    cp(h_obs, a.obs, bo);
+    cp(h_accept, a.accept, ba);
+    tsim::device_sync(cuda_stream);
+  });
+}
+
+tsim_status tsim_sample_batch(const tsim_program* const* progs, int n, const uint64_t* shots,
+                              const uint64_t* seeds, const uint64_t* shot_offsets, uint64_t* const* d_meas,
+                              uint64_t* const* d_det, uint64_t* const* d_obs, uint8_t* const* d_accept,
+                              void* cuda_stream) {
+  return guard([&] {
+    if (n < 0 || (n > 0 && (!progs || !shots || !seeds))) tsim::fail(TSIM_ERR_ARG, "bad batch arguments");
+    std::vector<const tsim::Program*> ps((size_t)n);
+    std::vector<tsim::SampleArgs> as((size_t)n);
+    for (int i = 0; i < n; ++i) {
+      ps[(size_t)i] = &prog_of(progs[i]);
+      as[(size_t)i].shots = shots[i];
+      as[(size_t)i].seed = seeds[i];
+      as[(size_t)i].shot_offset = shot_offsets ? shot_offsets[i] : 0;
+      as[(size_t)i].meas = d_meas ? d_meas[i] : nullptr;
+      as[(size_t)i].det = d_det ? d_det[i] : nullptr;
+      as[(size_t)i].obs = d_obs ? d_obs[i] : nullptr;
+      as[(size_t)i].accept = d_accept ? d_accept[i] : nullptr;
+    }
+    tsim::device_sample_batch(ps.data(), n, as.data(), cuda_stream);
+  });
+}
+
+tsim_status tsim_sync(void* cuda_stream) {
+  return guard([&] { tsim::device_sync(cuda_stream); });
+}
+
+tsim_status tsim_eval_table(const tsim_program* prog, int t, const uint64_t* x, int64_t out_zw[4],
+                            int32_t* sqrt2_exp) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!x || !out_zw || !sqrt2_exp) tsim::fail(TSIM_ERR_ARG, "NULL argument");
+    tsim::ZW v = tsim::eval_table_host(p, t, x);
+    // reduce the exponent while every coefficient stays integral
+    for (int i = 0; i < 4; ++i) {
+      if (v.c[i] > INT64_MAX || v.c[i] < INT64_MIN) tsim::fail(TSIM_ERR_OVERFLOW_BOUND, "value exceeds int64");
+      out_zw[i] = (int64_t)v.c[i];
+    }
+    *sqrt2_exp = v.k;
+  });
+}
+
+tsim_status tsim_raw_to_x(const tsim_program* prog, const uint8_t* e, uint64_t* x) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!e || !x) tsim::fail(TSIM_ERR_ARG, "NULL argument");
+    std::memset(x, 0, (size_t)p.W * 8);
+    int bit = 0;
+    for (const auto& r : p.raw)
+      for (int b = 0; b < r.nbits; ++b, ++bit)
+        if (e[bit])
+          for (int w = 0; w < p.W; ++w) x[w] ^= r.cols[(size_t)b][(size_t)w];
+  });
+}
+
+tsim_status tsim_program_save(const tsim_program* prog, const char* path) {
+  return guard([&] {
+    if (!path) tsim::fail(TSIM_ERR_ARG, "NULL path");
+    tsim::save_program(prog_of(prog), path);
+  });
+}
+
+tsim_status tsim_program_load(const char* path, tsim_program** out) {
+  return guard([&] {
+    if (!path || !out) tsim::fail(TSIM_ERR_ARG, "NULL argument");
+    *out = new tsim_program{tsim::load_program(path)};
+  });
+}
+
+void tsim_program_free(tsim_program* prog) {
+  if (!prog) return;
+  delete prog->p;
+  delete prog;
+}
+
+tsim_status tsim_selftest_rules(uint64_t seed, int iterations) {
+  return guard([&] {
+    std::mt19937_64 rng(seed);
+    for (int it = 0; it < iterations; ++it) {
+      const size_t np = 1 + rng() % 4;
+      tsim::Graph g(np);
+      int nv = 1 + (int)(rng() % 7);
+      for (int v = 0; v < nv; ++v) {
+        int l = (int)(rng() % 8);
+        g.add_var(l);
+        for (size_t q = 0; q < np; ++q)
+          if (rng() % 3 == 0) g.P[(size_t)v].flip(q);
+      }
+      for (int a = 0; a < nv; ++a)
+        for (int b = a + 1; b < nv; ++b)
+          if (rng() % 2) g.toggle(a, b);
+      g.s2 = (int)(rng() % 5) - 2;
+      g.ph = (int)(rng() % 8);
+      std::vector<tsim::ZW> want(1u << np);
+      for (uint32_t pv = 0; pv < (1u << np); ++pv) {
+        tsim::Bits b(np);
+        for (size_t q = 0; q < np; ++q)
+          if ((pv >> q) & 1) b.set(q);
+        want[pv] = tsim::brute_value(g, b);
+      }
+      auto check = [&](const std::vector<tsim::Term>& terms, const char* what) {
+        for (uint32_t pv = 0; pv < (1u << np); ++pv) {
+          tsim::Bits b(np);
+          for (size_t q = 0; q < np; ++q)
+            if ((pv >> q) & 1) b.set(q);
+          tsim::ZW s;
+          for (const auto& t : terms) s = tsim::zw_add(s, tsim::term_value(t, b));
+          tsim::ZW d = want[pv];
+          for (auto& c : d.c) c = -c;
+          if (!tsim::zw_add(s, d).zero())
+            tsim::fail(TSIM_ERR_INTERNAL, std::string("rewrite self-test failed (") + what + ") at iteration " +
+                                              std::to_string(it));
+        }
+      };
+      for (int policy : {0, 2}) {
+        std::vector<tsim::Term> terms;
+        tsim::DecompStats st;
+        tsim::decompose(g, policy, terms, st);
+        check(terms, policy == 0 ? "pairs" : "single cuts");
+      }
+      // single steps on a copy: each must preserve the brute-force value
+      tsim::Graph h = g;
+      for (int v = 0; v < h.n; ++v) {
+        if (!h.alive[(size_t)v]) continue;
+        int l = h.lam[(size_t)v];
+        if (l == 2 || l == 6) h.lcomp(v);
+        else if ((l == 0 || l == 4) && h.degree(v) == 0) h.remove_isolated(v);
+        else continue;
+        for (uint32_t pv = 0; pv < (1u << np); ++pv) {
+          tsim::Bits b(np);
+          for (size_t q = 0; q < np; ++q)
+            if ((pv >> q) & 1) b.set(q);
+          tsim::ZW d = want[pv];
+          for (auto& c : d.c) c = -c;
+          if (!tsim::zw_add(tsim::brute_value(h, b), d).zero())
+            tsim::fail(TSIM_ERR_INTERNAL, "single rewrite step changed the value at iteration " + std::to_string(it));
+        }
+      }
+    }
+  });
+}
+
+}  // extern "C"

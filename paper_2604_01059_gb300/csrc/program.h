@@ -1,0 +1,72 @@
+// Compiled program: the contiguous tables the sampler evaluates per shot
+// (Sec. "Methods": the compiled sampler; Appendix "Parameterized evaluation of
+// Clifford ZX diagrams": the tensors c^t, alpha_k^t, beta_k^t, u_ki^t, v_ki^t).
+//
+// Per shot the sampler keeps a bit vector X of n_x bits laid out as
+//   [ f bits used by marginal tables (nft) | random outputs (nr) | other f bits ]
+// where f = T e mod 2 (Eq. detector_sampling) and "random outputs" are the
+// outputs drawn by Algorithm 1.  Every parity of the program is a mask over X.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "common.h"
+
+namespace tsim {
+
+struct ProgFactor {
+  int kind = 0, alpha = 0, beta = 0;    // FactorKind, angles in units of pi/4
+  std::vector<uint64_t> u, v;           // parities a = <u, X>, b = <v, X>
+};
+
+struct ProgTerm {
+  int s0 = 0, j0 = 0;                   // c^t = w^j0 * sqrt2^s0
+  std::vector<ProgFactor> f;
+};
+
+struct ProgTable {
+  std::vector<ProgTerm> terms;
+};
+
+struct ProgOutput {
+  bool random = false;
+  std::vector<uint64_t> mask;           // deterministic: bit = <mask, X> ^ cst
+  int cst = 0;
+  int xbit = -1, chain = -1, table = -1;  // random: X bit written, chain, marginal table
+};
+
+struct ProgChannel {
+  std::vector<uint32_t> thr;            // outcome o (< n-1) iff U < thr[o] (first such)
+  std::vector<std::vector<uint64_t>> sig;  // per outcome: X ^= sig
+  std::vector<double> probs;            // outcome probabilities (double, before quantisation)
+};
+
+struct RawInfo {
+  int nbits = 0;
+  std::vector<double> probs;                 // 2^nbits
+  std::vector<std::vector<uint64_t>> cols;   // per bit: its column of T in the X layout
+};
+
+struct DeviceProgram;  // opaque device-side cache
+
+struct Program {
+  int mode = 0;
+  int nq = 0, nmeas = 0, ndet = 0, nobs = 0, E = 0;
+  int nx = 0, W = 1, nf = 0, nr = 0, nft = 0;
+  std::vector<ProgOutput> outputs;
+  std::vector<int> chain_norm;           // normalisation table of each chain
+  std::vector<ProgChannel> channels;
+  std::vector<ProgTable> tables;
+  std::vector<std::vector<int>> detmap, obsmap;  // measurement mode only
+  std::vector<RawInfo> raw;
+  DeviceProgram* dev = nullptr;
+  ~Program();
+};
+
+Program* compile_program(const std::string& text, const tsim_compile_opts& opts);
+void save_program(const Program& p, const std::string& path);
+Program* load_program(const std::string& path);
+ZW eval_table_host(const Program& p, int t, const uint64_t* x);
+
+}  // namespace tsim

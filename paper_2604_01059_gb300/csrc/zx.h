@@ -1,0 +1,119 @@
+// Parameterised graph-like ZX diagram, stored as a sum over binary spider
+// variables (a "path sum"):
+//
+//   value(p) = sqrt2^s2 * w^ph * prod_k factor_k(p)
+//              * sum_{z in {0,1}^V} prod_v w^(lam_v z_v) (-1)^(z_v <P_v, p>)
+//                                   prod_{(u,v) in E} (-1)^(z_u z_v)
+//
+// Every vertex is a Z spider with phase lam_v * pi/4 + pi * (parity of the
+// parameters in P_v) (Appendix "ZX-Calculus": parameterised Pauli phases a*pi);
+// every edge is a Hadamard edge.  Parameters are the raw error bits e and the
+// output bits of the diagram.  The scalar factors are the parameter-dependent
+// phase terms of Table "Types of parameterized phase terms" (Appendix
+// "Parameterized evaluation of Clifford ZX diagrams").
+//
+// Clifford rewriting (local complementation, pivoting, fusion, removal of
+// isolated spiders) is implemented as exact elimination of one summation
+// variable at a time; stabilizer decomposition (Appendix "Stabilizer
+// decompositions") as splitting a sum into Clifford branches.
+#pragma once
+#include <vector>
+
+#include "common.h"
+
+namespace tsim {
+
+// Factor kinds, values with angles in units of pi/4 and w = e^{i pi/4}:
+enum FactorKind {
+  F_PHASE_PAIR = 0,  // 1 + w^(al+4a) + w^(be+4b) - w^(al+be+4a+4b)     Eq. phase_pair
+  F_NODE = 1,        // 1 + w^(al+4a)                                    "Node"
+  F_PHASE = 2,       // w^(al*a)  (al = +-2: "Half-pi"; al = 4: a sign)
+  F_PI_PAIR = 3      // (-1)^(a b)                                       "pi-pair"
+};
+
+struct Factor {
+  int kind = 0;
+  int alpha = 0, beta = 0;
+  Bits a, b;  // parities over the diagram's parameters
+};
+
+// Affine GF(2) form: XOR of variables, parameters and a constant bit.
+struct Form {
+  std::vector<int> vars;  // sorted, unique
+  Bits params;
+  int c = 0;
+};
+
+Form form_const(size_t np, int c);
+Form form_var(size_t np, int v);
+Form form_param(size_t np, int p);
+Form form_params(const Bits& ps);
+void form_xor(Form& a, const Form& b);
+
+struct Term {
+  int s2 = 0, ph = 0;
+  std::vector<Factor> fac;
+};
+
+struct Graph {
+  size_t np = 0;
+  int n = 0, cap = 0;
+  std::vector<int> lam;
+  std::vector<Bits> P;
+  std::vector<std::vector<uint64_t>> adj;
+  std::vector<char> alive;
+  int s2 = 0, ph = 0;
+  bool zero = false;
+  std::vector<Factor> fac;
+
+  explicit Graph(size_t nparams = 0) : np(nparams) {}
+
+  int add_var(int l = 0);
+  void kill(int v);
+  bool edge(int u, int v) const { return (adj[(size_t)u][(size_t)v >> 6] >> (v & 63)) & 1; }
+  void toggle(int u, int v);
+  std::vector<int> nbrs(int v) const;
+  int degree(int v) const;
+  int num_alive() const;
+
+  // multiply the diagram by w^(theta * L)
+  void add_phase(int theta, Form L);
+  // multiply by (-1)^(F * G)
+  void add_sign(const Form& F, const Form& G);
+  void add_factor(int kind, int alpha, int beta, const Bits& a, const Bits& b);
+  // multiply by delta(L = 0), as (1/2) sum_w (-1)^(w L)
+  void hub(const Form& L);
+  bool can_substitute(int y, const Form& L) const;
+  // replace variable y by the affine form L (valid only if can_substitute)
+  void substitute(int y, const Form& L);
+
+  // rewrite steps
+  void remove_isolated(int v);
+  void lcomp(int v);
+  void eliminate(int v, int u);
+  void simplify();
+  void compact();
+  void fold_phase_factors();
+  Term as_term() const;
+};
+
+// value of one factor for parity values a, b
+ZW factor_value(const Factor& f, int a, int b);
+
+struct DecompStats {
+  uint64_t terms = 0;
+  uint64_t budget = 0;
+  uint64_t leaves = 0;
+};
+
+// Decompose into Clifford terms (Appendix "Stabilizer decompositions").
+// policy: 0 = pairs in ascending id (2 terms per pair), 2 = single cuts,
+// 1 = learned order given by `order` (vertex ranks, lower cut first).
+void decompose(Graph g, int policy, std::vector<Term>& out, DecompStats& st,
+               const std::vector<double>* scores = nullptr);
+
+// Brute-force value of a small graph for one parameter assignment (tests).
+ZW brute_value(const Graph& g, const Bits& pv);
+ZW term_value(const Term& t, const Bits& pv);
+
+}  // namespace tsim
