@@ -111,6 +111,9 @@ tsim_status tsim_program_info(const tsim_program* prog, tsim_program_info_t* out
 /* Number of stabilizer terms of marginal table t (0 <= t < num_tables). */
 tsim_status tsim_program_table_terms(const tsim_program* prog, int t, uint64_t* terms);
 
+/* Terms and total factors (sum over terms of m_t) of marginal table t. */
+tsim_status tsim_program_table_stats(const tsim_program* prog, int t, uint64_t* terms, uint64_t* factors);
+
 /* Sample shots [shot_offset, shot_offset + shots) on the current CUDA device,
  * asynchronously on cuda_stream (a cudaStream_t; NULL = legacy default stream).
  * Outputs are DEVICE pointers, caller-owned, each may be NULL when not wanted:

@@ -14,7 +14,7 @@ import os
 from .build import LIB, build as _build
 
 __all__ = [
-    "TsimError", "Program", "tsim_compile", "tsim_program_info", "tsim_program_table_terms",
+    "TsimError", "Program", "tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_program_table_stats",
     "tsim_sample", "tsim_sample_host", "tsim_sample_batch", "tsim_sync", "tsim_eval_table",
     "tsim_raw_to_x", "tsim_program_save", "tsim_program_load", "tsim_program_free",
     "tsim_last_error", "tsim_selftest_rules", "load_library",
@@ -70,6 +70,7 @@ def load_library(path: str | None = None):
     L.tsim_compile.argtypes = [ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(CompileOpts), pp]
     L.tsim_program_info.argtypes = [vp, ctypes.POINTER(ProgramInfo)]
     L.tsim_program_table_terms.argtypes = [vp, i32, ctypes.POINTER(u64)]
+    L.tsim_program_table_stats.argtypes = [vp, i32, ctypes.POINTER(u64), ctypes.POINTER(u64)]
     L.tsim_sample.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp, vp]
     L.tsim_sample_host.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp, vp]
     L.tsim_sample_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(u64), ctypes.POINTER(u64),
@@ -84,7 +85,7 @@ def load_library(path: str | None = None):
     L.tsim_program_free.restype = None
     L.tsim_last_error.restype = ctypes.c_char_p
     L.tsim_selftest_rules.argtypes = [u64, i32]
-    for n in ("tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_sample",
+    for n in ("tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_program_table_stats", "tsim_sample",
               "tsim_sample_host", "tsim_sample_batch", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
               "tsim_program_save", "tsim_program_load", "tsim_selftest_rules"):
         getattr(L, n).restype = ctypes.c_int
@@ -121,6 +122,13 @@ def tsim_program_table_terms(h, t) -> int:
     n = ctypes.c_uint64()
     _check(load_library().tsim_program_table_terms(h, t, ctypes.byref(n)))
     return n.value
+
+
+def tsim_program_table_stats(h, t):
+    """(terms, total factors) of marginal table t."""
+    n, f = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load_library().tsim_program_table_stats(h, t, ctypes.byref(n), ctypes.byref(f)))
+    return n.value, f.value
 
 
 def _ptr(t):
@@ -206,6 +214,9 @@ class Program:
 
     def save(self, path):
         tsim_program_save(self.h, path)
+
+    def table_stats(self, t):
+        return tsim_program_table_stats(self.h, t)
 
     def table_terms(self):
         return [tsim_program_table_terms(self.h, t) for t in range(self.info["num_tables"])]

@@ -101,6 +101,16 @@ tsim_status tsim_program_table_terms(const tsim_program* prog, int t, uint64_t* 
   });
 }
 
+tsim_status tsim_program_table_stats(const tsim_program* prog, int t, uint64_t* terms, uint64_t* factors) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!terms || !factors || t < 0 || t >= (int)p.tables.size()) tsim::fail(TSIM_ERR_ARG, "bad table index");
+    *terms = p.tables[(size_t)t].terms.size();
+    *factors = 0;
+    for (const auto& tm : p.tables[(size_t)t].terms) *factors += tm.f.size();
+  });
+}
+
 tsim_status tsim_sample(const tsim_program* prog, uint64_t shots, uint64_t seed, uint64_t shot_offset,
                         uint64_t* d_meas, uint64_t* d_det, uint64_t* d_obs, uint8_t* d_accept,
                         void* cuda_stream) {

@@ -1,0 +1,174 @@
+"""Seeded synthetic workload generators (Stim-format circuit text).
+
+These stand in for the paper's benchmark circuits (distillation, cultivation
+and random exponentiated-Pauli circuits), which are not reproduced here.
+Each generator is written from the textbook description of the code it
+builds; the module holds no part of the sampling method (no noise sampling,
+no GF(2) or Z[w] arithmetic) and is shared by the tests, the benchmark and
+the oracle comparisons.
+"""
+from __future__ import annotations
+
+import math
+import random
+
+
+# --------------------------------------------------------------------------
+# rotated surface code
+# --------------------------------------------------------------------------
+def rotated_surface_layout(d):
+    """Data qubits (i, j), 0 <= i, j < d, and stabilizer faces.
+
+    Face (a, b), 0 <= a, b <= d, touches data (a-1, b-1), (a-1, b), (a, b-1),
+    (a, b) where they exist; faces alternate X / Z in a checkerboard
+    ((a + b) even = X).  Weight-2 faces are kept on the top / bottom edges for
+    X type and on the left / right edges for Z type; weight-1 corners are
+    dropped.  Logical Z is Z on a row of data qubits, logical X is X on a
+    column.  Each face lists its data qubits in the order NW, NE, SW, SE
+    (None where absent).
+    """
+    data = {}
+    for i in range(d):
+        for j in range(d):
+            data[(i, j)] = len(data)
+    faces = []
+    for a in range(d + 1):
+        for b in range(d + 1):
+            kind = "X" if (a + b) % 2 == 0 else "Z"
+            corners = [(a - 1, b - 1), (a - 1, b), (a, b - 1), (a, b)]
+            qs = [data.get(c) for c in corners]
+            w = sum(q is not None for q in qs)
+            if w < 2:
+                continue
+            if w == 2:
+                top_bottom = a in (0, d)
+                if top_bottom and kind != "X":
+                    continue
+                if not top_bottom and kind != "Z":
+                    continue
+            faces.append({"kind": kind, "pos": (a, b), "q": qs})
+    return data, faces
+
+
+def _cx_layers(faces, anc):
+    """Four CX layers: Z faces visit NW, SW, NE, SE ('N' shape), X faces visit
+    NW, NE, SW, SE ('Z' shape), so hook errors run along the logicals."""
+    order = {"Z": [0, 2, 1, 3], "X": [0, 1, 2, 3]}
+    layers = []
+    for step in range(4):
+        pairs = []
+        for f, a in zip(faces, anc):
+            q = f["q"][order[f["kind"]][step]]
+            if q is None:
+                continue
+            pairs.append((a, q) if f["kind"] == "X" else (q, a))
+        layers.append(pairs)
+    return layers
+
+
+def surface_code_t_injection(d=3, rounds=3, p=1e-3, rotation=("T",), final_basis="X"):
+    """d x d rotated surface-code memory with a magic state injected at a corner.
+
+    Round 0 prepares a product state (Li-style injection): data qubits above
+    the anti-diagonal in |0>, below it in |+>, the rest of the anti-diagonal in
+    |0>, and the corner injection qubit (0, d-1) in R |+>, where R is the gate
+    sequence `rotation` (default: a single T, so the injected state is T|+>).
+    Row 0 (logical Z) then consists of |0> qubits plus the injection qubit and
+    column d-1 (logical X) of |+> qubits plus the injection qubit, so the
+    logical qubit inherits the injected state.  Each of `rounds` stabilizer
+    rounds uses the N-shaped CX order with DEPOLARIZE2(p) after every CX layer
+    and X_ERROR(p) before every ancilla measurement; detectors compare
+    consecutive rounds (first round: faces deterministic on the product state
+    only).  The final data measurement is in `final_basis` with Z_ERROR(p) or
+    X_ERROR(p) before it; its faces give the last detectors and the matching
+    logical operator is observable 0.  Returns Stim text.
+    """
+    data, faces = rotated_surface_layout(d)
+    nd = len(data)
+    anc = [nd + k for k in range(len(faces))]
+    L = []
+    inj = data[(0, d - 1)]
+    plus = [data[(i, j)] for (i, j) in data if i + j > d - 1]
+    zero = [data[(i, j)] for (i, j) in data if i + j <= d - 1 and data[(i, j)] != inj]
+    L.append("R " + " ".join(map(str, sorted(zero + anc))))
+    L.append("RX " + " ".join(map(str, sorted(plus + [inj]))))
+    for g in rotation:
+        L.append(f"{g} {inj}")
+    xa = [a for f, a in zip(faces, anc) if f["kind"] == "X"]
+    layers = _cx_layers(faces, anc)
+    state = {q: "0" for q in zero}
+    state.update({q: "+" for q in plus})
+    state[inj] = "T"
+
+    def deterministic_first(f):
+        want = "+" if f["kind"] == "X" else "0"
+        return all(q is None or state[q] == want for q in f["q"])
+
+    nf = len(faces)
+    for r in range(rounds):
+        if xa:
+            L.append("H " + " ".join(map(str, xa)))
+        for layer in layers:
+            flat = [x for pr in layer for x in pr]
+            L.append("CX " + " ".join(map(str, flat)))
+            L.append(f"DEPOLARIZE2({p}) " + " ".join(map(str, flat)))
+        if xa:
+            L.append("H " + " ".join(map(str, xa)))
+        L.append(f"X_ERROR({p}) " + " ".join(map(str, anc)))
+        L.append("MR " + " ".join(map(str, anc)))
+        for k, f in enumerate(faces):
+            cur = f"rec[-{nf - k}]"
+            if r == 0:
+                if deterministic_first(f):
+                    L.append(f"DETECTOR {cur}")
+            else:
+                L.append(f"DETECTOR {cur} rec[-{2 * nf - k}]")
+    flip = "X_ERROR" if final_basis == "Z" else "Z_ERROR"
+    L.append(f"{flip}({p}) " + " ".join(map(str, range(nd))))
+    L.append(("M " if final_basis == "Z" else "MX ") + " ".join(map(str, range(nd))))
+    for k, f in enumerate(faces):
+        if f["kind"] != final_basis:
+            continue
+        recs = [f"rec[-{nd - q}]" for q in f["q"] if q is not None]
+        recs.append(f"rec[-{nd + nf - k}]")
+        L.append("DETECTOR " + " ".join(recs))
+    if final_basis == "Z":
+        logical = [data[(0, j)] for j in range(d)]
+    else:
+        logical = [data[(i, d - 1)] for i in range(d)]
+    L.append("OBSERVABLE_INCLUDE(0) " + " ".join(f"rec[-{nd - q}]" for q in logical))
+    return "\n".join(L) + "\n"
+
+
+def t_rotation_sequence(n_t, seed=0):
+    """A seeded single-qubit Clifford+T word with n_t T/T_DAG gates, each
+    followed by H or SQRT_X so that consecutive T gates do not fuse."""
+    rng = random.Random(seed)
+    seq = []
+    for k in range(n_t):
+        seq.append(rng.choice(["T", "T_DAG"]))
+        seq.append(rng.choice(["H", "SQRT_X"]) if k + 1 < n_t else "H")
+    return tuple(seq)
+
+
+# --------------------------------------------------------------------------
+# named configurations
+# --------------------------------------------------------------------------
+def config1_circuit(p=1e-3):
+    """d=3 rotated surface code, 17 qubits, 3 rounds, one injected logical T."""
+    return surface_code_t_injection(d=3, rounds=3, p=p, rotation=("T",))
+
+
+def config2_circuit(p=1e-3, n_t=16, seed=0):
+    """d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG gates in the
+    rotation that prepares the injected state."""
+    return surface_code_t_injection(d=5, rounds=5, p=p, rotation=t_rotation_sequence(n_t, seed))
+
+
+def count_t(text):
+    n = 0
+    for line in text.splitlines():
+        parts = line.split()
+        if parts and parts[0] in ("T", "T_DAG"):
+            n += len(parts) - 1
+    return n
