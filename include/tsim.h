@@ -143,6 +143,29 @@ tsim_status tsim_sample_batch(const tsim_program* const* progs, int n, const uin
                               uint64_t* const* d_obs, uint8_t* const* d_accept,
                               void* cuda_stream);
 
+/* Same arguments, layout and records as tsim_sample, for callers that cannot
+ * allocate device memory (for example code running inside an allocator or
+ * memory pool it does not own, or a host that has carved up device memory in
+ * advance).  The paper has no counterpart: this is an interface of this
+ * library only.  The call allocates nothing, host or device: the program's
+ * device tables, which tsim_sample keeps in memory it allocates once per
+ * program, are packed into a fixed 4 MiB array in the library's device
+ * memory (every GPU that loads the library holds it until the process exits)
+ * and copied there on cuda_stream before the kernel runs.
+ *   - Programs whose packed tables exceed 4 MiB are rejected with
+ *     TSIM_ERR_ARG; tsim_sample has no such limit.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - Every call reuses the same array and rewrites all of it that the kernel
+ *     reads.  Calls whose work overlaps on the GPU (different streams without
+ *     ordering between them) race on the array and must not be issued; calls
+ *     on one stream are ordered and safe.  Host threads are serialised.
+ * Device-side errors are reported by tsim_sync, as for tsim_sample. */
+tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t shots, uint64_t seed,
+                                uint64_t shot_offset, uint64_t* d_meas, uint64_t* d_det,
+                                uint64_t* d_obs, uint8_t* d_accept, void* cuda_stream);
+
 /* Wait for cuda_stream and report any device-side error status. */
 tsim_status tsim_sync(void* cuda_stream);
 

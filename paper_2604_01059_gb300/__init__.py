@@ -15,7 +15,7 @@ from .build import LIB, build as _build
 
 __all__ = [
     "TsimError", "Program", "tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_program_table_stats",
-    "tsim_sample", "tsim_sample_host", "tsim_sample_batch", "tsim_sync", "tsim_eval_table",
+    "tsim_sample", "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_sync", "tsim_eval_table",
     "tsim_raw_to_x", "tsim_program_save", "tsim_program_load", "tsim_program_free",
     "tsim_last_error", "tsim_selftest_rules", "load_library",
     "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T",
@@ -73,6 +73,7 @@ def load_library(path: str | None = None):
     L.tsim_program_table_stats.argtypes = [vp, i32, ctypes.POINTER(u64), ctypes.POINTER(u64)]
     L.tsim_sample.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp, vp]
     L.tsim_sample_host.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp, vp]
+    L.tsim_sample_noalloc.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp, vp]
     L.tsim_sample_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                     ctypes.POINTER(u64), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                     ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -86,7 +87,7 @@ def load_library(path: str | None = None):
     L.tsim_last_error.restype = ctypes.c_char_p
     L.tsim_selftest_rules.argtypes = [u64, i32]
     for n in ("tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_program_table_stats", "tsim_sample",
-              "tsim_sample_host", "tsim_sample_batch", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
+              "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
               "tsim_program_save", "tsim_program_load", "tsim_selftest_rules"):
         getattr(L, n).restype = ctypes.c_int
     _lib = L
@@ -140,6 +141,13 @@ def tsim_sample(h, shots, seed, shot_offset=0, meas=None, det=None, obs=None, ac
     s = stream if isinstance(stream, (int, type(None))) else stream.cuda_stream
     _check(load_library().tsim_sample(h, shots, seed, shot_offset, _ptr(meas), _ptr(det), _ptr(obs),
                                       _ptr(accept), s))
+
+
+def tsim_sample_noalloc(h, shots, seed, shot_offset=0, meas=None, det=None, obs=None, accept=None, stream=None):
+    """tsim_sample for callers that cannot allocate device memory (fixed 4 MiB table scratch)."""
+    s = stream if isinstance(stream, (int, type(None))) else stream.cuda_stream
+    _check(load_library().tsim_sample_noalloc(h, shots, seed, shot_offset, _ptr(meas), _ptr(det), _ptr(obs),
+                                              _ptr(accept), s))
 
 
 def tsim_sample_host(h, shots, seed, shot_offset=0, meas=None, det=None, obs=None, accept=None, stream=None):

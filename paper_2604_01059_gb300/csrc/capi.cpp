@@ -1,4 +1,5 @@
 // extern "C" boundary: argument checks, exception -> status conversion.
+#include <cstdio>
 #include <cstring>
 #include <random>
 #include <string>
@@ -10,13 +11,9 @@
 
 #include <cuda_runtime.h>
 
-struct tsim_program {
-  tsim::Program* p;
-};
-
 namespace {
 
-thread_local std::string g_last_error;
+thread_local char g_last_error[1024];
 
 template <class F>
 tsim_status guard(F&& f) {
@@ -24,13 +21,13 @@ tsim_status guard(F&& f) {
     f();
     return TSIM_OK;
   } catch (const tsim::Error& e) {
-    g_last_error = e.what();
+    tsim::set_last_error(e.what());
     return e.code;
   } catch (const std::bad_alloc&) {
-    g_last_error = "host allocation failed";
+    tsim::set_last_error("host allocation failed");
     return TSIM_ERR_OOM;
   } catch (const std::exception& e) {
-    g_last_error = e.what();
+    tsim::set_last_error(e.what());
     return TSIM_ERR_INTERNAL;
   }
 }
@@ -44,9 +41,11 @@ const tsim::Program& prog_of(const tsim_program* p) {
 
 tsim::Program::~Program() { tsim::device_release(dev); }
 
+void tsim::set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
 extern "C" {
 
-const char* tsim_last_error(void) { return g_last_error.c_str(); }
+const char* tsim_last_error(void) { return g_last_error; }
 
 tsim_status tsim_compile(const char* text, size_t len, const tsim_compile_opts* opts, tsim_program** out) {
   return guard([&] {

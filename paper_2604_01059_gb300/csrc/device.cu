@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "device.h"
@@ -331,189 +332,293 @@ __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, u
 // ------------------------------------------------------------------ upload
 namespace {
 
-int padded_words(int W) {
+int padded_words_or_zero(int W) {
   for (int p : {1, 2, 4, 8, 16, 32})
     if (W <= p) return p;
-  fail(TSIM_ERR_ARG, "per-shot vector wider than 2048 bits is not supported");
+  return 0;
 }
 
-struct Blob {
-  std::vector<unsigned char> bytes;
-  size_t add(const void* p, size_t n) {
-    size_t off = (bytes.size() + 255) & ~(size_t)255;
-    bytes.resize(off + n);
-    if (n) std::memcpy(bytes.data() + off, p, n);
-    return off;
+// Byte sinks for the table packer: sections start on 256-byte boundaries and
+// alignment padding is zero.  VecSink grows a host vector; FixedSink writes
+// into a caller-provided buffer of fixed capacity and never allocates.
+struct VecSink {
+  std::vector<unsigned char> b;
+  size_t section() {
+    b.resize((b.size() + 255) & ~(size_t)255, 0);
+    return b.size();
   }
+  void put(const void* p, size_t n) {
+    size_t o = b.size();
+    b.resize(o + n);
+    if (n) std::memcpy(b.data() + o, p, n);
+  }
+  size_t size() const { return b.size(); }
 };
 
-DeviceProgram* upload(const Program& p) {
-  const int W = padded_words(p.W);
-  auto pad = [&](const std::vector<uint64_t>& m) {
-    std::vector<uint64_t> r((size_t)W, 0);
-    for (size_t i = 0; i < m.size() && i < (size_t)W; ++i) r[i] = m[i];
-    return r;
-  };
-  if ((int)p.chain_norm.size() > kMaxChains) fail(TSIM_ERR_ARG, "too many autoregressive chains for the kernel");
-  if ((int)p.outputs.size() > kMaxOutWords * 64) fail(TSIM_ERR_ARG, "too many outputs for the kernel");
+struct FixedSink {
+  unsigned char* base;
+  size_t cap;
+  size_t n = 0;
+  bool overflow = false;
+  size_t section() {
+    size_t off = (n + 255) & ~(size_t)255;
+    if (off > cap) overflow = true;
+    else std::memset(base + n, 0, off - n);
+    n = off;
+    return off;
+  }
+  void put(const void* p, size_t k) {
+    if (overflow || n + k > cap) { overflow = true; n += k; return; }
+    if (k) std::memcpy(base + n, p, k);
+    n += k;
+  }
+  size_t size() const { return n; }
+};
+
+struct Layout {
+  size_t o_ch = 0, o_thr = 0, o_sig = 0, o_out = 0, o_om = 0, o_cn = 0, o_tab = 0, o_term = 0,
+         o_fuv = 0, o_flut = 0, o_dmo = 0, o_dmi = 0, o_omo = 0, o_omi = 0, total = 0;
+  int W = 1;
+};
+
+// Four packed increments of one factor, inc = j | s << 11 | zero << 21
+// (J in bits 0-10, S in 11-20, vanishing factors in 21-31), with s relative
+// to the factor's smallest magnitude exponent smin.
+bool factor_lut(const ProgFactor& f, uint32_t inc[4], int* smin_out, int* spread) {
+  Factor fc;
+  fc.kind = f.kind;
+  fc.alpha = f.alpha;
+  fc.beta = f.beta;
+  int zs[4], ss[4], js[4], smin = 1 << 20, smax = -(1 << 20);
+  for (int idx = 0; idx < 4; ++idx) {
+    if (!monomial_of(factor_value(fc, idx & 1, idx >> 1), &zs[idx], &ss[idx], &js[idx])) return false;
+    if (!zs[idx]) { smin = std::min(smin, ss[idx]); smax = std::max(smax, ss[idx]); }
+  }
+  if (smin > smax) smin = smax = 0;
+  if (smax - smin > 3) return false;
+  for (int idx = 0; idx < 4; ++idx)
+    inc[idx] = zs[idx] ? (1u << 21) : ((uint32_t)js[idx] | ((uint32_t)(ss[idx] - smin) << 11));
+  *smin_out = smin;
+  *spread = smax - smin;
+  return true;
+}
+
+// raw sqrt2 exponent (s0 plus every factor's smin) and magnitude spread of a term
+bool term_exponents(const ProgTerm& tm, int* raw_s0, int* spread) {
+  uint32_t inc[4];
+  int s0 = tm.s0, sp = 0;
+  for (const ProgFactor& f : tm.f) {
+    int smin, spr;
+    if (!factor_lut(f, inc, &smin, &spr)) return false;
+    s0 += smin;
+    sp += spr;
+  }
+  *raw_s0 = s0;
+  *spread = sp;
+  return true;
+}
+
+// base exponent of a table = smallest raw term exponent; checks that the
+// 64-bit coefficient accumulation cannot overflow
+tsim_status table_base(const ProgTable& tb, int* base, const char** msg) {
+  int b = 0, dmax = 0;
+  bool first = true;
+  for (const ProgTerm& tm : tb.terms) {
+    int r, sp;
+    if (tm.f.size() > 255) { *msg = "term with more than 255 factors"; return TSIM_ERR_OVERFLOW_BOUND; }
+    if (!term_exponents(tm, &r, &sp)) { *msg = "factor value is not a monomial of bounded spread"; return TSIM_ERR_INTERNAL; }
+    if (first || r < b) b = r;
+    first = false;
+  }
+  for (const ProgTerm& tm : tb.terms) {
+    int r, sp;
+    term_exponents(tm, &r, &sp);
+    dmax = std::max(dmax, r - b + sp);
+  }
+  int lg = 0;
+  while ((1ull << lg) < (uint64_t)std::max<size_t>(1, tb.terms.size())) ++lg;
+  // |coefficient| <= terms * 2^(dmax/2 + 1) must stay below 2^62
+  if (dmax / 2 + 1 + lg >= 62) { *msg = "table magnitudes exceed 64-bit accumulation"; return TSIM_ERR_OVERFLOW_BOUND; }
+  *base = b;
+  return TSIM_OK;
+}
+
+template <class Sink>
+void put_padded(Sink& s, const std::vector<uint64_t>& m, int W) {
+  for (int i = 0; i < W; ++i) {
+    uint64_t x = (size_t)i < m.size() ? m[(size_t)i] : 0;
+    s.put(&x, 8);
+  }
+}
+
+// Packs the program into the device table layout.  Heap-free apart from
+// what the sink itself does.
+template <class Sink>
+tsim_status pack_tables(const Program& p, Sink& s, Layout& L, const char** msg) {
+  const int W = padded_words_or_zero(p.W);
+  if (!W) { *msg = "per-shot vector wider than 2048 bits is not supported"; return TSIM_ERR_ARG; }
+  if ((int)p.chain_norm.size() > kMaxChains) { *msg = "too many autoregressive chains for the kernel"; return TSIM_ERR_ARG; }
+  if ((int)p.outputs.size() > kMaxOutWords * 64) { *msg = "too many outputs for the kernel"; return TSIM_ERR_ARG; }
+  L.W = W;
   // channels
-  std::vector<DChan> ch;
-  std::vector<uint32_t> thr;
-  std::vector<uint64_t> sig;
-  for (const ProgChannel& c : p.channels) {
-    DChan d{};
-    d.n_out = (uint32_t)c.sig.size();
-    d.thr_off = (uint32_t)thr.size();
-    d.sig_off = (uint32_t)sig.size();
-    for (uint32_t t : c.thr) thr.push_back(t);
-    for (size_t o = 0; o < c.sig.size(); ++o) {
-      auto s = pad(c.sig[o]);
-      if (o == 0)
-        for (uint64_t x : s)
-          if (x) fail(TSIM_ERR_INTERNAL, "channel outcome 0 must not flip anything");
-      sig.insert(sig.end(), s.begin(), s.end());
+  L.o_ch = s.section();
+  {
+    uint32_t thr_off = 0, sig_off = 0;
+    for (const ProgChannel& c : p.channels) {
+      DChan d{};
+      d.n_out = (uint32_t)c.sig.size();
+      d.thr_off = thr_off;
+      d.sig_off = sig_off;
+      thr_off += (uint32_t)c.thr.size();
+      sig_off += (uint32_t)(c.sig.size() * (size_t)W);
+      s.put(&d, sizeof d);
+      for (size_t w = 0; !c.sig.empty() && w < c.sig[0].size(); ++w)
+        if (c.sig[0][w]) { *msg = "channel outcome 0 must not flip anything"; return TSIM_ERR_INTERNAL; }
     }
-    ch.push_back(d);
   }
-  thr.push_back(0);
+  L.o_thr = s.section();
+  for (const ProgChannel& c : p.channels)
+    for (uint32_t t : c.thr) s.put(&t, 4);
+  { uint32_t z = 0; s.put(&z, 4); }
+  L.o_sig = s.section();
+  for (const ProgChannel& c : p.channels)
+    for (const auto& sg : c.sig) put_padded(s, sg, W);
   // outputs
-  std::vector<DOut> out;
-  std::vector<uint64_t> omask;
-  for (const ProgOutput& o : p.outputs) {
-    DOut d{};
-    d.random = o.random ? 1 : 0;
-    d.cst = o.cst;
-    d.xbit = o.xbit;
-    d.chain = o.chain;
-    d.table = o.table;
-    d.mask_off = (uint32_t)omask.size();
-    auto m = pad(o.mask);
-    omask.insert(omask.end(), m.begin(), m.end());
-    out.push_back(d);
+  L.o_out = s.section();
+  {
+    uint32_t mo = 0;
+    for (const ProgOutput& o : p.outputs) {
+      DOut d{};
+      d.random = o.random ? 1 : 0;
+      d.cst = o.cst;
+      d.xbit = o.xbit;
+      d.chain = o.chain;
+      d.table = o.table;
+      d.mask_off = mo;
+      mo += (uint32_t)W;
+      s.put(&d, sizeof d);
+    }
   }
-  // tables: per factor a 4-entry table of packed increments
-  //   inc = j | s << 11 | zero << 21   (J in bits 0-10, S in 11-20, zeros in 21-31)
-  std::vector<DTable> tab;
-  std::vector<DTerm> term;
-  std::vector<uint64_t> fuv;
-  std::vector<uint32_t> flut;
-  for (const ProgTable& tb : p.tables) {
-    DTable dt{};
-    dt.term_off = (uint32_t)term.size();
-    dt.n_terms = (uint32_t)tb.terms.size();
-    std::vector<int> raw_s0;
-    std::vector<int> spread;
-    for (const ProgTerm& tm : tb.terms) {
-      if (tm.f.size() > 255) fail(TSIM_ERR_OVERFLOW_BOUND, "term with more than 255 factors");
-      DTerm d{};
-      d.fac_off = (uint32_t)(fuv.size() / (size_t)(2 * W));
-      d.n_fac = (uint32_t)tm.f.size();
-      d.j0 = tm.j0 & 7;
-      int s0 = tm.s0, sp = 0;
-      for (const ProgFactor& f : tm.f) {
-        Factor fc;
-        fc.kind = f.kind;
-        fc.alpha = f.alpha;
-        fc.beta = f.beta;
-        int zs[4], ss[4], js[4], smin = 1 << 20, smax = -(1 << 20);
-        for (int idx = 0; idx < 4; ++idx) {
-          if (!monomial_of(factor_value(fc, idx & 1, idx >> 1), &zs[idx], &ss[idx], &js[idx]))
-            fail(TSIM_ERR_INTERNAL, "factor value is not a monomial (non-Clifford factor)");
-          if (!zs[idx]) { smin = std::min(smin, ss[idx]); smax = std::max(smax, ss[idx]); }
-        }
-        if (smin > smax) smin = smax = 0;
-        if (smax - smin > 3) fail(TSIM_ERR_OVERFLOW_BOUND, "factor magnitude spread too large");
-        s0 += smin;
-        sp += smax - smin;
-        for (int idx = 0; idx < 4; ++idx) {
-          uint32_t inc = zs[idx] ? (1u << 21) : ((uint32_t)js[idx] | ((uint32_t)(ss[idx] - smin) << 11));
-          flut.push_back(inc);
-        }
-        auto u = pad(f.u), v = pad(f.v);
-        fuv.insert(fuv.end(), u.begin(), u.end());
-        fuv.insert(fuv.end(), v.begin(), v.end());
+  L.o_om = s.section();
+  for (const ProgOutput& o : p.outputs) put_padded(s, o.mask, W);
+  L.o_cn = s.section();
+  for (int c : p.chain_norm) { int32_t v = c; s.put(&v, 4); }
+  { int32_t z = 0; s.put(&z, 4); }
+  // tables
+  L.o_tab = s.section();
+  {
+    uint32_t term_off = 0;
+    for (const ProgTable& tb : p.tables) {
+      DTable dt{};
+      dt.term_off = term_off;
+      dt.n_terms = (uint32_t)tb.terms.size();
+      tsim_status st = table_base(tb, &dt.base, msg);
+      if (st != TSIM_OK) return st;
+      term_off += dt.n_terms;
+      s.put(&dt, sizeof dt);
+    }
+  }
+  L.o_term = s.section();
+  {
+    uint32_t fac_off = 0;
+    for (const ProgTable& tb : p.tables) {
+      int base = 0;
+      table_base(tb, &base, msg);
+      for (const ProgTerm& tm : tb.terms) {
+        DTerm d{};
+        int r, sp;
+        term_exponents(tm, &r, &sp);
+        d.fac_off = fac_off;
+        d.n_fac = (uint32_t)tm.f.size();
+        d.s0rel = r - base;
+        d.j0 = tm.j0 & 7;
+        fac_off += d.n_fac;
+        s.put(&d, sizeof d);
       }
-      raw_s0.push_back(s0);
-      spread.push_back(sp);
-      term.push_back(d);
     }
-    int base = 0;
-    if (!raw_s0.empty()) base = *std::min_element(raw_s0.begin(), raw_s0.end());
-    int dmax = 0;
-    for (size_t q = 0; q < raw_s0.size(); ++q) {
-      term[dt.term_off + q].s0rel = raw_s0[q] - base;
-      dmax = std::max(dmax, raw_s0[q] - base + spread[q]);
-    }
-    // |coefficient| <= terms * 2^(dmax/2 + 1) must stay below 2^62
-    int lg = 0;
-    while ((1ull << lg) < (uint64_t)std::max<size_t>(1, tb.terms.size())) ++lg;
-    if (dmax / 2 + 1 + lg >= 62) fail(TSIM_ERR_OVERFLOW_BOUND, "table magnitudes exceed 64-bit accumulation");
-    dt.base = base;
-    tab.push_back(dt);
   }
-  std::vector<int32_t> dmo{0}, dmi, omo{0}, omi;
-  for (const auto& d : p.detmap) { for (int j : d) dmi.push_back(j); dmo.push_back((int32_t)dmi.size()); }
-  for (const auto& d : p.obsmap) { for (int j : d) omi.push_back(j); omo.push_back((int32_t)omi.size()); }
-  std::vector<int32_t> cn(p.chain_norm.begin(), p.chain_norm.end());
-  dmi.push_back(0);
-  omi.push_back(0);
-  cn.push_back(0);
+  L.o_fuv = s.section();
+  for (const ProgTable& tb : p.tables)
+    for (const ProgTerm& tm : tb.terms)
+      for (const ProgFactor& f : tm.f) {
+        put_padded(s, f.u, W);
+        put_padded(s, f.v, W);
+      }
+  L.o_flut = s.section();
+  for (const ProgTable& tb : p.tables)
+    for (const ProgTerm& tm : tb.terms)
+      for (const ProgFactor& f : tm.f) {
+        uint32_t inc[4];
+        int smin, spr;
+        factor_lut(f, inc, &smin, &spr);
+        s.put(inc, sizeof inc);
+      }
+  // measurement-mode detector / observable maps (CSR)
+  auto csr = [&](const std::vector<std::vector<int>>& m, size_t* o_off, size_t* o_idx) {
+    *o_off = s.section();
+    int32_t acc = 0;
+    s.put(&acc, 4);
+    for (const auto& d : m) { acc += (int32_t)d.size(); s.put(&acc, 4); }
+    *o_idx = s.section();
+    for (const auto& d : m)
+      for (int j : d) { int32_t v = j; s.put(&v, 4); }
+    int32_t z = 0;
+    s.put(&z, 4);
+  };
+  csr(p.detmap, &L.o_dmo, &L.o_dmi);
+  csr(p.obsmap, &L.o_omo, &L.o_omi);
+  L.total = s.section();
+  return TSIM_OK;
+}
 
-  Blob b;
-  size_t o_ch = b.add(ch.data(), ch.size() * sizeof(DChan));
-  size_t o_thr = b.add(thr.data(), thr.size() * 4);
-  size_t o_sig = b.add(sig.data(), sig.size() * 8);
-  size_t o_out = b.add(out.data(), out.size() * sizeof(DOut));
-  size_t o_om = b.add(omask.data(), omask.size() * 8);
-  size_t o_cn = b.add(cn.data(), cn.size() * 4);
-  size_t o_tab = b.add(tab.data(), tab.size() * sizeof(DTable));
-  size_t o_term = b.add(term.data(), term.size() * sizeof(DTerm));
-  size_t o_fuv = b.add(fuv.data(), fuv.size() * 8);
-  size_t o_flut = b.add(flut.data(), flut.size() * 4);
-  size_t o_dmo = b.add(dmo.data(), dmo.size() * 4);
-  size_t o_dmi = b.add(dmi.data(), dmi.size() * 4);
-  size_t o_omo = b.add(omo.data(), omo.size() * 4);
-  size_t o_omi = b.add(omi.data(), omi.size() * 4);
-  b.add(nullptr, 0);
+DevView make_view(const unsigned char* base, const Layout& L, const Program& p) {
+  DevView v{};
+  v.W = L.W;
+  v.n_ch = (int)p.channels.size();
+  v.n_out = (int)p.outputs.size();
+  v.n_chains = (int)p.chain_norm.size();
+  v.n_tab = (int)p.tables.size();
+  v.nmeas = p.nmeas;
+  v.ndet = p.ndet;
+  v.nobs = p.nobs;
+  v.mode = p.mode;
+  v.ch = (const DChan*)(base + L.o_ch);
+  v.thr = (const uint32_t*)(base + L.o_thr);
+  v.sig = (const uint64_t*)(base + L.o_sig);
+  v.out = (const DOut*)(base + L.o_out);
+  v.omask = (const uint64_t*)(base + L.o_om);
+  v.chain_norm = (const int32_t*)(base + L.o_cn);
+  v.tab = (const DTable*)(base + L.o_tab);
+  v.term = (const DTerm*)(base + L.o_term);
+  v.fuv = (const uint64_t*)(base + L.o_fuv);
+  v.flut = (const uint32_t*)(base + L.o_flut);
+  v.dmap_off = (const int32_t*)(base + L.o_dmo);
+  v.dmap_idx = (const int32_t*)(base + L.o_dmi);
+  v.omap_off = (const int32_t*)(base + L.o_omo);
+  v.omap_idx = (const int32_t*)(base + L.o_omi);
+  return v;
+}
 
+DeviceProgram* upload(const Program& p) {
+  VecSink b;
+  Layout L;
+  const char* msg = "";
+  tsim_status st = pack_tables(p, b, L, &msg);
+  if (st != TSIM_OK) fail(st, msg);
   auto* d = new DeviceProgram();
   TSIM_CUDA(cudaGetDevice(&d->device));
-  cudaError_t e = cudaMalloc(&d->blob, std::max<size_t>(b.bytes.size(), 256));
+  cudaError_t e = cudaMalloc(&d->blob, std::max<size_t>(b.size(), 256));
   if (e != cudaSuccess) {
     delete d;
     fail(TSIM_ERR_OOM, std::string("cudaMalloc of program tables: ") + cudaGetErrorString(e));
   }
-  e = cudaMemcpy(d->blob, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(d->blob, b.b.data(), b.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(d->blob);
     delete d;
     fail(TSIM_ERR_CUDA, std::string("cudaMemcpy of program tables: ") + cudaGetErrorString(e));
   }
-  auto* base = (unsigned char*)d->blob;
-  DevView& v = d->v;
-  v.W = W;
-  v.n_ch = (int)ch.size();
-  v.n_out = (int)out.size();
-  v.n_chains = (int)p.chain_norm.size();
-  v.n_tab = (int)tab.size();
-  v.nmeas = p.nmeas;
-  v.ndet = p.ndet;
-  v.nobs = p.nobs;
-  v.mode = p.mode;
-  v.ch = (const DChan*)(base + o_ch);
-  v.thr = (const uint32_t*)(base + o_thr);
-  v.sig = (const uint64_t*)(base + o_sig);
-  v.out = (const DOut*)(base + o_out);
-  v.omask = (const uint64_t*)(base + o_om);
-  v.chain_norm = (const int32_t*)(base + o_cn);
-  v.tab = (const DTable*)(base + o_tab);
-  v.term = (const DTerm*)(base + o_term);
-  v.fuv = (const uint64_t*)(base + o_fuv);
-  v.flut = (const uint32_t*)(base + o_flut);
-  v.dmap_off = (const int32_t*)(base + o_dmo);
-  v.dmap_idx = (const int32_t*)(base + o_dmi);
-  v.omap_off = (const int32_t*)(base + o_omo);
-  v.omap_idx = (const int32_t*)(base + o_omi);
+  d->v = make_view((const unsigned char*)d->blob, L, p);
   return d;
 }
 
@@ -574,3 +679,85 @@ void device_sync(void* stream) {
 }
 
 }  // namespace tsim
+
+// ------------------------------------------------------------------------
+// Sampling without device allocation.
+//
+// Some callers cannot call cudaMalloc: code running inside a memory pool or
+// allocator they do not own, real-time loops that must not touch the driver's
+// allocator, or hosts whose device memory is carved up ahead of time.  For
+// them tsim_sample_noalloc runs the same sampling kernel, but the program's
+// device tables -- the scratch that tsim_sample allocates once per program --
+// live in the fixed array below instead.  Its size is kNoAllocBytes (4 MiB);
+// every GPU that loads the library holds it until the process exits.
+namespace tsim {
+namespace {
+
+constexpr size_t kNoAllocBytes = (size_t)4 << 20;
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// host staging of the packed tables (filled under the mutex, then copied)
+alignas(256) unsigned char g_noalloc_host[kNoAllocBytes];
+std::mutex g_noalloc_mutex;
+// device address of g_noalloc_scratch, per device, from cudaGetSymbolAddress
+void* g_noalloc_dev[kNoAllocMaxDevices];
+
+tsim_status noalloc_error(tsim_status st, const char* msg) {
+  set_last_error(msg);
+  return st;
+}
+
+}  // namespace
+}  // namespace tsim
+
+extern "C" tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t shots, uint64_t seed,
+                                           uint64_t shot_offset, uint64_t* d_meas, uint64_t* d_det,
+                                           uint64_t* d_obs, uint8_t* d_accept, void* cuda_stream) {
+  using namespace tsim;
+  if (!prog || !prog->p) return noalloc_error(TSIM_ERR_ARG, "NULL program");
+  const Program& p = *prog->p;
+  if (p.mode == TSIM_MODE_DETECTORS && d_meas)
+    return noalloc_error(TSIM_ERR_ARG, "measurement records requested from a detector-mode program");
+  if (shots == 0) return TSIM_OK;
+  const uint64_t blocks = (shots + kThreads - 1) / kThreads;
+  if (blocks > 0x7FFFFFFFull) return noalloc_error(TSIM_ERR_ARG, "too many shots for one launch");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
+    return noalloc_error(TSIM_ERR_CUDA, "cudaGetDevice failed or device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_dev[dev]) {
+    // once per device, with that device current: the host-side symbol is not
+    // a device address, so the kernel must be given the address looked up here
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
+      return noalloc_error(TSIM_ERR_CUDA, "cudaGetSymbolAddress of the no-alloc scratch array failed");
+    g_noalloc_dev[dev] = ptr;
+  }
+  FixedSink sink{g_noalloc_host, kNoAllocBytes};
+  Layout L;
+  const char* msg = "";
+  tsim_status st = pack_tables(p, sink, L, &msg);
+  if (st != TSIM_OK) return noalloc_error(st, msg);
+  if (sink.overflow)
+    return noalloc_error(TSIM_ERR_ARG, "program tables exceed the 4 MiB maximum of tsim_sample_noalloc");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // every byte the kernel reads is rewritten here, so nothing stale from the
+  // previous call survives
+  if (cudaMemcpyAsync(g_noalloc_dev[dev], g_noalloc_host, L.total, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return noalloc_error(TSIM_ERR_CUDA, "cudaMemcpyAsync into the no-alloc scratch array failed");
+  const DevView v = make_view((const unsigned char*)g_noalloc_dev[dev], L, p);
+  const unsigned nb = (unsigned)blocks;
+  switch (v.W) {
+    case 1: k_sample<1><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
+    case 2: k_sample<2><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
+    case 4: k_sample<4><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
+    case 8: k_sample<8><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
+    case 16: k_sample<16><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
+    case 32: k_sample<32><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
+    default: return noalloc_error(TSIM_ERR_INTERNAL, "unsupported word count");
+  }
+  if (cudaGetLastError() != cudaSuccess) return noalloc_error(TSIM_ERR_CUDA, "launch of the sampling kernel failed");
+  return TSIM_OK;
+}

@@ -69,4 +69,12 @@ void save_program(const Program& p, const std::string& path);
 Program* load_program(const std::string& path);
 ZW eval_table_host(const Program& p, int t, const uint64_t* x);
 
+// message for tsim_last_error(); copies into a fixed thread-local buffer
+void set_last_error(const char* msg);
+
 }  // namespace tsim
+
+// the opaque handle behind tsim_program*
+struct tsim_program {
+  tsim::Program* p;
+};
