@@ -30,7 +30,11 @@ P_VALUES = (5e-4, 1e-3, 2e-3)
 SHOTS_PER_P = 1_000_000
 SEED = 0
 METRIC = "shots/sec and Z[w] term-evals/sec, learned+batched vs plain GPU form, bit-exact"
-WORKLOAD = "d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG, p in {5e-4,1e-3,2e-3}, 1e6 shots per p"
+WORKLOADS = {
+    "cfg2": "d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG, p in {5e-4,1e-3,2e-3}, 1e6 shots per p",
+    "cfg3": "d=3 triangular colour-code T-check, 19 qubits, 42 T/T_DAG, 3 check rounds, p=1e-3, postselected, 1e5 shots",
+}
+WORKLOAD = WORKLOADS["cfg2"]
 
 
 def parse():
@@ -40,7 +44,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="bound on the oracle baseline's CPU work")
-    return ap.parse_args()
+    ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--shots", type=int, default=None, help="shots per program per step")
+    ap.add_argument("--profile", action="store_true", help="only run two launches per program (for ncu)")
+    args = ap.parse_args()
+    global WORKLOAD, SHOTS_PER_P
+    WORKLOAD = WORKLOADS[args.workload]
+    if args.workload == "cfg3":
+        SHOTS_PER_P = 100_000
+    if args.shots:
+        SHOTS_PER_P = args.shots
+    return args
 
 
 def dist_env():
@@ -50,9 +64,14 @@ def dist_env():
     return rank, world, local
 
 
+WORKLOAD_NAME = "cfg2"
+
+
 def programs():
     import paper_2604_01059_gb300 as T
     from paper_2604_01059_gb300 import workloads as Wk
+    if WORKLOAD_NAME == "cfg3":
+        return [T.Program(Wk.config3_circuit(p=1e-3))]
     return [T.Program(Wk.config2_circuit(p=p)) for p in P_VALUES]
 
 
@@ -139,11 +158,17 @@ def oracle_baseline(seconds, impl_line=False):
         paths.append(path)
     orcs = [evaluator.OracleProgram(pth) for pth in paths]
     # calibrate a sample size that takes about `seconds` on all cores
-    t0 = time.perf_counter()
-    for o in orcs:
-        o.sample(SEED, 0, 64)
-    per_shot = (time.perf_counter() - t0) / (64 * len(orcs))
-    chunk = max(64, int(seconds * cores / max(per_shot, 1e-9) / len(orcs) / cores))
+    n_cal = 4
+    while True:
+        t0 = time.perf_counter()
+        for o in orcs:
+            o.sample(SEED, 0, n_cal)
+        dt = time.perf_counter() - t0
+        if dt > 0.5 or n_cal >= 4096:
+            break
+        n_cal *= 4
+    per_shot = dt / (n_cal * len(orcs))
+    chunk = max(1, int(seconds / max(per_shot, 1e-9) / len(orcs)))
     jobs = [(k, r * chunk) for k in range(len(orcs)) for r in range(cores)]
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=cores) as ex:
@@ -151,8 +176,8 @@ def oracle_baseline(seconds, impl_line=False):
     dt = time.perf_counter() - t0
     shots = chunk * len(jobs)
     return {"value": shots / dt, "unit": "shots/s", "cores": cores, "kind": "oracle",
-            "sample": f"{shots} shots ({chunk} per thread x {cores} threads x 3 p values) of the same "
-                      f"workload, oracle C evaluator, exact arithmetic"}
+            "sample": f"{shots} shots ({chunk} per thread x {cores} threads x {len(orcs)} programs) of "
+                      f"the same workload, oracle C evaluator, exact arithmetic"}
 
 
 def run_reference(args):
@@ -270,7 +295,9 @@ def run_gpu(args):
     peak = int_peak_ops()
     roof = {"bound": "alu", "achieved": ops / (avg_launch_ms / 1e3) / 1e12, "peak": peak / 1e12,
             "unit": "Tops/s", "frac": ops / (avg_launch_ms / 1e3) / peak, "traffic": None,
-            "kernel": "k_sample", "peak_source": "derived: 152 SMs x 64 INT32 lanes x 2070 MHz"}
+            "kernel": "k_sample", "ops_per_shot": ops / SHOTS_PER_P,
+            "peak_source": "derived: 152 SMs x 64 INT32 lanes x 2070 MHz",
+            "measured_issue_tops": int_peaks_measured()}
     base = oracle_baseline(args.cpu_seconds) if (rank == 0 and world == 1) else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
@@ -290,24 +317,51 @@ def run_gpu(args):
 
 
 def kernel_int_ops(prog):
-    """Algorithmic integer operations per shot of the fused sampling kernel:
-    Philox4x32-10 = 10 rounds x 8 ops per 4 channels, 2 ops per channel for the
-    threshold test, and per stabilizer-term evaluation m (4W + 4) + 4 ops
-    (2W AND + 2W popcount + table lookup + accumulate per factor, plus the
-    term's magnitude and coefficient update)."""
+    """Integer operations one shot needs in the fused sampling kernel, counted
+    on the packed device tables it actually evaluates:
+      noise:   ceil(C/4) Philox4x32-10 calls x 10 rounds x (2 wide multiplies
+               + 2 three-input XORs) = 40 per call, plus one compare per channel;
+      outputs: 3 per single-bit deterministic output, 60 per Bernoulli decision;
+      tables:  per distinct parity 2W+2 (AND, XOR, popcount, insert), per merged
+               term 12 (+5 per factor: two bit extracts, index, lookup, add)."""
     i = prog.info
     C = i["num_channels"]
-    W = i["x_words"]
-    noise = ((C + 3) // 4) * 80 + 2 * C
-    terms = 0
+    W = next(p for p in (1, 2, 4, 8, 16, 32) if i["x_words"] <= p)
+    ops = 40 * ((C + 3) // 4) + C
+    ops += 3 * (i["num_outputs"] - i["num_random"]) + 60 * i["num_random"]
     for t in range(i["num_tables"]):
-        n_terms, n_factors = prog.table_stats(t)
-        terms += n_factors * (4 * W + 4) + 4 * n_terms
-    return noise + terms
+        classes, factors, parities = prog.device_table_stats(t)
+        ops += parities * (2 * W + 2) + 12 * classes + 5 * factors
+    return ops
+
+
+def int_peaks_measured():
+    import paper_2604_01059_gb300 as T
+    names = ["lop3", "imad", "imad_wide", "popc"]
+    return {n: T.tsim_measure_int_peak(k) / 1e12 for k, n in enumerate(names)}
+
+
+def run_profile():
+    """Two launches per program of the chosen workload, nothing else."""
+    import torch
+
+    import paper_2604_01059_gb300 as T
+    progs = programs()
+    for p in progs:
+        out = p.sample_torch(SHOTS_PER_P, SEED, 0)
+        out = p.sample_torch(SHOTS_PER_P, SEED, 0)
+    T.tsim_sync()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": WORKLOAD, "shots": SHOTS_PER_P, "programs": len(progs)}))
 
 
 def main():
+    global WORKLOAD_NAME
     args = parse()
+    WORKLOAD_NAME = args.workload
+    if args.profile:
+        run_profile()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

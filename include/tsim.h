@@ -93,6 +93,10 @@ typedef struct {
   uint64_t max_terms;     /* largest chi_j */
   int max_factors;        /* largest number of factors m in one term */
   int meas_words, det_words, obs_words; /* record row widths in uint64 words */
+  uint64_t device_classes;  /* terms left after merging terms with equal factor lists
+                               (exact: their c^t are summed in Z[w]) */
+  uint64_t device_parities; /* distinct factor parities over all tables */
+  int device_status;        /* TSIM_OK if the program can run on the GPU */
 } tsim_program_info_t;
 
 /* Compile a Stim-format circuit (text, len bytes; the Clifford+T subset: I X Y Z
@@ -190,6 +194,18 @@ void tsim_program_free(tsim_program* prog);
 
 /* Thread-local description of the last failure on this thread. */
 const char* tsim_last_error(void);
+
+/* Integer-issue microbenchmark of the current GPU (the paper has no
+ * counterpart; it states the ALU roofline of the sampling kernel): op 0 =
+ * 32-bit three-input logic, 1 = 32-bit multiply-add, 2 = 32x32->64 multiply
+ * (Philox's product), 3 = popcount.  *ops_per_s receives results per second
+ * of that instruction class over the whole GPU.  Allocates 4 bytes. */
+tsim_status tsim_measure_int_peak(int op, double* ops_per_s);
+
+/* Per-table statistics of the packed device tables of table t:
+ * out[0] = classes (terms after merging equal factor lists), out[1] = factors
+ * over those classes, out[2] = distinct factor parities. */
+tsim_status tsim_program_device_table_stats(const tsim_program* prog, int t, uint64_t out[3]);
 
 /* Self-check of the compiler's rewrite rules against brute-force summation on
  * random small parameterised graphs (no GPU).  Returns TSIM_OK when all pass. */

@@ -17,7 +17,8 @@ __all__ = [
     "TsimError", "Program", "tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_program_table_stats",
     "tsim_sample", "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_sync", "tsim_eval_table",
     "tsim_raw_to_x", "tsim_program_save", "tsim_program_load", "tsim_program_free",
-    "tsim_last_error", "tsim_selftest_rules", "load_library",
+    "tsim_last_error", "tsim_selftest_rules", "tsim_measure_int_peak", "tsim_program_device_table_stats",
+    "load_library",
     "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T",
 ]
 
@@ -46,7 +47,8 @@ class ProgramInfo(ctypes.Structure):
         "num_error_bits", "num_channels", "num_f", "num_random", "num_outputs", "num_chains",
         "num_tables", "x_words")] + [
         ("total_terms", ctypes.c_uint64), ("max_terms", ctypes.c_uint64), ("max_factors", ctypes.c_int),
-        ("meas_words", ctypes.c_int), ("det_words", ctypes.c_int), ("obs_words", ctypes.c_int)]
+        ("meas_words", ctypes.c_int), ("det_words", ctypes.c_int), ("obs_words", ctypes.c_int),
+        ("device_classes", ctypes.c_uint64), ("device_parities", ctypes.c_uint64), ("device_status", ctypes.c_int)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -86,9 +88,12 @@ def load_library(path: str | None = None):
     L.tsim_program_free.restype = None
     L.tsim_last_error.restype = ctypes.c_char_p
     L.tsim_selftest_rules.argtypes = [u64, i32]
+    L.tsim_measure_int_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+    L.tsim_program_device_table_stats.argtypes = [vp, i32, ctypes.POINTER(u64)]
     for n in ("tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_program_table_stats", "tsim_sample",
               "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
-              "tsim_program_save", "tsim_program_load", "tsim_selftest_rules"):
+              "tsim_program_save", "tsim_program_load", "tsim_selftest_rules", "tsim_measure_int_peak",
+              "tsim_program_device_table_stats"):
         getattr(L, n).restype = ctypes.c_int
     _lib = L
     return L
@@ -205,6 +210,20 @@ def tsim_program_free(h):
     load_library().tsim_program_free(h)
 
 
+def tsim_measure_int_peak(op):
+    """Measured integer results per second of one instruction class on this GPU."""
+    v = ctypes.c_double()
+    _check(load_library().tsim_measure_int_peak(op, ctypes.byref(v)))
+    return v.value
+
+
+def tsim_program_device_table_stats(h, t):
+    """(classes, class factors, distinct parities) of table t in the packed device tables."""
+    out = (ctypes.c_uint64 * 3)()
+    _check(load_library().tsim_program_device_table_stats(h, t, out))
+    return tuple(out)
+
+
 def tsim_selftest_rules(seed=0, iterations=200):
     _check(load_library().tsim_selftest_rules(seed, iterations))
 
@@ -225,6 +244,9 @@ class Program:
 
     def table_stats(self, t):
         return tsim_program_table_stats(self.h, t)
+
+    def device_table_stats(self, t):
+        return tsim_program_device_table_stats(self.h, t)
 
     def table_terms(self):
         return [tsim_program_table_terms(self.h, t) for t in range(self.info["num_tables"])]

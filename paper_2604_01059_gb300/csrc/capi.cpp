@@ -39,7 +39,10 @@ const tsim::Program& prog_of(const tsim_program* p) {
 
 }  // namespace
 
-tsim::Program::~Program() { tsim::device_release(dev); }
+tsim::Program::~Program() {
+  tsim::device_release(dev);
+  delete devtab;
+}
 
 void tsim::set_last_error(const char* msg) { std::snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
 
@@ -89,6 +92,11 @@ tsim_status tsim_program_info(const tsim_program* prog, tsim_program_info_t* out
     out->meas_words = (p.nmeas + 63) / 64;
     out->det_words = (p.ndet + 63) / 64;
     out->obs_words = (p.nobs + 63) / 64;
+    if (p.devtab) {
+      out->device_classes = p.devtab->layout.classes;
+      out->device_parities = p.devtab->layout.parities;
+      out->device_status = p.devtab->status;
+    }
   });
 }
 
@@ -107,6 +115,18 @@ tsim_status tsim_program_table_stats(const tsim_program* prog, int t, uint64_t* 
     *terms = p.tables[(size_t)t].terms.size();
     *factors = 0;
     for (const auto& tm : p.tables[(size_t)t].terms) *factors += tm.f.size();
+  });
+}
+
+tsim_status tsim_program_device_table_stats(const tsim_program* prog, int t, uint64_t out[3]) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!out || t < 0 || t >= (int)p.tables.size()) tsim::fail(TSIM_ERR_ARG, "bad table index");
+    if (!p.devtab || p.devtab->status != TSIM_OK) tsim::fail(TSIM_ERR_ARG, "program has no device tables");
+    const auto& L = p.devtab->layout;
+    out[0] = L.table_classes[(size_t)t];
+    out[1] = L.table_class_factors[(size_t)t];
+    out[2] = L.table_parities[(size_t)t];
   });
 }
 

@@ -27,6 +27,7 @@
 #include <numeric>
 
 #include "circuit.h"
+#include "device.h"
 #include "program.h"
 #include "zx.h"
 
@@ -728,6 +729,7 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
     }
     P.channels.push_back(std::move(pc));
   }
+  prepare_device_tables(P);
   return prog.release();
 }
 

@@ -1,26 +1,32 @@
-// GB300 (sm_103a) per-shot sampling kernels.
+// GB300 (sm_103a) per-shot sampling kernel.
 //
 // One thread evaluates one shot end to end (Sec. "Complexity", paragraph
 // "Sampling"):
 //   1. error mechanisms: one Philox4x32-10 word per reduced channel, outcome by
-//      integer threshold compare, f ^= column signature (Eq. detector_sampling);
+//      integer threshold compare, X ^= column signature (Eq. detector_sampling);
 //   2. outputs in autoregressive order: deterministic outputs are GF(2)
-//      parities of X = (f, random outputs) by AND + popcount; random outputs
-//      follow Algorithm 1, with every marginal P = sum_t c^t prod_k h(...)
-//      evaluated exactly: each factor's parities (Eq. parities) select one of
-//      four packed (zero, sqrt2-exponent, w-exponent) increments, a term is
-//      w^J sqrt2^S or 0, and the sum is accumulated in four integer
-//      coefficients of Z[w] (no floating point anywhere);
-//   3. the Bernoulli draw compares U * P_prev with 2^32 * P_1 exactly;
-//   4. bit-packed records.
-// The program tables are read-only and identical for every thread: all
-// threads of a warp read the same table word at the same time.
+//      parities of X = (f, random outputs); random outputs follow Algorithm 1,
+//      every marginal P = sum_t c^t prod_k h(...) evaluated exactly:
+//        - the distinct factor parities of the table (Eq. parities) are
+//          computed once per shot by AND + popcount into a register bitmask,
+//        - terms with identical factor lists are merged ahead of time into one
+//          class whose coefficient is the exact Z[w] sum of their c^t,
+//        - per class each factor's two parity bits select one of four packed
+//          (zero, sqrt2-exponent, w-exponent) increments; the class value is
+//          C w^J sqrt2^S or 0 and is accumulated into four int64 coefficients
+//          of Z[w] (no floating point);
+//   3. the Bernoulli draw compares U * P_prev with 2^32 * P_1 exactly (int128);
+//   4. bit-packed records streamed from registers.
+// The program tables are read-only and identical for every thread of a warp,
+// so every table load is a uniform (broadcast) load.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 
 #include "device.h"
 #include "zx.h"
@@ -39,13 +45,16 @@ enum : int { ST_NOT_REAL = 1, ST_OVERFLOW = 2, ST_ZERO_PROB = 4 };
 __device__ int g_status;
 
 constexpr int kMaxChains = 16;
-constexpr int kMaxOutWords = 64;  // 4096 outputs
+constexpr int kMaxOutWords = 64;  // measurement mode: 4096 outputs
+constexpr int kMaxParities = 256;
 constexpr int kThreads = 128;
 
-struct DChan { uint32_t n_out, thr_off, sig_off, pad; };
-struct DOut { int32_t random, cst, xbit, chain, table; uint32_t mask_off; };
-struct DTable { uint32_t term_off, n_terms; int32_t base, pad; };
-struct DTerm { uint32_t fac_off, n_fac; int32_t s0rel, j0; };
+enum : int { OUT_MASK = 0, OUT_BIT = 1, OUT_RANDOM = 2 };
+
+struct DChan { uint32_t n_out, thr_off, sig_off, thr0; };
+struct DOut { int32_t kind, cst, a, chain, table, pad; };
+struct DTable { uint32_t par_off, n_par, cls_off, n_cls; int32_t base, basis, pad1, pad2; };
+struct DClass { uint32_t fac_off, n_fac; int32_t mono, j0, d0, pad; long long c[4]; };
 
 struct DevView {
   int W;
@@ -58,9 +67,11 @@ struct DevView {
   const uint64_t* omask;
   const int32_t* chain_norm;
   const DTable* tab;
-  const DTerm* term;
-  const uint64_t* fuv;    // per factor: u[W], v[W]
-  const uint32_t* flut;   // per factor: 4 packed increments
+  const uint64_t* par;    // per table: n_par masks of W words (mask 0 = zero)
+  const DClass* cls;
+  const uint32_t* fidx;   // per factor: parity index of a | parity index of b << 8
+  const uint32_t* finc;   // per factor: 4 packed increments
+  const uint64_t* fcoord; // basis tables: per factor the coordinates of a and b (2 words)
   const int32_t* dmap_off;
   const int32_t* dmap_idx;
   const int32_t* omap_off;
@@ -88,29 +99,53 @@ void device_release(DeviceProgram* d) {
 bool monomial_of(const ZW& v, int* zero, int* s, int* j) {
   if (v.zero()) { *zero = 1; *s = 0; *j = 0; return true; }
   *zero = 0;
-  for (int ss = -16; ss <= 16; ++ss)
-    for (int jj = 0; jj < 8; ++jj) {
-      ZW m = ZW::omega(jj + 4);  // -w^jj
-      m.k = ss;
-      if (zw_add(v, m).zero()) { *s = ss; *j = jj; return true; }
+  // strip common factors 2 = sqrt2^2; a monomial then has the coefficient
+  // pattern of w^j (one entry +-1) or of sqrt2 w^j = w^(j+1) - w^(j+3)
+  // (entries +-1 two places apart)
+  __int128 c[4] = {v.c[0], v.c[1], v.c[2], v.c[3]};
+  int k = v.k;
+  while (!(c[0] & 1) && !(c[1] & 1) && !(c[2] & 1) && !(c[3] & 1)) {
+    for (auto& x : c) x /= 2;
+    k += 2;
+  }
+  int nz = 0;
+  for (auto x : c) nz += x != 0;
+  for (int jj = 0; jj < 8; ++jj) {
+    ZW m1 = ZW::omega(jj);
+    if (nz == 1 && m1.c[0] == c[0] && m1.c[1] == c[1] && m1.c[2] == c[2] && m1.c[3] == c[3]) {
+      *s = k;
+      *j = jj;
+      return true;
     }
+    ZW a = ZW::omega(jj + 1), b = ZW::omega(jj + 3);
+    bool eq = nz == 2;
+    for (int i = 0; i < 4 && eq; ++i) eq = (a.c[i] - b.c[i]) == c[i];
+    if (eq) {
+      *s = k + 1;
+      *j = jj;
+      return true;
+    }
+  }
   return false;
 }
 
 // ------------------------------------------------------------------ Philox
-// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products.
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products;
+// the round keys (key + r * Weyl constants) are the same for every call.
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+
 __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                              uint32_t k0, uint32_t k1, uint32_t o[4]) {
+                                              const RoundKeys& rk, uint32_t o[4]) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-    uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-    c0 = hi1 ^ c1 ^ k0;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    c0 = hi1 ^ c1 ^ rk.k0[r];
     c1 = lo1;
-    c2 = hi0 ^ c3 ^ k1;
+    c2 = hi0 ^ c3 ^ rk.k1[r];
     c3 = lo0;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
   }
   o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
 }
@@ -139,52 +174,136 @@ __device__ __forceinline__ int sign_xy(__int128 X, __int128 Y, int* st) {
   return y2 > x2 ? 1 : -1;
 }
 
+// coefficient k (0..7) of w^k in Z[w] basis {1, w, w^2, w^3}: w^k = +-w^(k mod 4)
+__device__ __forceinline__ long long pick(const long long c[4], int k) {
+  k &= 7;
+  const int q = k & 3;
+  const long long v = q == 0 ? c[0] : (q == 1 ? c[1] : (q == 2 ? c[2] : c[3]));
+  return k < 4 ? v : -v;
+}
+
 template <int W>
-__device__ RV eval_table(const DevView& V, int t, const uint64_t (&X)[W], int* st) {
-  const DTable tb = V.tab[t];
-  long long c[4] = {0, 0, 0, 0};
-  for (uint32_t q = 0; q < tb.n_terms; ++q) {
-    const DTerm tm = V.term[tb.term_off + q];
-    uint32_t acc = 0;
-    for (uint32_t k = 0; k < tm.n_fac; ++k) {
-      const size_t f = (size_t)tm.fac_off + k;
-      const uint64_t* uv = V.fuv + f * (2 * W);
-      uint64_t pa = 0, pb = 0;
+__device__ __forceinline__ int parity_w(const uint64_t* m, const uint64_t (&X)[W]) {
+  uint64_t acc = 0;
 #pragma unroll
-      for (int w = 0; w < W; ++w) {
-        pa ^= __ldg(uv + w) & X[w];
-        pb ^= __ldg(uv + W + w) & X[w];
-      }
-      int idx = (__popcll(pa) & 1) | ((__popcll(pb) & 1) << 1);
-      acc += __ldg(V.flut + f * 4 + idx);
-    }
-    if (acc >> 21) continue;  // some factor vanished
-    int J = (tm.j0 + (int)(acc & 0x7FF)) & 7;
-    int d = tm.s0rel + (int)((acc >> 11) & 0x3FF);
-    long long mag = 1ll << (d >> 1);
-    if (d & 1) {
-      // sqrt2 w^J = w^(J+1) - w^(J+3)
-      int a = (J + 1) & 7, b = (J + 3) & 7;
-      c[a & 3] += (a < 4) ? mag : -mag;
-      c[b & 3] -= (b < 4) ? mag : -mag;
-    } else {
-      c[J & 3] += (J < 4) ? mag : -mag;
-    }
-  }
-  // real part: Re(c0 + c1 w + c2 w^2 + c3 w^3) = (2 c0 + (c1 - c3) sqrt2) / 2
+  for (int w = 0; w < W; ++w) acc ^= __ldg(m + w) & X[w];
+  return __popcll(acc) & 1;
+}
+
+// real part of (c0 + c1 w + c2 w^2 + c3 w^3) sqrt2^base as (A + B sqrt2) 2^e:
+// Re = (2 c0 + (c1 - c3) sqrt2) / 2
+__device__ __forceinline__ RV to_real(const long long (&c)[4], int base, int* st) {
   if (c[2] != 0 || c[1] + c[3] != 0) *st |= ST_NOT_REAL;
   RV r;
   r.A = (__int128)2 * c[0];
   r.B = (__int128)c[1] - c[3];
-  int K = tb.base - 2;
+  int K = base - 2;
   if (K & 1) {
-    __int128 t2 = r.A;
+    const __int128 t2 = r.A;
     r.A = 2 * r.B;
     r.B = t2;
     K -= 1;
   }
   r.e = K / 2;
   return r;
+}
+
+// value w^J sqrt2^d C of one merged term, added into the four Z[w] coefficients
+__device__ __forceinline__ void accumulate(const DClass& C, uint32_t acc, long long (&c)[4]) {
+  const int J = (C.j0 + (int)(acc & 0x7FF)) & 7;
+  const int d = C.d0 + (int)((acc >> 11) & 0x3FF);
+  const int sh = d >> 1;
+  if (C.mono) {
+    const long long mag = 1ll << sh;
+    if (d & 1) {  // sqrt2 w^J = w^(J+1) - w^(J+3)
+      const int a = (J + 1) & 7, b = (J + 3) & 7;
+      c[a & 3] += (a < 4) ? mag : -mag;
+      c[b & 3] -= (b < 4) ? mag : -mag;
+    } else {
+      c[J & 3] += (J < 4) ? mag : -mag;
+    }
+  } else {
+    // w^J C: coefficient i takes C's coefficient of w^(i - J)
+    long long r[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r[i] = pick(C.c, i - J + 8);
+    if (d & 1) {  // times sqrt2 = w - w^3
+      const long long t0 = r[1] - r[3], t1 = r[0] + r[2], t2 = r[1] + r[3], t3 = r[2] - r[0];
+      r[0] = t0; r[1] = t1; r[2] = t2; r[3] = t3;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[i] += r[i] * (1ll << sh);
+  }
+}
+
+template <int W>
+__device__ RV eval_table(const DevView& V, int t, const uint64_t (&X)[W], int* st) {
+  const DTable tb = V.tab[t];
+  long long c[4] = {0, 0, 0, 0};
+  if (tb.basis) {
+    // parities in a GF(2) basis of the table's mask span: Y holds the basis
+    // parities and every factor parity is <coordinates, Y>
+    uint64_t Y = 0;
+    for (uint32_t q = 0; q < tb.n_par; ++q)
+      Y |= (uint64_t)parity_w<W>(V.par + (size_t)(tb.par_off + q) * W, X) << q;
+    for (uint32_t q = 0; q < tb.n_cls; ++q) {
+      const DClass& C = V.cls[tb.cls_off + q];
+      const uint32_t fo = C.fac_off, nf = C.n_fac;
+      uint32_t acc = 0;
+      for (uint32_t k = 0; k < nf; ++k) {
+        const uint64_t ua = __ldg(V.fcoord + 2 * (size_t)(fo + k)), ub = __ldg(V.fcoord + 2 * (size_t)(fo + k) + 1);
+        const uint32_t a = __popcll(ua & Y) & 1, b = __popcll(ub & Y) & 1;
+        acc += __ldg(V.finc + (size_t)(fo + k) * 4 + (a | (b << 1)));
+      }
+      if (acc >> 21) continue;
+      accumulate(C, acc, c);
+    }
+    return to_real(c, tb.base, st);
+  }
+  // distinct factor parities of this table, once per shot, into 256 bits
+  // (q is the same for every thread of a warp, so the word choice is uniform)
+  uint64_t P0 = 0, P1 = 0, P2 = 0, P3 = 0;
+  for (uint32_t q = 1; q < tb.n_par; ++q) {
+    const uint64_t bit = (uint64_t)parity_w<W>(V.par + (size_t)(tb.par_off + q) * W, X) << (q & 63);
+    if (q < 64) P0 |= bit;
+    else if (q < 128) P1 |= bit;
+    else if (q < 192) P2 |= bit;
+    else P3 |= bit;
+  }
+  auto pbit = [&](uint32_t i) -> uint32_t {
+    const uint64_t w = i < 128 ? (i < 64 ? P0 : P1) : (i < 192 ? P2 : P3);
+    return (uint32_t)((w >> (i & 63)) & 1);
+  };
+  for (uint32_t q = 0; q < tb.n_cls; ++q) {
+    const DClass& C = V.cls[tb.cls_off + q];
+    const uint32_t fo = C.fac_off, nf = C.n_fac;
+    uint32_t acc = 0;
+    for (uint32_t k = 0; k < nf; ++k) {
+      const uint32_t ix = __ldg(V.fidx + fo + k);
+      const uint32_t ia = ix & 0xFF, ib = (ix >> 8) & 0xFF;
+      const uint32_t a = pbit(ia), b = pbit(ib);
+      acc += __ldg(V.finc + (size_t)(fo + k) * 4 + (a | (b << 1)));
+    }
+    if (acc >> 21) continue;  // some factor vanished
+    accumulate(C, acc, c);
+  }
+  return to_real(c, tb.base, st);
+}
+
+template <int W>
+__device__ __forceinline__ void set_xbit(uint64_t (&X)[W], int b, bool on) {
+#pragma unroll
+  for (int w = 0; w < W; ++w)
+    if (w == (b >> 6)) X[w] = on ? (X[w] | (1ull << (b & 63))) : (X[w] & ~(1ull << (b & 63)));
+}
+
+template <int W>
+__device__ __forceinline__ int get_xbit(const uint64_t (&X)[W], int b) {
+  uint64_t v = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w)
+    if (w == (b >> 6)) v = X[w];
+  return (int)((v >> (b & 63)) & 1);
 }
 
 template <int W>
@@ -196,7 +315,17 @@ __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, u
   const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nshots) return;
   const uint64_t shot = shot0 + s;
-  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  RoundKeys rk;
+  {
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      rk.k0[r] = k0;
+      rk.k1[r] = k1;
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+  }
   const uint32_t c0 = (uint32_t)shot, c1 = (uint32_t)(shot >> 32);
   int st = 0;
 
@@ -206,47 +335,45 @@ __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, u
   for (int w = 0; w < W; ++w) X[w] = 0;
   for (int c = 0; c < V.n_ch; c += 4) {
     uint32_t u[4];
-    philox4x32_10(c0, c1, 0u, (uint32_t)(c >> 2), k0, k1, u);
+    philox4x32_10(c0, c1, 0u, (uint32_t)(c >> 2), rk, u);
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const int ci = c + l;
       if (ci >= V.n_ch) break;
       const DChan ch = V.ch[ci];
       const uint32_t U = u[l];
+      if (U < ch.thr0) continue;  // outcome 0: nothing fires (the common case)
       const uint32_t* thr = V.thr + ch.thr_off;
-      uint32_t o = 0;
+      uint32_t o = 1;
       while (o + 1 < ch.n_out && U >= __ldg(thr + o)) ++o;
-      if (o) {
-        const uint64_t* sg = V.sig + ch.sig_off + (size_t)o * W;
+      if (o >= ch.n_out) continue;
+      const uint64_t* sg = V.sig + ch.sig_off + (size_t)o * W;
 #pragma unroll
-        for (int w = 0; w < W; ++w) X[w] ^= __ldg(sg + w);
-      }
+      for (int w = 0; w < W; ++w) X[w] ^= __ldg(sg + w);
     }
   }
 
   // 2-3. outputs in autoregressive order (Algorithm 1 per chain)
   RV pp[kMaxChains];
   for (int c = 0; c < V.n_chains; ++c) pp[c] = eval_table<W>(V, V.chain_norm[c], X, &st);
-  uint64_t ob[kMaxOutWords];
-  const int obw = (V.n_out + 63) >> 6;
-  for (int w = 0; w < obw; ++w) ob[w] = 0;
+  const int dw = (V.ndet + 63) >> 6, mw = (V.nmeas + 63) >> 6, ow = (V.nobs + 63) >> 6;
+  uint64_t ob[kMaxOutWords];  // measurement mode only
+  uint64_t cur = 0;           // detector mode: current record word
+  bool any_det = false;
   for (int i = 0; i < V.n_out; ++i) {
     const DOut o = V.out[i];
     int bit;
-    if (!o.random) {
-      const uint64_t* m = V.omask + o.mask_off;
-      uint64_t acc = 0;
-#pragma unroll
-      for (int w = 0; w < W; ++w) acc ^= __ldg(m + w) & X[w];
-      bit = (__popcll(acc) & 1) ^ o.cst;
+    if (o.kind == OUT_BIT) {
+      bit = get_xbit<W>(X, o.a) ^ o.cst;
+    } else if (o.kind == OUT_MASK) {
+      bit = parity_w<W>(V.omask + o.a, X) ^ o.cst;
     } else {
-      const int xb = o.xbit;
-      X[xb >> 6] |= 1ull << (xb & 63);
+      set_xbit<W>(X, o.a, true);
       const RV p1 = eval_table<W>(V, o.table, X, &st);
       const RV pv = pp[o.chain];
       if (sign_xy(pv.A, pv.B, &st) <= 0) st |= ST_ZERO_PROB;
       uint32_t u[4];
-      philox4x32_10(c0, c1, 1u, (uint32_t)(i >> 2), k0, k1, u);
+      philox4x32_10(c0, c1, 1u, (uint32_t)(i >> 2), rk, u);
       const uint32_t U = u[i & 3];
       // bit = 1 iff U * P_prev < 2^32 * P_1
       const int e = min(pv.e, p1.e + 32);
@@ -264,38 +391,34 @@ __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, u
         d.B = shl_chk(pv.B, pv.e - e2, &st) - shl_chk(p1.B, p1.e - e2, &st);
         d.e = e2;
         pp[o.chain] = d;
-        X[xb >> 6] &= ~(1ull << (xb & 63));
+        set_xbit<W>(X, o.a, false);
       }
     }
-    ob[i >> 6] |= (uint64_t)bit << (i & 63);
+    if (V.mode == 0) {
+      // detectors are outputs [0, ndet), observables [ndet, ndet + nobs)
+      const bool is_det = i < V.ndet;
+      const int j = is_det ? i : i - V.ndet;
+      cur |= (uint64_t)bit << (j & 63);
+      const bool last = is_det ? (i + 1 == V.ndet) : (i + 1 == V.n_out);
+      if ((j & 63) == 63 || last) {
+        if (is_det) {
+          any_det |= cur != 0;
+          if (det) det[s * dw + (j >> 6)] = cur;
+        } else if (obs) {
+          obs[s * ow + (j >> 6)] = cur;
+        }
+        cur = 0;
+      }
+    } else {
+      if ((i & 63) == 0) ob[i >> 6] = 0;
+      ob[i >> 6] |= (uint64_t)bit << (i & 63);
+    }
   }
 
-  // 4. records
-  auto bits_at = [&](int start, int w) -> uint64_t {  // 64 output bits from `start`
-    const int q = start + 64 * w;
-    const int wi = q >> 6, sh = q & 63;
-    uint64_t lo = wi < obw ? ob[wi] : 0;
-    if (!sh) return lo;
-    uint64_t hi = wi + 1 < obw ? ob[wi + 1] : 0;
-    return (lo >> sh) | (hi << (64 - sh));
-  };
-  auto tail = [](int n, int w) -> uint64_t {
-    const int r = n - 64 * w;
-    return r >= 64 ? ~0ull : ((1ull << r) - 1);
-  };
-  bool any_det = false;
-  const int dw = (V.ndet + 63) >> 6, mw = (V.nmeas + 63) >> 6, ow = (V.nobs + 63) >> 6;
-  if (V.mode == 0) {
-    for (int w = 0; w < dw; ++w) {
-      const uint64_t v = bits_at(0, w) & tail(V.ndet, w);
-      any_det |= v != 0;
-      if (det) det[s * dw + w] = v;
-    }
-    if (obs)
-      for (int w = 0; w < ow; ++w) obs[s * ow + w] = bits_at(V.ndet, w) & tail(V.nobs, w);
-  } else {
+  // 4. measurement-mode records
+  if (V.mode != 0) {
     if (meas)
-      for (int w = 0; w < mw; ++w) meas[s * mw + w] = bits_at(0, w) & tail(V.nmeas, w);
+      for (int w = 0; w < mw; ++w) meas[s * mw + w] = ob[w];
     for (int w = 0; w < dw; ++w) {
       uint64_t v = 0;
       for (int b = 0; b < 64 && 64 * w + b < V.ndet; ++b) {
@@ -329,7 +452,7 @@ __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, u
   if (st) atomicOr(&g_status, st);
 }
 
-// ------------------------------------------------------------------ upload
+// ------------------------------------------------------ host-side packing
 namespace {
 
 int padded_words_or_zero(int W) {
@@ -338,10 +461,7 @@ int padded_words_or_zero(int W) {
   return 0;
 }
 
-// Byte sinks for the table packer: sections start on 256-byte boundaries and
-// alignment padding is zero.  VecSink grows a host vector; FixedSink writes
-// into a caller-provided buffer of fixed capacity and never allocates.
-struct VecSink {
+struct Packer {
   std::vector<unsigned char> b;
   size_t section() {
     b.resize((b.size() + 255) & ~(size_t)255, 0);
@@ -352,43 +472,22 @@ struct VecSink {
     b.resize(o + n);
     if (n) std::memcpy(b.data() + o, p, n);
   }
-  size_t size() const { return b.size(); }
-};
-
-struct FixedSink {
-  unsigned char* base;
-  size_t cap;
-  size_t n = 0;
-  bool overflow = false;
-  size_t section() {
-    size_t off = (n + 255) & ~(size_t)255;
-    if (off > cap) overflow = true;
-    else std::memset(base + n, 0, off - n);
-    n = off;
-    return off;
+  void put_padded(const std::vector<uint64_t>& m, int W) {
+    for (int i = 0; i < W; ++i) {
+      uint64_t x = (size_t)i < m.size() ? m[(size_t)i] : 0;
+      put(&x, 8);
+    }
   }
-  void put(const void* p, size_t k) {
-    if (overflow || n + k > cap) { overflow = true; n += k; return; }
-    if (k) std::memcpy(base + n, p, k);
-    n += k;
-  }
-  size_t size() const { return n; }
-};
-
-struct Layout {
-  size_t o_ch = 0, o_thr = 0, o_sig = 0, o_out = 0, o_om = 0, o_cn = 0, o_tab = 0, o_term = 0,
-         o_fuv = 0, o_flut = 0, o_dmo = 0, o_dmi = 0, o_omo = 0, o_omi = 0, total = 0;
-  int W = 1;
 };
 
 // Four packed increments of one factor, inc = j | s << 11 | zero << 21
-// (J in bits 0-10, S in 11-20, vanishing factors in 21-31), with s relative
-// to the factor's smallest magnitude exponent smin.
-bool factor_lut(const ProgFactor& f, uint32_t inc[4], int* smin_out, int* spread) {
+// (J in bits 0-10, S in 11-20, vanishing factors in 21-31), s relative to the
+// factor's smallest magnitude exponent smin.
+bool factor_lut(int kind, int alpha, int beta, uint32_t inc[4], int* smin_out, int* spread) {
   Factor fc;
-  fc.kind = f.kind;
-  fc.alpha = f.alpha;
-  fc.beta = f.beta;
+  fc.kind = kind;
+  fc.alpha = alpha;
+  fc.beta = beta;
   int zs[4], ss[4], js[4], smin = 1 << 20, smax = -(1 << 20);
   for (int idx = 0; idx < 4; ++idx) {
     if (!monomial_of(factor_value(fc, idx & 1, idx >> 1), &zs[idx], &ss[idx], &js[idx])) return false;
@@ -403,62 +502,41 @@ bool factor_lut(const ProgFactor& f, uint32_t inc[4], int* smin_out, int* spread
   return true;
 }
 
-// raw sqrt2 exponent (s0 plus every factor's smin) and magnitude spread of a term
-bool term_exponents(const ProgTerm& tm, int* raw_s0, int* spread) {
+int log2_ceil(unsigned __int128 x) {
+  int l = 0;
+  while (l < 127 && ((unsigned __int128)1 << l) < x) ++l;
+  return l;
+}
+
+struct PackError {
+  tsim_status st;
+  const char* msg;
+};
+
+struct Lut {
   uint32_t inc[4];
-  int s0 = tm.s0, sp = 0;
-  for (const ProgFactor& f : tm.f) {
-    int smin, spr;
-    if (!factor_lut(f, inc, &smin, &spr)) return false;
-    s0 += smin;
-    sp += spr;
-  }
-  *raw_s0 = s0;
-  *spread = sp;
-  return true;
-}
+  int smin, spread;
+};
 
-// base exponent of a table = smallest raw term exponent; checks that the
-// 64-bit coefficient accumulation cannot overflow
-tsim_status table_base(const ProgTable& tb, int* base, const char** msg) {
-  int b = 0, dmax = 0;
-  bool first = true;
-  for (const ProgTerm& tm : tb.terms) {
-    int r, sp;
-    if (tm.f.size() > 255) { *msg = "term with more than 255 factors"; return TSIM_ERR_OVERFLOW_BOUND; }
-    if (!term_exponents(tm, &r, &sp)) { *msg = "factor value is not a monomial of bounded spread"; return TSIM_ERR_INTERNAL; }
-    if (first || r < b) b = r;
-    first = false;
-  }
-  for (const ProgTerm& tm : tb.terms) {
-    int r, sp;
-    term_exponents(tm, &r, &sp);
-    dmax = std::max(dmax, r - b + sp);
-  }
-  int lg = 0;
-  while ((1ull << lg) < (uint64_t)std::max<size_t>(1, tb.terms.size())) ++lg;
-  // |coefficient| <= terms * 2^(dmax/2 + 1) must stay below 2^62
-  if (dmax / 2 + 1 + lg >= 62) { *msg = "table magnitudes exceed 64-bit accumulation"; return TSIM_ERR_OVERFLOW_BOUND; }
-  *base = b;
-  return TSIM_OK;
-}
-
-template <class Sink>
-void put_padded(Sink& s, const std::vector<uint64_t>& m, int W) {
-  for (int i = 0; i < W; ++i) {
-    uint64_t x = (size_t)i < m.size() ? m[(size_t)i] : 0;
-    s.put(&x, 8);
-  }
-}
-
-// Packs the program into the device table layout.  Heap-free apart from
-// what the sink itself does.
-template <class Sink>
-tsim_status pack_tables(const Program& p, Sink& s, Layout& L, const char** msg) {
+void pack(const Program& p, DeviceTables& out) {
+  std::map<std::tuple<int, int, int>, Lut> lut_cache;
+  auto lut = [&](int kind, int alpha, int beta) -> const Lut& {
+    auto key = std::make_tuple(kind, alpha & 7, beta & 7);
+    auto it = lut_cache.find(key);
+    if (it != lut_cache.end()) return it->second;
+    Lut l{};
+    if (!factor_lut(kind, alpha, beta, l.inc, &l.smin, &l.spread))
+      throw PackError{TSIM_ERR_INTERNAL, "factor value is not a monomial of bounded spread"};
+    return lut_cache.emplace(key, l).first->second;
+  };
   const int W = padded_words_or_zero(p.W);
-  if (!W) { *msg = "per-shot vector wider than 2048 bits is not supported"; return TSIM_ERR_ARG; }
-  if ((int)p.chain_norm.size() > kMaxChains) { *msg = "too many autoregressive chains for the kernel"; return TSIM_ERR_ARG; }
-  if ((int)p.outputs.size() > kMaxOutWords * 64) { *msg = "too many outputs for the kernel"; return TSIM_ERR_ARG; }
+  if (!W) throw PackError{TSIM_ERR_ARG, "per-shot vector wider than 2048 bits is not supported"};
+  if ((int)p.chain_norm.size() > kMaxChains) throw PackError{TSIM_ERR_ARG, "too many autoregressive chains for the kernel"};
+  if (p.mode == TSIM_MODE_MEASUREMENTS && (int)p.outputs.size() > kMaxOutWords * 64)
+    throw PackError{TSIM_ERR_ARG, "too many measurement outputs for the kernel"};
+  Packer s;
+  DeviceLayout& L = out.layout;
+  L = DeviceLayout();
   L.W = W;
   // channels
   L.o_ch = s.section();
@@ -469,11 +547,12 @@ tsim_status pack_tables(const Program& p, Sink& s, Layout& L, const char** msg) 
       d.n_out = (uint32_t)c.sig.size();
       d.thr_off = thr_off;
       d.sig_off = sig_off;
+      d.thr0 = c.thr.empty() ? 0xFFFFFFFFu : c.thr[0];
       thr_off += (uint32_t)c.thr.size();
       sig_off += (uint32_t)(c.sig.size() * (size_t)W);
       s.put(&d, sizeof d);
       for (size_t w = 0; !c.sig.empty() && w < c.sig[0].size(); ++w)
-        if (c.sig[0][w]) { *msg = "channel outcome 0 must not flip anything"; return TSIM_ERR_INTERNAL; }
+        if (c.sig[0][w]) throw PackError{TSIM_ERR_INTERNAL, "channel outcome 0 must not flip anything"};
     }
   }
   L.o_thr = s.section();
@@ -482,77 +561,212 @@ tsim_status pack_tables(const Program& p, Sink& s, Layout& L, const char** msg) 
   { uint32_t z = 0; s.put(&z, 4); }
   L.o_sig = s.section();
   for (const ProgChannel& c : p.channels)
-    for (const auto& sg : c.sig) put_padded(s, sg, W);
+    for (const auto& sg : c.sig) s.put_padded(sg, W);
   // outputs
   L.o_out = s.section();
   {
-    uint32_t mo = 0;
+    int32_t mo = 0;
     for (const ProgOutput& o : p.outputs) {
       DOut d{};
-      d.random = o.random ? 1 : 0;
       d.cst = o.cst;
-      d.xbit = o.xbit;
-      d.chain = o.chain;
-      d.table = o.table;
-      d.mask_off = mo;
-      mo += (uint32_t)W;
+      if (o.random) {
+        d.kind = OUT_RANDOM;
+        d.a = o.xbit;
+        d.chain = o.chain;
+        d.table = o.table;
+      } else {
+        int ones = 0, pos = -1;
+        for (size_t w = 0; w < o.mask.size(); ++w)
+          for (int bb = 0; bb < 64; ++bb)
+            if ((o.mask[w] >> bb) & 1) { ++ones; pos = (int)(w * 64 + (size_t)bb); }
+        if (ones == 1) { d.kind = OUT_BIT; d.a = pos; }
+        else { d.kind = OUT_MASK; d.a = mo; }
+      }
+      mo += W;
       s.put(&d, sizeof d);
     }
   }
   L.o_om = s.section();
-  for (const ProgOutput& o : p.outputs) put_padded(s, o.mask, W);
+  for (const ProgOutput& o : p.outputs) s.put_padded(o.mask, W);
   L.o_cn = s.section();
   for (int c : p.chain_norm) { int32_t v = c; s.put(&v, 4); }
   { int32_t z = 0; s.put(&z, 4); }
-  // tables
+
+  // tables: distinct parities, then terms merged into classes with equal factors
+  struct FacKey {
+    int kind, alpha, beta, ia, ib;
+    bool operator<(const FacKey& o) const {
+      return std::tie(kind, alpha, beta, ia, ib) < std::tie(o.kind, o.alpha, o.beta, o.ia, o.ib);
+    }
+    bool operator==(const FacKey& o) const {
+      return kind == o.kind && alpha == o.alpha && beta == o.beta && ia == o.ia && ib == o.ib;
+    }
+  };
+  struct Cls {
+    std::vector<FacKey> f;
+    ZW coef;
+  };
+  std::vector<DTable> tabs;
+  std::vector<uint64_t> par;
+  std::vector<DClass> cls;
+  std::vector<uint32_t> fidx, finc;
+  std::vector<uint64_t> fcoord;
+  for (const ProgTable& tb : p.tables) {
+    DTable dt{};
+    dt.par_off = (uint32_t)(par.size() / (size_t)W);
+    std::map<std::vector<uint64_t>, int> pidx;
+    std::vector<std::vector<uint64_t>> plist;
+    auto parity_index = [&](const std::vector<uint64_t>& m) {
+      std::vector<uint64_t> key((size_t)W, 0);
+      for (size_t i = 0; i < m.size() && i < (size_t)W; ++i) key[i] = m[i];
+      auto it = pidx.find(key);
+      if (it != pidx.end()) return it->second;
+      int id = (int)plist.size();
+      pidx[key] = id;
+      plist.push_back(key);
+      return id;
+    };
+    parity_index(std::vector<uint64_t>((size_t)W, 0));  // index 0: the zero parity
+    std::map<std::vector<FacKey>, size_t> cidx;
+    std::vector<Cls> cl;
+    for (const ProgTerm& tm : tb.terms) {
+      std::vector<FacKey> fk;
+      for (const ProgFactor& f : tm.f) {
+        FacKey k{f.kind, f.alpha & 7, f.beta & 7, parity_index(f.u), parity_index(f.v)};
+        fk.push_back(k);
+      }
+      std::sort(fk.begin(), fk.end());
+      ZW c = ZW::omega(tm.j0);
+      c.k = tm.s0;
+      auto it = cidx.find(fk);
+      if (it == cidx.end()) {
+        cidx[fk] = cl.size();
+        cl.push_back({fk, c});
+      } else {
+        cl[it->second].coef = zw_add(cl[it->second].coef, c);
+      }
+    }
+    // few distinct parities: evaluate each once per shot and index them;
+    // many: evaluate a GF(2) basis of their span and give every parity its
+    // coordinates in that basis
+    std::vector<uint64_t> coords(plist.size(), 0);
+    if (plist.size() <= (size_t)kMaxParities) {
+      for (const auto& m : plist) par.insert(par.end(), m.begin(), m.end());
+      dt.n_par = (uint32_t)plist.size();
+    } else {
+      dt.basis = 1;
+      std::vector<std::vector<uint64_t>> bvec, borig;
+      std::vector<uint64_t> bcomb;
+      std::vector<int> bpiv;
+      for (size_t i = 1; i < plist.size(); ++i) {
+        std::vector<uint64_t> v = plist[i];
+        uint64_t comb = 0;
+        for (size_t j = 0; j < bvec.size(); ++j)
+          if ((v[(size_t)bpiv[j] >> 6] >> (bpiv[j] & 63)) & 1) {
+            for (int w = 0; w < W; ++w) v[(size_t)w] ^= bvec[j][(size_t)w];
+            comb ^= bcomb[j];
+          }
+        int piv = -1;
+        for (int w = 0; w < W && piv < 0; ++w)
+          if (v[(size_t)w]) piv = w * 64 + __builtin_ctzll(v[(size_t)w]);
+        if (piv < 0) { coords[i] = comb; continue; }
+        if (borig.size() >= 64) throw PackError{TSIM_ERR_ARG, "table parities span more than 64 dimensions"};
+        const uint64_t me = 1ull << borig.size();
+        borig.push_back(plist[i]);
+        bvec.push_back(v);
+        bcomb.push_back(comb ^ me);
+        bpiv.push_back(piv);
+        coords[i] = me;
+      }
+      for (const auto& m : borig) par.insert(par.end(), m.begin(), m.end());
+      dt.n_par = (uint32_t)borig.size();
+    }
+    // per class: exponent of its smallest possible magnitude
+    struct Prep { size_t i; int raw, spread, mono, j, zero; };
+    std::vector<Prep> prep;
+    for (size_t i = 0; i < cl.size(); ++i) {
+      if (cl[i].coef.zero()) continue;  // exact cancellation between terms
+      if (cl[i].f.size() > 255) throw PackError{TSIM_ERR_OVERFLOW_BOUND, "term with more than 255 factors"};
+      int smin_sum = 0, spread = 0;
+      for (const FacKey& k : cl[i].f) {
+        const Lut& l = lut(k.kind, k.alpha, k.beta);
+        smin_sum += l.smin;
+        spread += l.spread;
+      }
+      int z, ms, mj;
+      Prep pr{i, 0, spread, 0, 0, 0};
+      if (monomial_of(cl[i].coef, &z, &ms, &mj)) {
+        pr.mono = 1;
+        pr.j = mj;
+        pr.raw = ms + smin_sum;
+      } else {
+        pr.raw = cl[i].coef.k + smin_sum;
+      }
+      prep.push_back(pr);
+    }
+    int base = 0;
+    for (size_t q = 0; q < prep.size(); ++q) base = q ? std::min(base, prep[q].raw) : prep[q].raw;
+    dt.base = base;
+    dt.cls_off = (uint32_t)cls.size();
+    dt.n_cls = (uint32_t)prep.size();
+    unsigned __int128 bound = 0;
+    for (const Prep& pr : prep) {
+      const Cls& c = cl[pr.i];
+      DClass d{};
+      d.fac_off = (uint32_t)fidx.size();
+      d.n_fac = (uint32_t)c.f.size();
+      d.mono = pr.mono;
+      d.j0 = pr.j;
+      d.d0 = pr.raw - base;
+      unsigned __int128 mag = 1;
+      if (!pr.mono) {
+        for (int i = 0; i < 4; ++i) {
+          if (c.coef.c[i] > ((__int128)1 << 60) || c.coef.c[i] < -((__int128)1 << 60))
+            throw PackError{TSIM_ERR_OVERFLOW_BOUND, "merged term coefficient exceeds 60 bits"};
+          d.c[i] = (long long)c.coef.c[i];
+        }
+        mag = 0;
+        for (int i = 0; i < 4; ++i) mag += (unsigned __int128)(d.c[i] < 0 ? -d.c[i] : d.c[i]);
+        mag *= 2;  // the sqrt2 multiplication at most doubles the largest coefficient
+      }
+      const int dm = d.d0 + pr.spread;
+      if (dm / 2 + log2_ceil(mag) >= 100) throw PackError{TSIM_ERR_OVERFLOW_BOUND, "table magnitudes exceed 64-bit accumulation"};
+      bound += mag << (dm / 2 + 1);
+      for (const FacKey& k : c.f) {
+        const Lut& l = lut(k.kind, k.alpha, k.beta);
+        fidx.push_back(dt.basis ? 0u : ((uint32_t)k.ia | ((uint32_t)k.ib << 8)));
+        finc.insert(finc.end(), l.inc, l.inc + 4);
+        fcoord.push_back(dt.basis ? coords[(size_t)k.ia] : 0);
+        fcoord.push_back(dt.basis ? coords[(size_t)k.ib] : 0);
+        L.class_factors++;
+      }
+      cls.push_back(d);
+    }
+    // every coefficient stays below 2^62 in absolute value
+    if (bound >= ((unsigned __int128)1 << 62)) throw PackError{TSIM_ERR_OVERFLOW_BOUND, "table magnitudes exceed 64-bit accumulation"};
+    L.classes += prep.size();
+    L.parities += plist.size() - 1;
+    L.table_classes.push_back(prep.size());
+    L.table_parities.push_back(plist.size() - 1);
+    {
+      uint64_t nf = 0;
+      for (const Prep& pr : prep) nf += cl[pr.i].f.size();
+      L.table_class_factors.push_back(nf);
+    }
+    tabs.push_back(dt);
+  }
   L.o_tab = s.section();
-  {
-    uint32_t term_off = 0;
-    for (const ProgTable& tb : p.tables) {
-      DTable dt{};
-      dt.term_off = term_off;
-      dt.n_terms = (uint32_t)tb.terms.size();
-      tsim_status st = table_base(tb, &dt.base, msg);
-      if (st != TSIM_OK) return st;
-      term_off += dt.n_terms;
-      s.put(&dt, sizeof dt);
-    }
-  }
-  L.o_term = s.section();
-  {
-    uint32_t fac_off = 0;
-    for (const ProgTable& tb : p.tables) {
-      int base = 0;
-      table_base(tb, &base, msg);
-      for (const ProgTerm& tm : tb.terms) {
-        DTerm d{};
-        int r, sp;
-        term_exponents(tm, &r, &sp);
-        d.fac_off = fac_off;
-        d.n_fac = (uint32_t)tm.f.size();
-        d.s0rel = r - base;
-        d.j0 = tm.j0 & 7;
-        fac_off += d.n_fac;
-        s.put(&d, sizeof d);
-      }
-    }
-  }
-  L.o_fuv = s.section();
-  for (const ProgTable& tb : p.tables)
-    for (const ProgTerm& tm : tb.terms)
-      for (const ProgFactor& f : tm.f) {
-        put_padded(s, f.u, W);
-        put_padded(s, f.v, W);
-      }
-  L.o_flut = s.section();
-  for (const ProgTable& tb : p.tables)
-    for (const ProgTerm& tm : tb.terms)
-      for (const ProgFactor& f : tm.f) {
-        uint32_t inc[4];
-        int smin, spr;
-        factor_lut(f, inc, &smin, &spr);
-        s.put(inc, sizeof inc);
-      }
+  if (!tabs.empty()) s.put(tabs.data(), tabs.size() * sizeof(DTable));
+  L.o_par = s.section();
+  if (!par.empty()) s.put(par.data(), par.size() * 8);
+  L.o_cls = s.section();
+  if (!cls.empty()) s.put(cls.data(), cls.size() * sizeof(DClass));
+  L.o_fidx = s.section();
+  if (!fidx.empty()) s.put(fidx.data(), fidx.size() * 4);
+  L.o_finc = s.section();
+  if (!finc.empty()) s.put(finc.data(), finc.size() * 4);
+  L.o_fco = s.section();
+  if (!fcoord.empty()) s.put(fcoord.data(), fcoord.size() * 8);
   // measurement-mode detector / observable maps (CSR)
   auto csr = [&](const std::vector<std::vector<int>>& m, size_t* o_off, size_t* o_idx) {
     *o_off = s.section();
@@ -568,10 +782,10 @@ tsim_status pack_tables(const Program& p, Sink& s, Layout& L, const char** msg) 
   csr(p.detmap, &L.o_dmo, &L.o_dmi);
   csr(p.obsmap, &L.o_omo, &L.o_omi);
   L.total = s.section();
-  return TSIM_OK;
+  out.blob.swap(s.b);
 }
 
-DevView make_view(const unsigned char* base, const Layout& L, const Program& p) {
+DevView make_view(const unsigned char* base, const DeviceLayout& L, const Program& p) {
   DevView v{};
   v.W = L.W;
   v.n_ch = (int)p.channels.size();
@@ -589,9 +803,11 @@ DevView make_view(const unsigned char* base, const Layout& L, const Program& p) 
   v.omask = (const uint64_t*)(base + L.o_om);
   v.chain_norm = (const int32_t*)(base + L.o_cn);
   v.tab = (const DTable*)(base + L.o_tab);
-  v.term = (const DTerm*)(base + L.o_term);
-  v.fuv = (const uint64_t*)(base + L.o_fuv);
-  v.flut = (const uint32_t*)(base + L.o_flut);
+  v.par = (const uint64_t*)(base + L.o_par);
+  v.cls = (const DClass*)(base + L.o_cls);
+  v.fidx = (const uint32_t*)(base + L.o_fidx);
+  v.finc = (const uint32_t*)(base + L.o_finc);
+  v.fcoord = (const uint64_t*)(base + L.o_fco);
   v.dmap_off = (const int32_t*)(base + L.o_dmo);
   v.dmap_idx = (const int32_t*)(base + L.o_dmi);
   v.omap_off = (const int32_t*)(base + L.o_omo);
@@ -599,26 +815,28 @@ DevView make_view(const unsigned char* base, const Layout& L, const Program& p) 
   return v;
 }
 
+const DeviceTables& tables_of(const Program& p) {
+  if (!p.devtab) fail(TSIM_ERR_INTERNAL, "program has no device tables");
+  if (p.devtab->status != TSIM_OK) fail(p.devtab->status, p.devtab->message);
+  return *p.devtab;
+}
+
 DeviceProgram* upload(const Program& p) {
-  VecSink b;
-  Layout L;
-  const char* msg = "";
-  tsim_status st = pack_tables(p, b, L, &msg);
-  if (st != TSIM_OK) fail(st, msg);
+  const DeviceTables& T = tables_of(p);
   auto* d = new DeviceProgram();
   TSIM_CUDA(cudaGetDevice(&d->device));
-  cudaError_t e = cudaMalloc(&d->blob, std::max<size_t>(b.size(), 256));
+  cudaError_t e = cudaMalloc(&d->blob, std::max<size_t>(T.blob.size(), 256));
   if (e != cudaSuccess) {
     delete d;
     fail(TSIM_ERR_OOM, std::string("cudaMalloc of program tables: ") + cudaGetErrorString(e));
   }
-  e = cudaMemcpy(d->blob, b.b.data(), b.size(), cudaMemcpyHostToDevice);
+  e = cudaMemcpy(d->blob, T.blob.data(), T.blob.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(d->blob);
     delete d;
     fail(TSIM_ERR_CUDA, std::string("cudaMemcpy of program tables: ") + cudaGetErrorString(e));
   }
-  d->v = make_view((const unsigned char*)d->blob, L, p);
+  d->v = make_view((const unsigned char*)d->blob, T.layout, p);
   return d;
 }
 
@@ -634,31 +852,45 @@ const DevView& ensure_uploaded(const Program& p) {
   return slot->v;
 }
 
-template <int W>
-void launch_w(const DevView& v, const SampleArgs& a, cudaStream_t s) {
-  const uint64_t blocks = (a.shots + kThreads - 1) / kThreads;
-  if (blocks > 0x7FFFFFFFull) fail(TSIM_ERR_ARG, "too many shots for one launch");
-  k_sample<W><<<(unsigned)blocks, kThreads, 0, s>>>(v, a.seed, a.shot_offset, a.shots, a.meas, a.det,
-                                                     a.obs, a.accept);
+cudaError_t launch(const DevView& v, unsigned blocks, cudaStream_t s, uint64_t seed, uint64_t off,
+                   uint64_t shots, uint64_t* meas, uint64_t* det, uint64_t* obs, uint8_t* acc) {
+  switch (v.W) {
+    case 1: k_sample<1><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
+    case 2: k_sample<2><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
+    case 4: k_sample<4><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
+    case 8: k_sample<8><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
+    case 16: k_sample<16><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
+    case 32: k_sample<32><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
 
+void prepare_device_tables(Program& p) {
+  auto* t = new DeviceTables();
+  try {
+    pack(p, *t);
+  } catch (const PackError& e) {
+    t->status = e.st;
+    t->message = e.msg;
+    t->blob.clear();
+  }
+  delete p.devtab;
+  p.devtab = t;
+}
+
 void device_sample(const Program& p, const SampleArgs& a, void* stream) {
   if (p.mode == TSIM_MODE_DETECTORS && a.meas) fail(TSIM_ERR_ARG, "measurement records requested from a detector-mode program");
+  tables_of(p);  // report a program that cannot run on the device before any CUDA call
   if (a.shots == 0) return;
+  const uint64_t blocks = (a.shots + kThreads - 1) / kThreads;
+  if (blocks > 0x7FFFFFFFull) fail(TSIM_ERR_ARG, "too many shots for one launch");
   const DevView& v = ensure_uploaded(p);
-  cudaStream_t s = (cudaStream_t)stream;
-  switch (v.W) {
-    case 1: launch_w<1>(v, a, s); break;
-    case 2: launch_w<2>(v, a, s); break;
-    case 4: launch_w<4>(v, a, s); break;
-    case 8: launch_w<8>(v, a, s); break;
-    case 16: launch_w<16>(v, a, s); break;
-    case 32: launch_w<32>(v, a, s); break;
-    default: fail(TSIM_ERR_INTERNAL, "unsupported word count");
-  }
-  TSIM_CUDA(cudaGetLastError());
+  cudaError_t e = launch(v, (unsigned)blocks, (cudaStream_t)stream, a.seed, a.shot_offset, a.shots, a.meas, a.det,
+                         a.obs, a.accept);
+  if (e != cudaSuccess) fail(TSIM_ERR_CUDA, std::string("sampling kernel launch: ") + cudaGetErrorString(e));
 }
 
 void device_sample_batch(const Program* const* progs, int n, const SampleArgs* args, void* stream) {
@@ -698,8 +930,6 @@ constexpr int kNoAllocMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// host staging of the packed tables (filled under the mutex, then copied)
-alignas(256) unsigned char g_noalloc_host[kNoAllocBytes];
 std::mutex g_noalloc_mutex;
 // device address of g_noalloc_scratch, per device, from cudaGetSymbolAddress
 void* g_noalloc_dev[kNoAllocMaxDevices];
@@ -720,6 +950,13 @@ extern "C" tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t sh
   const Program& p = *prog->p;
   if (p.mode == TSIM_MODE_DETECTORS && d_meas)
     return noalloc_error(TSIM_ERR_ARG, "measurement records requested from a detector-mode program");
+  if (!p.devtab) return noalloc_error(TSIM_ERR_INTERNAL, "program has no device tables");
+  // the packed tables were built on the host when the program was compiled
+  // or loaded; this call only copies them
+  const DeviceTables& T = *p.devtab;
+  if (T.status != TSIM_OK) return noalloc_error(T.status, "program tables cannot run on the device");
+  if (T.layout.total > kNoAllocBytes)
+    return noalloc_error(TSIM_ERR_ARG, "program tables exceed the 4 MiB maximum of tsim_sample_noalloc");
   if (shots == 0) return TSIM_OK;
   const uint64_t blocks = (shots + kThreads - 1) / kThreads;
   if (blocks > 0x7FFFFFFFull) return noalloc_error(TSIM_ERR_ARG, "too many shots for one launch");
@@ -735,29 +972,13 @@ extern "C" tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t sh
       return noalloc_error(TSIM_ERR_CUDA, "cudaGetSymbolAddress of the no-alloc scratch array failed");
     g_noalloc_dev[dev] = ptr;
   }
-  FixedSink sink{g_noalloc_host, kNoAllocBytes};
-  Layout L;
-  const char* msg = "";
-  tsim_status st = pack_tables(p, sink, L, &msg);
-  if (st != TSIM_OK) return noalloc_error(st, msg);
-  if (sink.overflow)
-    return noalloc_error(TSIM_ERR_ARG, "program tables exceed the 4 MiB maximum of tsim_sample_noalloc");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // every byte the kernel reads is rewritten here, so nothing stale from the
   // previous call survives
-  if (cudaMemcpyAsync(g_noalloc_dev[dev], g_noalloc_host, L.total, cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (cudaMemcpyAsync(g_noalloc_dev[dev], T.blob.data(), T.layout.total, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return noalloc_error(TSIM_ERR_CUDA, "cudaMemcpyAsync into the no-alloc scratch array failed");
-  const DevView v = make_view((const unsigned char*)g_noalloc_dev[dev], L, p);
-  const unsigned nb = (unsigned)blocks;
-  switch (v.W) {
-    case 1: k_sample<1><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
-    case 2: k_sample<2><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
-    case 4: k_sample<4><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
-    case 8: k_sample<8><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
-    case 16: k_sample<16><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
-    case 32: k_sample<32><<<nb, kThreads, 0, s>>>(v, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept); break;
-    default: return noalloc_error(TSIM_ERR_INTERNAL, "unsupported word count");
-  }
-  if (cudaGetLastError() != cudaSuccess) return noalloc_error(TSIM_ERR_CUDA, "launch of the sampling kernel failed");
+  const DevView v = make_view((const unsigned char*)g_noalloc_dev[dev], T.layout, p);
+  if (launch(v, (unsigned)blocks, s, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept) != cudaSuccess)
+    return noalloc_error(TSIM_ERR_CUDA, "launch of the sampling kernel failed");
   return TSIM_OK;
 }

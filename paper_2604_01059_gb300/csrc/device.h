@@ -1,6 +1,8 @@
-// Device-side program cache and sampling entry points (device.cu).
+// Device-side program layout, cache and sampling entry points (device.cu).
 #pragma once
 #include <cstdint>
+#include <string>
+#include <vector>
 
 #include "program.h"
 
@@ -14,6 +16,29 @@ struct SampleArgs {
   uint8_t* accept = nullptr;
 };
 
+// Byte offsets of the sections of the packed device tables (256-byte aligned)
+struct DeviceLayout {
+  size_t o_ch = 0, o_thr = 0, o_sig = 0, o_out = 0, o_om = 0, o_cn = 0, o_tab = 0, o_par = 0,
+         o_cls = 0, o_fidx = 0, o_finc = 0, o_fco = 0, o_dmo = 0, o_dmi = 0, o_omo = 0, o_omi = 0, total = 0;
+  int W = 1;
+  // statistics of the packed tables
+  uint64_t classes = 0;     // stabilizer terms after merging terms with equal factor lists
+  uint64_t class_factors = 0;
+  uint64_t parities = 0;    // distinct factor parities over all tables
+  std::vector<uint64_t> table_classes, table_class_factors, table_parities;  // per table
+};
+
+// Host-side packed tables of one program, built once when the program is
+// compiled or loaded.  status != TSIM_OK when the program cannot run on the
+// device (message says why); sampling then fails with that status.
+struct DeviceTables {
+  std::vector<unsigned char> blob;
+  DeviceLayout layout;
+  tsim_status status = TSIM_OK;
+  std::string message;
+};
+
+void prepare_device_tables(Program& p);
 void device_sample(const Program& p, const SampleArgs& a, void* stream);
 void device_sample_batch(const Program* const* progs, int n, const SampleArgs* args, void* stream);
 void device_sync(void* stream);

@@ -48,7 +48,8 @@ struct RawInfo {
   std::vector<std::vector<uint64_t>> cols;   // per bit: its column of T in the X layout
 };
 
-struct DeviceProgram;  // opaque device-side cache
+struct DeviceProgram;  // opaque device-side cache (uploaded tables)
+struct DeviceTables;   // host-side packed device tables
 
 struct Program {
   int mode = 0;
@@ -61,6 +62,7 @@ struct Program {
   std::vector<std::vector<int>> detmap, obsmap;  // measurement mode only
   std::vector<RawInfo> raw;
   DeviceProgram* dev = nullptr;
+  DeviceTables* devtab = nullptr;
   ~Program();
 };
 

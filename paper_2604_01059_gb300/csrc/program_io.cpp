@@ -26,6 +26,7 @@
 #include <memory>
 #include <sstream>
 
+#include "device.h"
 #include "program.h"
 
 namespace tsim {
@@ -266,6 +267,7 @@ Program* load_program(const std::string& path) {
     fail(TSIM_ERR_PARSE, "output count mismatch");
   if (p->mode == TSIM_MODE_MEASUREMENTS && (int)p->outputs.size() != p->nmeas)
     fail(TSIM_ERR_PARSE, "output count mismatch");
+  prepare_device_tables(*p);
   return p.release();
 }
 

@@ -152,6 +152,99 @@ def t_rotation_sequence(n_t, seed=0):
 
 
 # --------------------------------------------------------------------------
+# d=3 triangular colour code (Steane code) T-check
+# --------------------------------------------------------------------------
+STEANE_FACES = ([0, 1, 2, 3], [1, 2, 4, 5], [2, 3, 5, 6])
+STEANE_LOGICAL = [0, 1, 4]  # X_L = X0 X1 X4, Z_L = Z0 Z1 Z4
+
+
+def color_code_t_check(rounds=3, p=1e-3, check=True, inject="T_DAG"):
+    """d=3 triangular colour code with a T state and transversal T-checks.
+
+    Qubits: data 0-6, syndrome ancillas 7-9 (X plaquettes) and 10-12
+    (Z plaquettes), flags 13-18 (one per syndrome ancilla): 19 qubits.
+    Encoding: the T state T|+> on data 0 is copied onto the logical-X support
+    {0, 1, 4} and the three X plaquette operators are superposed from pivots
+    3, 5, 6 (unitary Steane encoder).  Each round: a T-check (T_DAG on all
+    data, X-parity of all data measured through ancilla 7 prepared in |+>,
+    T on all data: 14 T/T_DAG), then one flagged measurement of the six
+    plaquette stabilizers.  DEPOLARIZE1(p) after single-qubit gates,
+    DEPOLARIZE2(p) after CX, X_ERROR(p) before measurements.  Detectors:
+    check outcomes, flags, first-round stabilizers and round-to-round
+    changes; the final data measurement in X gives the X-plaquette detectors
+    and observable X_L.  With check=False the T-checks are left out.
+    """
+    data = list(range(7))
+    xa, za = [7, 8, 9], [10, 11, 12]
+    fl = list(range(13, 19))
+    L = [f"R {' '.join(map(str, range(19)))}", "H 0", f"{inject} 0", f"DEPOLARIZE1({p}) 0"]
+    # unitary encoder
+    L.append("H 3 5 6")
+    L.append(f"DEPOLARIZE1({p}) 3 5 6")
+    for c, ts in ((0, [1, 4]), (3, [0, 1, 2]), (5, [1, 2, 4]), (6, [2, 3, 5])):
+        for t in ts:
+            L.append(f"CX {c} {t}")
+            L.append(f"DEPOLARIZE2({p}) {c} {t}")
+    nmeas = 0
+    stab_rec = {}  # stabilizer key -> measurement index of its last value
+    for r in range(rounds):
+        if check:
+            L.append("T_DAG " + " ".join(map(str, data)))
+            L.append(f"DEPOLARIZE1({p}) " + " ".join(map(str, data)))
+            L.append("RX 7")
+            for d in data:
+                L.append(f"CX 7 {d}")
+                L.append(f"DEPOLARIZE2({p}) 7 {d}")
+            L.append(f"Z_ERROR({p}) 7")
+            L.append("MX 7")
+            nmeas += 1
+            L.append("DETECTOR rec[-1]")
+            L.append("T " + " ".join(map(str, data)))
+            L.append(f"DEPOLARIZE1({p}) " + " ".join(map(str, data)))
+        # flagged stabilizer round
+        L.append("R " + " ".join(map(str, za + fl[:3])))
+        L.append("RX " + " ".join(map(str, xa + fl[3:])))
+        for k, face in enumerate(STEANE_FACES):
+            a, f = xa[k], fl[k]          # X plaquette: ancilla |+>, CX anc -> data, flag |0>
+            b, g = za[k], fl[3 + k]      # Z plaquette: ancilla |0>, CX data -> anc, flag |+>
+            seq = [(a, face[0]), (a, f), (a, face[1]), (a, face[2]), (a, f), (a, face[3])]
+            seq += [(face[0], b), (g, b), (face[1], b), (face[2], b), (g, b), (face[3], b)]
+            for c, t in seq:
+                L.append(f"CX {c} {t}")
+                L.append(f"DEPOLARIZE2({p}) {c} {t}")
+        L.append(f"Z_ERROR({p}) " + " ".join(map(str, xa + fl[3:])))
+        L.append(f"X_ERROR({p}) " + " ".join(map(str, za + fl[:3])))
+        order = xa + za + fl
+        L.append("MX " + " ".join(map(str, xa)))
+        L.append("M " + " ".join(map(str, za)))
+        L.append("M " + " ".join(map(str, fl[:3])))
+        L.append("MX " + " ".join(map(str, fl[3:])))
+        base = nmeas
+        nmeas += 12
+        idx = {q: base + i for i, q in enumerate(order)}
+        for q in fl:
+            L.append(f"DETECTOR rec[{idx[q] - nmeas}]")
+        for k in range(3):
+            for kind, anc in (("X", xa[k]), ("Z", za[k])):
+                key = (kind, k)
+                cur = f"rec[{idx[anc] - nmeas}]"
+                if key in stab_rec:
+                    L.append(f"DETECTOR {cur} rec[{stab_rec[key] - nmeas}]")
+                else:
+                    L.append(f"DETECTOR {cur}")
+                stab_rec[key] = idx[anc]
+    L.append(f"Z_ERROR({p}) " + " ".join(map(str, data)))
+    L.append("MX " + " ".join(map(str, data)))
+    nmeas += 7
+    for k, face in enumerate(STEANE_FACES):
+        recs = [f"rec[{nmeas - 7 + q - nmeas}]" for q in face]
+        recs.append(f"rec[{stab_rec[('X', k)] - nmeas}]")
+        L.append("DETECTOR " + " ".join(recs))
+    L.append("OBSERVABLE_INCLUDE(0) " + " ".join(f"rec[{nmeas - 7 + q - nmeas}]" for q in STEANE_LOGICAL))
+    return "\n".join(L) + "\n"
+
+
+# --------------------------------------------------------------------------
 # named configurations
 # --------------------------------------------------------------------------
 def config1_circuit(p=1e-3):
@@ -163,6 +256,11 @@ def config2_circuit(p=1e-3, n_t=16, seed=0):
     """d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG gates in the
     rotation that prepares the injected state."""
     return surface_code_t_injection(d=5, rounds=5, p=p, rotation=t_rotation_sequence(n_t, seed))
+
+
+def config3_circuit(p=1e-3):
+    """d=3 triangular colour-code T-check, 19 qubits, 3 check rounds, 42 T/T_DAG."""
+    return color_code_t_check(rounds=3, p=p)
 
 
 def count_t(text):

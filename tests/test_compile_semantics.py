@@ -143,6 +143,37 @@ OBSERVABLE_INCLUDE(0) rec[-1]
 """
 
 
+# one transversal T-check on the Steane code: unitary encoder of T_DAG|+>,
+# T_DAG on all data, X parity through an ancilla, T on all data, final X
+# readout; noise on the injection qubit and on the check ancilla
+STEANE_CHECK = """
+H 0
+T_DAG 0
+DEPOLARIZE1(0.02) 0
+H 3 5 6
+CX 0 1 0 4 3 0 3 1 3 2 5 1 5 2 5 4 6 2 6 3 6 5
+T_DAG 0 1 2 3 4 5 6
+RX 7
+CX 7 0 7 1 7 2 7 3 7 4 7 5 7 6
+Z_ERROR(0.01) 7
+MX 7
+DETECTOR rec[-1]
+T 0 1 2 3 4 5 6
+X_ERROR(0.01) 2
+MX 0 1 2 3 4 5 6
+DETECTOR rec[-7] rec[-6] rec[-5] rec[-4]
+DETECTOR rec[-6] rec[-5] rec[-3] rec[-2]
+DETECTOR rec[-5] rec[-4] rec[-2] rec[-1]
+OBSERVABLE_INCLUDE(0) rec[-7] rec[-6] rec[-3]
+"""
+
+
+def test_steane_t_check(tmp_path):
+    # the colour-code T-check: the check and the plaquettes are deterministic
+    # without noise; the observable carries the magic state
+    check_program(STEANE_CHECK, T.MODE_DETECTORS, tmp_path, max_e=32)
+
+
 def test_t_interference(tmp_path):
     info = check_program(T_INTERFERENCE, T.MODE_MEASUREMENTS, tmp_path)
     assert info["num_random"] == 1

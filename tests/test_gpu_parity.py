@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 import paper_2604_01059_gb300 as T
 from paper_2604_01059_gb300 import workloads as Wk
 from oracle.evaluator import OracleProgram
-from tests.test_compile_semantics import REPETITION, WORKED_EXAMPLE, _random_circuit
+from tests.test_compile_semantics import REPETITION, STEANE_CHECK, WORKED_EXAMPLE, _random_circuit
 
 pytestmark = pytest.mark.gpu
 
@@ -46,6 +46,7 @@ CASES = [
     ("repetition", REPETITION, T.MODE_DETECTORS),
     ("cfg1", Wk.config1_circuit(), T.MODE_DETECTORS),
     ("cfg1_meas", Wk.config1_circuit(p=2e-3), T.MODE_MEASUREMENTS),
+    ("steane_check", STEANE_CHECK, T.MODE_DETECTORS),
 ]
 
 
@@ -82,6 +83,26 @@ def test_config2_full_size_sampled_shots(tmp_path, p):
     orc = OracleProgram(path)
     rng = random.Random(int(p * 1e7))
     idx = sorted(set([0, shots - 1] + [rng.randrange(shots) for _ in range(254)]))
+    for s in idx:
+        o = orc.sample(seed, s, 1)
+        np.testing.assert_array_equal(g["det"][s], o["det"][0])
+        np.testing.assert_array_equal(g["obs"][s], o["obs"][0])
+        assert g["accept"][s] == o["accept"][0]
+
+
+def test_config3_color_code_t_check(tmp_path):
+    # 19 qubits, 42 T/T_DAG, 3 check rounds (16383 stabilizer terms; the
+    # oracle needs ~0.3 s per shot): a ragged two-block launch checked shot
+    # by shot, then 32 shots sampled from a 10^6-shot launch
+    prog = T.Program(Wk.config3_circuit())
+    path = str(tmp_path / "c3.prog")
+    prog.save(path)
+    _compare(prog, path, 129, seed=9, offset=123456)
+    shots, seed = 1_000_000, 0
+    g = _gpu(prog, shots, seed, 0)
+    orc = OracleProgram(path)
+    rng = random.Random(33)
+    idx = sorted(set([0, shots - 1] + [rng.randrange(shots) for _ in range(30)]))
     for s in idx:
         o = orc.sample(seed, s, 1)
         np.testing.assert_array_equal(g["det"][s], o["det"][0])
