@@ -33,7 +33,12 @@ METRIC = "shots/sec and Z[w] term-evals/sec, learned+batched vs plain GPU form, 
 WORKLOADS = {
     "cfg2": "d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG, p in {5e-4,1e-3,2e-3}, 1e6 shots per p",
     "cfg3": "d=3 triangular colour-code T-check, 19 qubits, 42 T/T_DAG, 3 check rounds, p=1e-3, postselected, 1e5 shots",
+    "cfg4": "batched launch: 256 seeded random noisy Clifford+T mirror circuits (20-60 qubits, depth 20-100, "
+            "8-40 T/T_DAG, 2-qubit density 0.3, p in U[1e-4,3e-3]), shots log-uniform in [1e3,1e6], "
+            "one persistent launch replayed from a CUDA graph, autotuned shot block",
 }
+CFG4_TABLE_BUDGET = 2048     # terms per marginal table
+CFG4_PROGRAM_BUDGET = 8192   # terms per program
 WORKLOAD = WORKLOADS["cfg2"]
 
 
@@ -65,14 +70,54 @@ def dist_env():
 
 
 WORKLOAD_NAME = "cfg2"
+SHOTS_LIST = None
+
+
+def config4_programs(n=256):
+    """Compile the batched workload in parallel host threads; circuits over the
+    term budgets are skipped and the next seeds drawn (deterministic order)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import paper_2604_01059_gb300 as T
+    from paper_2604_01059_gb300 import workloads as Wk
+    pool = Wk.config4_batch(n=4 * n, seed=0)
+
+    def build(item):
+        txt, shots = item
+        try:
+            p = T.Program(txt, chi_budget=CFG4_TABLE_BUDGET)
+        except T.TsimError as e:
+            if e.code == 3:
+                return None
+            raise
+        return (p, shots) if p.info["total_terms"] <= CFG4_PROGRAM_BUDGET else None
+
+    out = []
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        for k in range(0, len(pool), 64):
+            for r in ex.map(build, pool[k:k + 64]):
+                if r is not None and len(out) < n:
+                    out.append(r)
+            if len(out) >= n:
+                break
+    return out
 
 
 def programs():
     import paper_2604_01059_gb300 as T
     from paper_2604_01059_gb300 import workloads as Wk
+    global SHOTS_LIST
     if WORKLOAD_NAME == "cfg3":
         return [T.Program(Wk.config3_circuit(p=1e-3))]
+    if WORKLOAD_NAME == "cfg4":
+        pr = config4_programs()
+        SHOTS_LIST = [s for _, s in pr]
+        return [p for p, _ in pr]
     return [T.Program(Wk.config2_circuit(p=p)) for p in P_VALUES]
+
+
+def shots_of(k):
+    return SHOTS_LIST[k] if SHOTS_LIST else SHOTS_PER_P
 
 
 def term_evals_per_shot(prog):
@@ -140,8 +185,9 @@ def int_peak_ops(sm_mhz=None):
     return 152 * 4 * 16 * clk * 1e6
 
 
-def oracle_baseline(seconds, impl_line=False):
-    """Time the oracle's C evaluator on a bounded sample of the same workload."""
+def oracle_baseline(seconds, progs=None):
+    """Time the oracle's C evaluator on a bounded sample of the same workload
+    (at most 16 of its programs)."""
     import tempfile
     from concurrent.futures import ThreadPoolExecutor
 
@@ -149,7 +195,7 @@ def oracle_baseline(seconds, impl_line=False):
 
     evaluator.build()
     cores = os.cpu_count() or 1
-    progs = programs()
+    progs = (progs if progs is not None else programs())[:16]
     paths = []
     tmp = tempfile.mkdtemp()
     for k, p in enumerate(progs):
@@ -181,22 +227,26 @@ def oracle_baseline(seconds, impl_line=False):
 
 
 def run_reference(args):
+    """The reference arm: the oracle (plain C, exact) on the host cores, on the
+    same programs, each step a bounded sample of the workload."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    base = oracle_baseline(args.cpu_seconds)
-    times = []
+    progs = programs()
+    per_step = max(0.5, args.cpu_seconds / max(args.steps, 1))
     for _ in range(args.warmup):
-        pass
+        oracle_baseline(0.05, progs)
+    vals = []
+    b = None
     for _ in range(args.steps):
-        b = oracle_baseline(max(1.0, args.cpu_seconds / max(args.steps, 1)))
-        times.append(b["value"])
-    val = statistics.median(times) if times else base["value"]
+        b = oracle_baseline(per_step, progs)
+        vals.append(b["value"])
+    val = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "shots/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"kind": "oracle", "cores": base["cores"], "sample": base["sample"], "value": val},
+            "cpu_baseline": {"kind": "oracle", "cores": b["cores"], "sample": b["sample"], "value": val},
             "e2e": {"value": val, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -214,23 +264,33 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     progs = programs()
+    n = len(progs)
+    shots = [shots_of(k) for k in range(n)]
+    offsets = [rank * shots[k] for k in range(n)]  # weak scaling: every rank its own shot range
+    seeds = [SEED] * n
     stream = torch.cuda.current_stream()
-    info = progs[0].info
-    dw, ow = max(info["det_words"], 1), max(info["obs_words"], 1)
     outs = []
-    for _ in progs:
-        outs.append((torch.empty((SHOTS_PER_P, dw), dtype=torch.int64, device="cuda"),
-                     torch.empty((SHOTS_PER_P, ow), dtype=torch.int64, device="cuda"),
-                     torch.empty((SHOTS_PER_P,), dtype=torch.uint8, device="cuda")))
+    for p, ns in zip(progs, shots):
+        i = p.info
+        outs.append((torch.empty((ns, max(i["det_words"], 1)), dtype=torch.int64, device="cuda"),
+                     torch.empty((ns, max(i["obs_words"], 1)), dtype=torch.int64, device="cuda"),
+                     torch.empty((ns,), dtype=torch.uint8, device="cuda")))
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    offset = rank * SHOTS_PER_P
 
-    def step():
-        for p, (d, o, a) in zip(progs, outs):
-            T.tsim_sample(p.h, SHOTS_PER_P, SEED, offset, None, d, o, a, stream)
+    def plain_step():
+        for k, (p, (d, o, a)) in enumerate(zip(progs, outs)):
+            T.tsim_sample(p.h, shots[k], seeds[k], offsets[k], None, d, o, a, stream)
+
+    batch = T.tsim_batch_create([p.h for p in progs], shots, seeds, offsets, None,
+                                [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs], autotune=True)
+    binfo = T.tsim_batch_info(batch)
+
+    def batch_step():
+        T.tsim_batch_launch(batch, stream)
 
     for _ in range(max(args.warmup, 3)):
-        step()
+        plain_step()
+        batch_step()
     T.tsim_sync(stream)
 
     def barrier():
@@ -239,77 +299,91 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def timed(step_fn, steps):
+        total = 0.0
+        for _ in range(steps):
+            flush.fill_(1)  # evict L2 between timed iterations
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step_fn()
+            e1.record(stream)
+            barrier()
+            total += e0.elapsed_time(e1)
+        T.tsim_sync(stream)
+        if dist is not None:
+            t = torch.tensor([total], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total
+
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     ids = [v.strip() for v in vis.split(",") if v.strip()]
-    smi_id = ids[local] if local < len(ids) else str(local)
-    clocks = ClockSampler(smi_id)
+    clocks = ClockSampler(ids[local] if local < len(ids) else str(local))
     clocks.start()
-    step_ms = []
-    per_launch = []
-    for _ in range(args.steps):
-        flush.fill_(1)  # evict L2 between timed iterations
-        barrier()
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(progs) + 1)]
-        evs[0].record(stream)
-        for k, (p, (d, o, a)) in enumerate(zip(progs, outs)):
-            T.tsim_sample(p.h, SHOTS_PER_P, SEED, offset, None, d, o, a, stream)
-            evs[k + 1].record(stream)
-        barrier()
-        step_ms.append(evs[0].elapsed_time(evs[-1]))
-        per_launch.append([evs[k].elapsed_time(evs[k + 1]) for k in range(len(progs))])
-    T.tsim_sync(stream)
+    batch_ms = timed(batch_step, args.steps)
+    plain_ms = timed(plain_step, args.steps)
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    shots_all = SHOTS_PER_P * len(progs) * args.steps * world
-    value = shots_all / (total_ms / 1e3)
-    tev = sum(term_evals_per_shot(p) for p in progs) * SHOTS_PER_P * args.steps * world / (total_ms / 1e3)
+    T.tsim_batch_free(batch)
+    shots_step = sum(shots) * world
+    value = shots_step * args.steps / (batch_ms / 1e3)
+    plain = shots_step * args.steps / (plain_ms / 1e3)
+    terms_step = sum(term_evals_per_shot(p) * ns for p, ns in zip(progs, shots)) * world
+    tev = terms_step * args.steps / (batch_ms / 1e3)
 
     # end to end through the host-buffer entry point: copies inside the timed region
-    hd = [np.zeros((SHOTS_PER_P, dw), dtype=np.uint64) for _ in progs]
-    ho = [np.zeros((SHOTS_PER_P, ow), dtype=np.uint64) for _ in progs]
-    ha = [np.zeros(SHOTS_PER_P, dtype=np.uint8) for _ in progs]
-    for k, p in enumerate(progs):
-        T.tsim_sample_host(p.h, SHOTS_PER_P, SEED, offset, None, hd[k], ho[k], ha[k], stream)
+    hbuf = []
+    for p, ns in zip(progs, shots):
+        i = p.info
+        hbuf.append((np.zeros((ns, max(i["det_words"], 1)), dtype=np.uint64),
+                     np.zeros((ns, max(i["obs_words"], 1)), dtype=np.uint64), np.zeros(ns, dtype=np.uint8)))
+
+    def e2e_step():
+        for k, p in enumerate(progs):
+            i = p.info
+            d, o, a = hbuf[k]
+            T.tsim_sample_host(p.h, shots[k], seeds[k], offsets[k], None, d if i["det_words"] else None,
+                               o if i["obs_words"] else None, a, stream)
+
+    e2e_step()
     e2e_steps = max(1, min(args.steps, 3))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for k, p in enumerate(progs):
-            T.tsim_sample_host(p.h, SHOTS_PER_P, SEED, offset, None, hd[k], ho[k], ha[k], stream)
+        e2e_step()
     barrier()
     e2e_s = time.perf_counter() - t0
     if dist is not None:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = SHOTS_PER_P * len(progs) * e2e_steps * world / e2e_s
-    d2h = SHOTS_PER_P * len(progs) * (dw * 8 + ow * 8 + 1)
+    e2e = shots_step * e2e_steps / e2e_s
+    d2h = sum(ns * (p.info["det_words"] * 8 + p.info["obs_words"] * 8 + 1) for p, ns in zip(progs, shots))
 
-    # roofline of the dominant kernel (the fused sampling kernel)
-    avg_launch_ms = statistics.mean(x for row in per_launch for x in row)
-    ops = sum(kernel_int_ops(p) for p in progs) / len(progs) * SHOTS_PER_P
+    # roofline of the dominant kernel: the persistent batched sampling kernel
+    ops = sum(kernel_int_ops(p) * ns for p, ns in zip(progs, shots))
     peak = int_peak_ops()
-    roof = {"bound": "alu", "achieved": ops / (avg_launch_ms / 1e3) / 1e12, "peak": peak / 1e12,
-            "unit": "Tops/s", "frac": ops / (avg_launch_ms / 1e3) / peak, "traffic": None,
-            "kernel": "k_sample", "ops_per_shot": ops / SHOTS_PER_P,
-            "peak_source": "derived: 152 SMs x 64 INT32 lanes x 2070 MHz",
+    achieved = ops / (batch_ms / args.steps / 1e3)
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": None, "kernel": "k_batch (persistent, graph replay)",
+            "ops_per_shot": ops / sum(shots),
+            "peak_source": "derived: 152 SMs x 4 sub-partitions x 16 INT32 lanes x 2070 MHz",
             "measured_issue_tops": int_peaks_measured()}
-    base = oracle_baseline(args.cpu_seconds) if (rank == 0 and world == 1) else None
+    base = oracle_baseline(args.cpu_seconds, progs) if (rank == 0 and world == 1 and args.cpu_seconds > 0) else None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "warmup": args.warmup, "ms_per_step": batch_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (256 MiB write)",
-                           "shots_per_step": SHOTS_PER_P * len(progs) * world,
-                           "terms_per_shot": [term_evals_per_shot(p) for p in progs],
-                           "channels": [p.info["num_channels"] for p in progs]},
+                           "programs": n, "shots_per_step": shots_step,
+                           "terms_per_shot": [term_evals_per_shot(p) for p in progs][:8],
+                           "channels": [p.info["num_channels"] for p in progs][:8],
+                           "cut_order": "heuristic", "batch": binfo},
                 "term_evals_per_s": tev,
+                "plain": {"value": plain, "unit": "shots/s", "ms_per_step": plain_ms / args.steps,
+                          "form": "one tsim_sample launch per program"},
                 "e2e": {"value": e2e, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
-                "gpu_launches": len(progs) * args.steps, "roofline": roof, "clocks": clk,
+                "gpu_launches": args.steps, "roofline": roof, "clocks": clk,
                 "cpu_baseline": base}
         print(json.dumps(line))
     if dist is not None:
@@ -347,9 +421,9 @@ def run_profile():
 
     import paper_2604_01059_gb300 as T
     progs = programs()
-    for p in progs:
-        out = p.sample_torch(SHOTS_PER_P, SEED, 0)
-        out = p.sample_torch(SHOTS_PER_P, SEED, 0)
+    for k, p in enumerate(progs):
+        out = p.sample_torch(shots_of(k), SEED, 0)
+        out = p.sample_torch(shots_of(k), SEED, 0)
     T.tsim_sync()
     torch.cuda.synchronize()
     print(json.dumps({"profile": WORKLOAD, "shots": SHOTS_PER_P, "programs": len(progs)}))

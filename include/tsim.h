@@ -140,7 +140,9 @@ tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t 
 
 /* Batched launch: n programs, each with its own shots / seed / offset and its
  * own output pointers (arrays of n device pointers; entries may be NULL), in
- * one persistent-kernel launch over (program, shot-block) work items. */
+ * one persistent-kernel launch over (program, shot-block) work items.  Every
+ * record equals what tsim_sample gives for the same program, seed and shot.
+ * Synchronises cuda_stream before returning (the plan it builds is freed). */
 tsim_status tsim_sample_batch(const tsim_program* const* progs, int n, const uint64_t* shots,
                               const uint64_t* seeds, const uint64_t* shot_offsets,
                               uint64_t* const* d_meas, uint64_t* const* d_det,
@@ -169,6 +171,29 @@ tsim_status tsim_sample_batch(const tsim_program* const* progs, int n, const uin
 tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t shots, uint64_t seed,
                                 uint64_t shot_offset, uint64_t* d_meas, uint64_t* d_det,
                                 uint64_t* d_obs, uint8_t* d_accept, void* cuda_stream);
+
+/* Reusable batched launch (Appendix "Additional benchmarks": batched sampling;
+ * here heterogeneous programs share one persistent kernel).  tsim_batch_create
+ * uploads every program, lays out the (program, shot-block) work items,
+ * optionally autotunes the shot-block size (128, 512, 2048 shots) and the
+ * resident blocks per SM (4, 8, 16) by timing each candidate on the real
+ * batch, and captures "reset the work counter + persistent launch" in a CUDA
+ * graph.  tsim_batch_launch replays that graph on cuda_stream (asynchronous);
+ * the output pointers given at creation are written on every launch.  The
+ * batch owns a small device allocation (descriptors, work counter) freed by
+ * tsim_batch_free, which must not be called while a launch is in flight.
+ * tsim_batch_info: out[0] shots per work item, out[1] blocks per SM,
+ * out[2] work items, out[3] 1 if a graph is captured, out[4] words of X,
+ * out[5] autotuned launch time in microseconds (0 without autotuning). */
+typedef struct tsim_batch tsim_batch;
+tsim_status tsim_batch_create(const tsim_program* const* progs, int n, const uint64_t* shots,
+                              const uint64_t* seeds, const uint64_t* shot_offsets,
+                              uint64_t* const* d_meas, uint64_t* const* d_det,
+                              uint64_t* const* d_obs, uint8_t* const* d_accept, int autotune,
+                              tsim_batch** out);
+tsim_status tsim_batch_launch(tsim_batch* batch, void* cuda_stream);
+tsim_status tsim_batch_info(const tsim_batch* batch, int64_t out[6]);
+void tsim_batch_free(tsim_batch* batch);
 
 /* Wait for cuda_stream and report any device-side error status. */
 tsim_status tsim_sync(void* cuda_stream);

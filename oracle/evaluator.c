@@ -17,7 +17,11 @@
  *      parity of (f, earlier outputs); a random output follows Algorithm 1
  *      (Appendix "Sampling from marginals"): P_prev starts at the chain's
  *      normalisation P, P_1 is the marginal with m_i = 1, the bit is drawn
- *      from Bernoulli(P_1 / P_prev) and P_prev is updated;
+ *      from Bernoulli(P_1 / P_prev) and P_prev is updated.  The diagrams of a
+ *      chain are known up to the scalars that were discarded and that the
+ *      normalisation P restores (Sec. "Observables"); with exact Clifford
+ *      scalars that is a common phase w^j, so every table of the chain is
+ *      multiplied by the w^-j that makes P real and positive;
  *   4. every marginal is P = sum_t c^t prod_k h(alpha_k, beta_k; a_k, b_k)
  *      with a_k = XOR_i u_ki f_i and b_k = XOR_i v_ki f_i (Eqs. parities,
  *      phase_pair, scalar_product), each factor computed from its defining
@@ -452,8 +456,21 @@ int oracle_eval_table(const struct oracle_prog* p, int ti, const uint64_t* X, in
   return 0;
 }
 
+/* the j in 0..7 for which w^-j z is real and positive */
+static int chain_phase(const zw* z, int* rot) {
+  for (int j = 0; j < 8; ++j) {
+    zw r = zw_mul(*z, zw_omega(-j));
+    if (r.c[2] == 0 && add_(r.c[1], r.c[3]) == 0) {
+      rv v;
+      if (zw_to_real(&r, &v)) return -1;
+      if (sign_xy(v.A, v.B) > 0) { *rot = j; return 0; }
+    }
+  }
+  return fail("normalisation has no positive real phase");
+}
+
 static int sample_shot(const struct oracle_prog* p, uint64_t seed, uint64_t shot, uint64_t* X,
-                       uint8_t* bits, rv* pprev) {
+                       uint8_t* bits, rv* pprev, int* rot) {
   int W = p->W;
   memset(X, 0, (size_t)W * 8);
   /* 1-2: error mechanisms and f = T e */
@@ -465,10 +482,12 @@ static int sample_shot(const struct oracle_prog* p, uint64_t seed, uint64_t shot
       if (U < ch->thr[j]) { o = j; break; }
     for (int w = 0; w < W; ++w) X[w] ^= ch->sig[(size_t)o * W + w];
   }
-  /* Algorithm 1: P_prev <- P for every chain */
+  /* Algorithm 1: P_prev <- P for every chain (phase removed) */
   for (int c = 0; c < p->n_chains; ++c) {
     zw z;
     if (eval_table(p, p->chain_norm[c], X, &z)) return -1;
+    if (chain_phase(&z, &rot[c])) return -1;
+    z = zw_mul(z, zw_omega(-rot[c]));
     if (zw_to_real(&z, &pprev[c])) return -1;
   }
   /* 3: outputs in autoregressive order */
@@ -482,7 +501,9 @@ static int sample_shot(const struct oracle_prog* p, uint64_t seed, uint64_t shot
       X[xb >> 6] |= (uint64_t)1 << (xb & 63);
       zw z;
       rv p1;
-      if (eval_table(p, o->table, X, &z) || zw_to_real(&z, &p1)) return -1;
+      if (eval_table(p, o->table, X, &z)) return -1;
+      z = zw_mul(z, zw_omega(-rot[o->chain]));
+      if (zw_to_real(&z, &p1)) return -1;
       rv pp = pprev[o->chain];
       if (sign_xy(pp.A, pp.B) <= 0) return fail("P_prev is not positive");
       uint32_t U = philox_word(seed, shot, 1, (uint32_t)i);
@@ -517,9 +538,10 @@ int oracle_sample(const struct oracle_prog* p, uint64_t seed, uint64_t shot_begi
   uint64_t* X = calloc((size_t)W, 8);
   uint8_t* bits = calloc((size_t)p->n_out + 1, 1);
   rv* pprev = calloc((size_t)p->n_chains + 1, sizeof(rv));
+  int* rot = calloc((size_t)p->n_chains + 1, sizeof(int));
   int rc = 0;
   for (uint64_t s = 0; s < n; ++s) {
-    if (sample_shot(p, seed, shot_begin + s, X, bits, pprev)) { rc = -1; break; }
+    if (sample_shot(p, seed, shot_begin + s, X, bits, pprev, rot)) { rc = -1; break; }
     if (g_ovf) { rc = fail("int128 overflow while sampling"); break; }
     uint8_t dbits[4096];
     int nd = p->ndet;
@@ -562,7 +584,7 @@ int oracle_sample(const struct oracle_prog* p, uint64_t seed, uint64_t shot_begi
       accept[s] = (uint8_t)ok;
     }
   }
-  free(X); free(bits); free(pprev);
+  free(X); free(bits); free(pprev); free(rot);
   return rc;
 }
 

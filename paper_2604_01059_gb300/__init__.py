@@ -15,7 +15,8 @@ from .build import LIB, build as _build
 
 __all__ = [
     "TsimError", "Program", "tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_program_table_stats",
-    "tsim_sample", "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_sync", "tsim_eval_table",
+    "tsim_sample", "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_batch_create",
+    "tsim_batch_launch", "tsim_batch_info", "tsim_batch_free", "tsim_sync", "tsim_eval_table",
     "tsim_raw_to_x", "tsim_program_save", "tsim_program_load", "tsim_program_free",
     "tsim_last_error", "tsim_selftest_rules", "tsim_measure_int_peak", "tsim_program_device_table_stats",
     "load_library",
@@ -79,6 +80,13 @@ def load_library(path: str | None = None):
     L.tsim_sample_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(u64), ctypes.POINTER(u64),
                                     ctypes.POINTER(u64), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                     ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.tsim_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(u64), ctypes.POINTER(u64),
+                                    ctypes.POINTER(u64), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                    ctypes.POINTER(vp), ctypes.POINTER(vp), i32, pp]
+    L.tsim_batch_launch.argtypes = [vp, vp]
+    L.tsim_batch_info.argtypes = [vp, ctypes.POINTER(i64)]
+    L.tsim_batch_free.argtypes = [vp]
+    L.tsim_batch_free.restype = None
     L.tsim_sync.argtypes = [vp]
     L.tsim_eval_table.argtypes = [vp, i32, ctypes.POINTER(u64), ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)]
     L.tsim_raw_to_x.argtypes = [vp, ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(u64)]
@@ -91,7 +99,8 @@ def load_library(path: str | None = None):
     L.tsim_measure_int_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
     L.tsim_program_device_table_stats.argtypes = [vp, i32, ctypes.POINTER(u64)]
     for n in ("tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_program_table_stats", "tsim_sample",
-              "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
+              "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_batch_create",
+              "tsim_batch_launch", "tsim_batch_info", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
               "tsim_program_save", "tsim_program_load", "tsim_selftest_rules", "tsim_measure_int_peak",
               "tsim_program_device_table_stats"):
         getattr(L, n).restype = ctypes.c_int
@@ -172,6 +181,40 @@ def tsim_sample_batch(hs, shots, seeds, shot_offsets=None, meas=None, det=None, 
     _check(load_library().tsim_sample_batch(arr(hs, vp), n, arr(shots, u64), arr(seeds, u64),
                                             arr(shot_offsets or [0] * n, u64), ptrs(meas), ptrs(det),
                                             ptrs(obs), ptrs(accept), s))
+
+
+def _batch_arrays(hs, shots, seeds, shot_offsets, meas, det, obs, accept):
+    n = len(hs)
+    vp, u64 = ctypes.c_void_p, ctypes.c_uint64
+    arr = lambda xs, T: (T * n)(*xs)  # noqa: E731
+    ptrs = lambda ts: None if ts is None else arr([_ptr(t) for t in ts], vp)  # noqa: E731
+    return (arr(hs, vp), n, arr(shots, u64), arr(seeds, u64), arr(shot_offsets or [0] * n, u64),
+            ptrs(meas), ptrs(det), ptrs(obs), ptrs(accept))
+
+
+def tsim_batch_create(hs, shots, seeds, shot_offsets=None, meas=None, det=None, obs=None, accept=None,
+                      autotune=True):
+    """Reusable batched launch (persistent kernel captured in a CUDA graph)."""
+    out = ctypes.c_void_p()
+    _check(load_library().tsim_batch_create(*_batch_arrays(hs, shots, seeds, shot_offsets, meas, det, obs,
+                                                           accept), 1 if autotune else 0, ctypes.byref(out)))
+    return out.value
+
+
+def tsim_batch_launch(b, stream=None):
+    s = stream if isinstance(stream, (int, type(None))) else stream.cuda_stream
+    _check(load_library().tsim_batch_launch(b, s))
+
+
+def tsim_batch_info(b):
+    out = (ctypes.c_int64 * 6)()
+    _check(load_library().tsim_batch_info(b, out))
+    keys = ["shots_per_item", "blocks_per_sm", "work_items", "graph", "x_words", "tuned_us"]
+    return dict(zip(keys, list(out)))
+
+
+def tsim_batch_free(b):
+    load_library().tsim_batch_free(b)
 
 
 def tsim_sync(stream=None):

@@ -183,26 +183,80 @@ tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t 
   });
 }
 
+struct tsim_batch {
+  tsim::BatchPlan* b;
+};
+
+namespace {
+
+std::vector<tsim::SampleArgs> batch_args(int n, const uint64_t* shots, const uint64_t* seeds,
+                                         const uint64_t* shot_offsets, uint64_t* const* d_meas,
+                                         uint64_t* const* d_det, uint64_t* const* d_obs,
+                                         uint8_t* const* d_accept) {
+  if (n < 0 || (n > 0 && (!shots || !seeds))) tsim::fail(TSIM_ERR_ARG, "bad batch arguments");
+  std::vector<tsim::SampleArgs> as((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    as[(size_t)i].shots = shots[i];
+    as[(size_t)i].seed = seeds[i];
+    as[(size_t)i].shot_offset = shot_offsets ? shot_offsets[i] : 0;
+    as[(size_t)i].meas = d_meas ? d_meas[i] : nullptr;
+    as[(size_t)i].det = d_det ? d_det[i] : nullptr;
+    as[(size_t)i].obs = d_obs ? d_obs[i] : nullptr;
+    as[(size_t)i].accept = d_accept ? d_accept[i] : nullptr;
+  }
+  return as;
+}
+
+std::vector<const tsim::Program*> batch_progs(const tsim_program* const* progs, int n) {
+  if (n > 0 && !progs) tsim::fail(TSIM_ERR_ARG, "NULL program array");
+  std::vector<const tsim::Program*> ps((size_t)n);
+  for (int i = 0; i < n; ++i) ps[(size_t)i] = &prog_of(progs[i]);
+  return ps;
+}
+
+}  // namespace
+
 tsim_status tsim_sample_batch(const tsim_program* const* progs, int n, const uint64_t* shots,
                               const uint64_t* seeds, const uint64_t* shot_offsets, uint64_t* const* d_meas,
                               uint64_t* const* d_det, uint64_t* const* d_obs, uint8_t* const* d_accept,
                               void* cuda_stream) {
   return guard([&] {
-    if (n < 0 || (n > 0 && (!progs || !shots || !seeds))) tsim::fail(TSIM_ERR_ARG, "bad batch arguments");
-    std::vector<const tsim::Program*> ps((size_t)n);
-    std::vector<tsim::SampleArgs> as((size_t)n);
-    for (int i = 0; i < n; ++i) {
-      ps[(size_t)i] = &prog_of(progs[i]);
-      as[(size_t)i].shots = shots[i];
-      as[(size_t)i].seed = seeds[i];
-      as[(size_t)i].shot_offset = shot_offsets ? shot_offsets[i] : 0;
-      as[(size_t)i].meas = d_meas ? d_meas[i] : nullptr;
-      as[(size_t)i].det = d_det ? d_det[i] : nullptr;
-      as[(size_t)i].obs = d_obs ? d_obs[i] : nullptr;
-      as[(size_t)i].accept = d_accept ? d_accept[i] : nullptr;
-    }
+    auto as = batch_args(n, shots, seeds, shot_offsets, d_meas, d_det, d_obs, d_accept);
+    auto ps = batch_progs(progs, n);
     tsim::device_sample_batch(ps.data(), n, as.data(), cuda_stream);
   });
+}
+
+tsim_status tsim_batch_create(const tsim_program* const* progs, int n, const uint64_t* shots,
+                              const uint64_t* seeds, const uint64_t* shot_offsets, uint64_t* const* d_meas,
+                              uint64_t* const* d_det, uint64_t* const* d_obs, uint8_t* const* d_accept,
+                              int autotune, tsim_batch** out) {
+  return guard([&] {
+    if (!out) tsim::fail(TSIM_ERR_ARG, "NULL output");
+    auto as = batch_args(n, shots, seeds, shot_offsets, d_meas, d_det, d_obs, d_accept);
+    auto ps = batch_progs(progs, n);
+    *out = new tsim_batch{tsim::batch_create(ps.data(), n, as.data(), autotune)};
+  });
+}
+
+tsim_status tsim_batch_launch(tsim_batch* batch, void* cuda_stream) {
+  return guard([&] {
+    if (!batch || !batch->b) tsim::fail(TSIM_ERR_ARG, "NULL batch");
+    tsim::batch_launch(batch->b, cuda_stream);
+  });
+}
+
+tsim_status tsim_batch_info(const tsim_batch* batch, int64_t out[6]) {
+  return guard([&] {
+    if (!batch || !batch->b || !out) tsim::fail(TSIM_ERR_ARG, "NULL argument");
+    tsim::batch_info(batch->b, out);
+  });
+}
+
+void tsim_batch_free(tsim_batch* batch) {
+  if (!batch) return;
+  tsim::batch_free(batch->b);
+  delete batch;
 }
 
 tsim_status tsim_sync(void* cuda_stream) {

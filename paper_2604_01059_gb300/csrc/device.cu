@@ -182,17 +182,33 @@ __device__ __forceinline__ long long pick(const long long c[4], int k) {
   return k < 4 ? v : -v;
 }
 
+// parity of (mask & X); masks are stored with ws words (ws <= W, the rest of X
+// is zero for such a program)
 template <int W>
-__device__ __forceinline__ int parity_w(const uint64_t* m, const uint64_t (&X)[W]) {
+__device__ __forceinline__ int parity_w(const uint64_t* m, const uint64_t (&X)[W], int ws) {
   uint64_t acc = 0;
 #pragma unroll
-  for (int w = 0; w < W; ++w) acc ^= __ldg(m + w) & X[w];
+  for (int w = 0; w < W; ++w)
+    if (w < ws) acc ^= __ldg(m + w) & X[w];
   return __popcll(acc) & 1;
 }
 
-// real part of (c0 + c1 w + c2 w^2 + c3 w^3) sqrt2^base as (A + B sqrt2) 2^e:
-// Re = (2 c0 + (c1 - c3) sqrt2) / 2
-__device__ __forceinline__ RV to_real(const long long (&c)[4], int base, int* st) {
+// exact table value (c0 + c1 w + c2 w^2 + c3 w^3) sqrt2^base
+struct ZC {
+  long long c[4];
+  int base;
+};
+
+// real part of w^-rot (c0 + c1 w + c2 w^2 + c3 w^3) sqrt2^base as
+// (A + B sqrt2) 2^e:  Re = (2 c0 + (c1 - c3) sqrt2) / 2.  A chain's tables
+// share one parameter-dependent phase w^rot (the discarded scalars that the
+// normalisation P restores, Sec. "Observables"); rotating it away leaves the
+// real marginal.
+__device__ __forceinline__ RV to_real_rot(const ZC& z, int rot, int* st) {
+  long long c[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) c[i] = pick(z.c, i + rot);
+  const int base = z.base;
   if (c[2] != 0 || c[1] + c[3] != 0) *st |= ST_NOT_REAL;
   RV r;
   r.A = (__int128)2 * c[0];
@@ -237,15 +253,16 @@ __device__ __forceinline__ void accumulate(const DClass& C, uint32_t acc, long l
 }
 
 template <int W>
-__device__ RV eval_table(const DevView& V, int t, const uint64_t (&X)[W], int* st) {
+__device__ ZC eval_table(const DevView& V, int t, const uint64_t (&X)[W]) {
   const DTable tb = V.tab[t];
-  long long c[4] = {0, 0, 0, 0};
+  ZC z{{0, 0, 0, 0}, tb.base};
+  long long (&c)[4] = z.c;
   if (tb.basis) {
     // parities in a GF(2) basis of the table's mask span: Y holds the basis
     // parities and every factor parity is <coordinates, Y>
     uint64_t Y = 0;
     for (uint32_t q = 0; q < tb.n_par; ++q)
-      Y |= (uint64_t)parity_w<W>(V.par + (size_t)(tb.par_off + q) * W, X) << q;
+      Y |= (uint64_t)parity_w<W>(V.par + (size_t)(tb.par_off + q) * V.W, X, V.W) << q;
     for (uint32_t q = 0; q < tb.n_cls; ++q) {
       const DClass& C = V.cls[tb.cls_off + q];
       const uint32_t fo = C.fac_off, nf = C.n_fac;
@@ -258,13 +275,13 @@ __device__ RV eval_table(const DevView& V, int t, const uint64_t (&X)[W], int* s
       if (acc >> 21) continue;
       accumulate(C, acc, c);
     }
-    return to_real(c, tb.base, st);
+    return z;
   }
   // distinct factor parities of this table, once per shot, into 256 bits
   // (q is the same for every thread of a warp, so the word choice is uniform)
   uint64_t P0 = 0, P1 = 0, P2 = 0, P3 = 0;
   for (uint32_t q = 1; q < tb.n_par; ++q) {
-    const uint64_t bit = (uint64_t)parity_w<W>(V.par + (size_t)(tb.par_off + q) * W, X) << (q & 63);
+    const uint64_t bit = (uint64_t)parity_w<W>(V.par + (size_t)(tb.par_off + q) * V.W, X, V.W) << (q & 63);
     if (q < 64) P0 |= bit;
     else if (q < 128) P1 |= bit;
     else if (q < 192) P2 |= bit;
@@ -287,7 +304,22 @@ __device__ RV eval_table(const DevView& V, int t, const uint64_t (&X)[W], int* s
     if (acc >> 21) continue;  // some factor vanished
     accumulate(C, acc, c);
   }
-  return to_real(c, tb.base, st);
+  return z;
+}
+
+// the power of w that makes a chain's normalisation real and positive
+__device__ __forceinline__ int chain_rotation(const ZC& z, int* st) {
+  for (int rot = 0; rot < 8; ++rot) {
+    long long c[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[i] = pick(z.c, i + rot);
+    if (c[2] == 0 && c[1] + c[3] == 0) {
+      const __int128 A = (__int128)2 * c[0], B = (__int128)c[1] - c[3];
+      if (sign_xy(A, B, st) > 0) return rot;
+    }
+  }
+  *st |= ST_NOT_REAL;
+  return 0;
 }
 
 template <int W>
@@ -306,14 +338,11 @@ __device__ __forceinline__ int get_xbit(const uint64_t (&X)[W], int b) {
   return (int)((v >> (b & 63)) & 1);
 }
 
+// One shot s of a launch (global shot index shot0 + s), records at row s.
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, uint64_t shot0,
-                                                     uint64_t nshots, uint64_t* __restrict__ meas,
-                                                     uint64_t* __restrict__ det,
-                                                     uint64_t* __restrict__ obs,
-                                                     uint8_t* __restrict__ accept) {
-  const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nshots) return;
+__device__ void sample_one(const DevView& V, uint64_t s, uint64_t seed, uint64_t shot0,
+                           uint64_t* __restrict__ meas, uint64_t* __restrict__ det,
+                           uint64_t* __restrict__ obs, uint8_t* __restrict__ accept) {
   const uint64_t shot = shot0 + s;
   RoundKeys rk;
   {
@@ -347,15 +376,21 @@ __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, u
       uint32_t o = 1;
       while (o + 1 < ch.n_out && U >= __ldg(thr + o)) ++o;
       if (o >= ch.n_out) continue;
-      const uint64_t* sg = V.sig + ch.sig_off + (size_t)o * W;
+      const uint64_t* sg = V.sig + ch.sig_off + (size_t)o * V.W;
 #pragma unroll
-      for (int w = 0; w < W; ++w) X[w] ^= __ldg(sg + w);
+      for (int w = 0; w < W; ++w)
+        if (w < V.W) X[w] ^= __ldg(sg + w);
     }
   }
 
   // 2-3. outputs in autoregressive order (Algorithm 1 per chain)
   RV pp[kMaxChains];
-  for (int c = 0; c < V.n_chains; ++c) pp[c] = eval_table<W>(V, V.chain_norm[c], X, &st);
+  int rot[kMaxChains];
+  for (int c = 0; c < V.n_chains; ++c) {
+    const ZC z = eval_table<W>(V, V.chain_norm[c], X);
+    rot[c] = chain_rotation(z, &st);
+    pp[c] = to_real_rot(z, rot[c], &st);
+  }
   const int dw = (V.ndet + 63) >> 6, mw = (V.nmeas + 63) >> 6, ow = (V.nobs + 63) >> 6;
   uint64_t ob[kMaxOutWords];  // measurement mode only
   uint64_t cur = 0;           // detector mode: current record word
@@ -366,10 +401,10 @@ __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, u
     if (o.kind == OUT_BIT) {
       bit = get_xbit<W>(X, o.a) ^ o.cst;
     } else if (o.kind == OUT_MASK) {
-      bit = parity_w<W>(V.omask + o.a, X) ^ o.cst;
+      bit = parity_w<W>(V.omask + o.a, X, V.W) ^ o.cst;
     } else {
       set_xbit<W>(X, o.a, true);
-      const RV p1 = eval_table<W>(V, o.table, X, &st);
+      const RV p1 = to_real_rot(eval_table<W>(V, o.table, X), rot[o.chain], &st);
       const RV pv = pp[o.chain];
       if (sign_xy(pv.A, pv.B, &st) <= 0) st |= ST_ZERO_PROB;
       uint32_t u[4];
@@ -450,6 +485,56 @@ __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, u
   }
   if (accept) accept[s] = any_det ? 0 : 1;
   if (st) atomicOr(&g_status, st);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, uint64_t shot0,
+                                                     uint64_t nshots, uint64_t* __restrict__ meas,
+                                                     uint64_t* __restrict__ det,
+                                                     uint64_t* __restrict__ obs,
+                                                     uint8_t* __restrict__ accept) {
+  const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nshots) sample_one<W>(V, s, seed, shot0, meas, det, obs, accept);
+}
+
+// ------------------------------------------------------- batched launch
+// One persistent launch over many programs: work item i is a block of `sb`
+// shots of one program; blocks take items from an atomic counter until all
+// are done (no waiting on other blocks).  Program p owns items
+// [item_start[p], item_start[p+1]).
+struct BatchProg {
+  DevView v;
+  uint64_t shots, seed, shot_offset;
+  uint64_t* meas;
+  uint64_t* det;
+  uint64_t* obs;
+  uint8_t* accept;
+};
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_batch(const BatchProg* __restrict__ progs, int n,
+                                                    const uint64_t* __restrict__ item_start,
+                                                    uint64_t total_items, uint32_t sb,
+                                                    unsigned long long* counter) {
+  __shared__ unsigned long long item;
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(counter, 1ull);
+    __syncthreads();
+    const uint64_t it = item;
+    __syncthreads();
+    if (it >= total_items) return;
+    int lo = 0, hi = n - 1;  // last program with item_start <= it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (item_start[mid] <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchProg& P = progs[lo];
+    const uint64_t first = (it - item_start[lo]) * sb;
+    const uint64_t last = min(first + sb, P.shots);
+    for (uint64_t s = first + threadIdx.x; s < last; s += blockDim.x)
+      sample_one<W>(P.v, s, P.seed, P.shot_offset, P.meas, P.det, P.obs, P.accept);
+  }
 }
 
 // ------------------------------------------------------ host-side packing
@@ -893,8 +978,163 @@ void device_sample(const Program& p, const SampleArgs& a, void* stream) {
   if (e != cudaSuccess) fail(TSIM_ERR_CUDA, std::string("sampling kernel launch: ") + cudaGetErrorString(e));
 }
 
+// ----------------------------------------------------------- batch plans
+struct BatchPlan {
+  int device = -1, n = 0, wmax = 1, sms = 1;
+  uint32_t sb = 512;        // shots per work item
+  int blocks_per_sm = 8;
+  uint64_t total_items = 0;
+  std::vector<BatchProg> h_progs;
+  unsigned char* dmem = nullptr;
+  BatchProg* d_progs = nullptr;
+  uint64_t* d_item_start = nullptr;
+  unsigned long long* d_counter = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  float tuned_ms = 0;
+};
+
+namespace {
+
+void plan_items(BatchPlan& b, cudaStream_t s) {
+  std::vector<uint64_t> start((size_t)b.n + 1, 0);
+  for (int i = 0; i < b.n; ++i) start[(size_t)i + 1] = start[(size_t)i] + (b.h_progs[(size_t)i].shots + b.sb - 1) / b.sb;
+  b.total_items = start[(size_t)b.n];
+  TSIM_CUDA(cudaMemcpyAsync(b.d_item_start, start.data(), start.size() * 8, cudaMemcpyHostToDevice, s));
+  TSIM_CUDA(cudaStreamSynchronize(s));
+}
+
+cudaError_t launch_batch(const BatchPlan& b, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (!b.total_items) return cudaSuccess;
+  const uint64_t want = (uint64_t)b.sms * (uint64_t)b.blocks_per_sm;
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, b.total_items));
+  switch (b.wmax) {
+    case 1: k_batch<1><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
+    case 2: k_batch<2><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
+    case 4: k_batch<4><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
+    case 8: k_batch<8><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
+    case 16: k_batch<16><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
+    case 32: k_batch<32><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* args, int autotune) {
+  auto b = std::make_unique<BatchPlan>();
+  b->n = n;
+  TSIM_CUDA(cudaGetDevice(&b->device));
+  TSIM_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device));
+  for (int i = 0; i < n; ++i) {
+    const Program& p = *progs[i];
+    if (p.mode == TSIM_MODE_DETECTORS && args[i].meas)
+      fail(TSIM_ERR_ARG, "measurement records requested from a detector-mode program");
+    tables_of(p);
+    BatchProg bp{};
+    bp.v = ensure_uploaded(p);
+    bp.shots = args[i].shots;
+    bp.seed = args[i].seed;
+    bp.shot_offset = args[i].shot_offset;
+    bp.meas = args[i].meas;
+    bp.det = args[i].det;
+    bp.obs = args[i].obs;
+    bp.accept = args[i].accept;
+    b->wmax = std::max(b->wmax, bp.v.W);
+    b->h_progs.push_back(bp);
+  }
+  const size_t bytes = (size_t)n * sizeof(BatchProg) + ((size_t)n + 1) * 8 + 64;
+  cudaError_t e = cudaMalloc(&b->dmem, bytes);
+  if (e != cudaSuccess) fail(TSIM_ERR_OOM, std::string("cudaMalloc of the batch plan: ") + cudaGetErrorString(e));
+  b->d_progs = (BatchProg*)b->dmem;
+  b->d_item_start = (uint64_t*)(b->dmem + (size_t)n * sizeof(BatchProg));
+  b->d_counter = (unsigned long long*)(b->dmem + (size_t)n * sizeof(BatchProg) + ((size_t)n + 1) * 8);
+  cudaStream_t s = nullptr;
+  TSIM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  struct SD { cudaStream_t s; ~SD() { cudaStreamDestroy(s); } } sd{s};
+  if (n) TSIM_CUDA(cudaMemcpyAsync(b->d_progs, b->h_progs.data(), (size_t)n * sizeof(BatchProg), cudaMemcpyHostToDevice, s));
+  plan_items(*b, s);
+  if (autotune && b->total_items) {
+    // shot-block size x resident blocks per SM: time every candidate twice on
+    // the real batch (records are overwritten with identical values)
+    cudaEvent_t e0, e1;
+    TSIM_CUDA(cudaEventCreate(&e0));
+    TSIM_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    uint32_t best_sb = b->sb;
+    int best_bps = b->blocks_per_sm;
+    for (uint32_t sb : {128u, 512u, 2048u}) {
+      b->sb = sb;
+      plan_items(*b, s);
+      for (int bps : {4, 8, 16}) {
+        b->blocks_per_sm = bps;
+        float t = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          TSIM_CUDA(cudaEventRecord(e0, s));
+          TSIM_CUDA(launch_batch(*b, s));
+          TSIM_CUDA(cudaEventRecord(e1, s));
+          TSIM_CUDA(cudaEventSynchronize(e1));
+          float ms = 0;
+          TSIM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          t = std::min(t, ms);
+        }
+        if (t < best) { best = t; best_sb = sb; best_bps = bps; }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->sb = best_sb;
+    b->blocks_per_sm = best_bps;
+    b->tuned_ms = best;
+    plan_items(*b, s);
+  }
+  // capture counter reset + persistent launch as one graph
+  TSIM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = launch_batch(*b, s);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(s, &g);
+  if (le != cudaSuccess || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    fail(TSIM_ERR_CUDA, std::string("graph capture of the batched launch: ") +
+                            cudaGetErrorString(le != cudaSuccess ? le : ce));
+  }
+  b->graph = g;
+  TSIM_CUDA(cudaGraphInstantiate(&b->exec, g, 0));
+  return b.release();
+}
+
+void batch_launch(BatchPlan* b, void* stream) {
+  int cur = -1;
+  TSIM_CUDA(cudaGetDevice(&cur));
+  if (cur != b->device) fail(TSIM_ERR_ARG, "batch launched on another device than it was created on");
+  TSIM_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+}
+
+void batch_free(BatchPlan* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->dmem) cudaFree(b->dmem);
+  delete b;
+}
+
+void batch_info(const BatchPlan* b, int64_t out[6]) {
+  out[0] = b->sb;
+  out[1] = b->blocks_per_sm;
+  out[2] = (int64_t)b->total_items;
+  out[3] = b->exec ? 1 : 0;
+  out[4] = b->wmax;
+  out[5] = (int64_t)(b->tuned_ms * 1000.0f);
+}
+
 void device_sample_batch(const Program* const* progs, int n, const SampleArgs* args, void* stream) {
-  for (int i = 0; i < n; ++i) device_sample(*progs[i], args[i], stream);
+  BatchPlan* b = batch_create(progs, n, args, 0);
+  struct F { BatchPlan* b; ~F() { batch_free(b); } } f{b};
+  batch_launch(b, stream);
+  TSIM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
 }
 
 void device_sync(void* stream) {

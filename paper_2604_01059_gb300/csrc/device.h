@@ -1,6 +1,7 @@
 // Device-side program layout, cache and sampling entry points (device.cu).
 #pragma once
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -41,6 +42,12 @@ struct DeviceTables {
 void prepare_device_tables(Program& p);
 void device_sample(const Program& p, const SampleArgs& a, void* stream);
 void device_sample_batch(const Program* const* progs, int n, const SampleArgs* args, void* stream);
+
+struct BatchPlan;
+BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* args, int autotune);
+void batch_launch(BatchPlan* b, void* stream);
+void batch_free(BatchPlan* b);
+void batch_info(const BatchPlan* b, int64_t out[6]);
 void device_sync(void* stream);
 void device_release(DeviceProgram* d);
 

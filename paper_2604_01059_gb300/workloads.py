@@ -245,6 +245,68 @@ def color_code_t_check(rounds=3, p=1e-3, check=True, inject="T_DAG"):
 
 
 # --------------------------------------------------------------------------
+# random noisy Clifford+T circuits (batched-launch workload)
+# --------------------------------------------------------------------------
+_INV = {"H": "H", "S": "S_DAG", "S_DAG": "S", "SQRT_X": "SQRT_X_DAG", "SQRT_X_DAG": "SQRT_X",
+        "X": "X", "Z": "Z", "T": "T_DAG", "T_DAG": "T", "CX": "CX", "CZ": "CZ"}
+
+
+def random_clifford_t(seed, n=None, depth=None, t_count=None, p=None):
+    """A seeded random noisy Clifford+T mirror circuit.
+
+    n qubits in U[20, 60], depth in U[20, 100] layers (half a random circuit U,
+    half its inverse U^-1, so the noiseless output is all zeros), t_count
+    T/T_DAG gates in U[8, 40] (half in U at random positions, mirrored in
+    U^-1), a two-qubit gate density of 0.3 per layer (fraction of qubits
+    covered by CX/CZ pairs on random partners), random single-qubit Cliffords
+    on the other qubits, depolarising p in U[1e-4, 3e-3] after every layer
+    and X_ERROR(p) before the final Z measurement of every qubit.  Every
+    measurement is a detector; observable 0 is the parity of qubits 0-2.
+    """
+    rng = random.Random(seed)
+    n = n if n is not None else rng.randint(20, 60)
+    depth = depth if depth is not None else rng.randint(20, 100)
+    t_count = t_count if t_count is not None else rng.randint(8, 40)
+    p = p if p is not None else rng.uniform(1e-4, 3e-3)
+    half = max(1, depth // 2)
+    t_pos = set()
+    while len(t_pos) < min(max(1, t_count // 2), n * half):
+        t_pos.add((rng.randrange(half), rng.randrange(n)))
+    one_q = ["H", "S", "S_DAG", "SQRT_X", "SQRT_X_DAG", "X", "Z"]
+    layers = []
+    for layer in range(half):
+        qs = list(range(n))
+        rng.shuffle(qs)
+        n_pair = int(round(0.3 * n / 2))
+        ops = [(rng.choice(["CX", "CZ"]), (qs[2 * k], qs[2 * k + 1])) for k in range(n_pair)]
+        ops += [(rng.choice(one_q), (q,)) for q in qs[2 * n_pair:]]
+        ops += [(rng.choice(["T", "T_DAG"]), (q,)) for q in range(n) if (layer, q) in t_pos]
+        layers.append(ops)
+
+    def emit(ops, L):
+        pairs = [x for g, t in ops if len(t) == 2 for x in t]
+        singles = sorted({t[0] for g, t in ops if len(t) == 1})
+        for g, t in ops:
+            L.append(f"{g} " + " ".join(map(str, t)))
+        if pairs:
+            L.append(f"DEPOLARIZE2({p:.6g}) " + " ".join(map(str, pairs)))
+        if singles:
+            L.append(f"DEPOLARIZE1({p:.6g}) " + " ".join(map(str, singles)))
+
+    L = ["R " + " ".join(map(str, range(n)))]
+    for ops in layers:
+        emit(ops, L)
+    for ops in reversed(layers):
+        emit([(_INV[g], t) for g, t in reversed(ops)], L)
+    L.append(f"X_ERROR({p:.6g}) " + " ".join(map(str, range(n))))
+    L.append("M " + " ".join(map(str, range(n))))
+    for q in range(n):
+        L.append(f"DETECTOR rec[-{n - q}]")
+    L.append("OBSERVABLE_INCLUDE(0) " + " ".join(f"rec[-{n - q}]" for q in range(min(3, n))))
+    return "\n".join(L) + "\n"
+
+
+# --------------------------------------------------------------------------
 # named configurations
 # --------------------------------------------------------------------------
 def config1_circuit(p=1e-3):
@@ -261,6 +323,20 @@ def config2_circuit(p=1e-3, n_t=16, seed=0):
 def config3_circuit(p=1e-3):
     """d=3 triangular colour-code T-check, 19 qubits, 3 check rounds, 42 T/T_DAG."""
     return color_code_t_check(rounds=3, p=p)
+
+
+def config4_batch(n=256, seed=0):
+    """(circuit, shots) pairs of the batched-launch workload: seeded random
+    mirror circuits (see random_clifford_t) with shot counts drawn
+    log-uniformly from 1e3 to 1e6.  Circuit k uses generator seed
+    seed * 100003 + k; the caller may skip circuits it cannot compile and
+    draw more with larger k."""
+    rng = random.Random(seed)
+    out = []
+    for k in range(n):
+        shots = int(round(10 ** rng.uniform(3, 6)))
+        out.append((random_clifford_t(seed * 100003 + k), shots))
+    return out
 
 
 def count_t(text):

@@ -59,3 +59,16 @@ def test_chi_budget_is_enforced():
     with __import__("pytest").raises(T.TsimError) as e:
         T.tsim_compile(Wk.config2_circuit(), chi_budget=10)
     assert e.value.code == 3
+
+
+def test_config4_generator_is_seeded_and_in_range():
+    from oracle import circuit as oc
+    from paper_2604_01059_gb300 import workloads as Wk
+    a = Wk.config4_batch(n=8, seed=3)
+    b = Wk.config4_batch(n=8, seed=3)
+    assert a == b
+    for txt, shots in a:
+        c = oc.parse(txt)
+        assert 20 <= c.num_qubits <= 60 and 1_000 <= shots <= 1_000_000
+        assert 4 <= Wk.count_t(txt) <= 40
+        assert c.num_detectors == c.num_qubits and c.num_observables == 1

@@ -22,6 +22,8 @@ from oracle.evaluator import OracleProgram
 from oracle.zomega import DOmega, compare_real
 from tests import progfile
 
+W = DOmega.omega_pow
+
 
 def check_program(text, mode, tmp_path, max_e=64, seed=0, decomp=T.DECOMP_HEURISTIC, reduction=True):
     h = T.tsim_compile(text, mode=mode, decomp=decomp, channel_reduction=reduction)
@@ -50,8 +52,13 @@ def check_program(text, mode, tmp_path, max_e=64, seed=0, decomp=T.DECOMP_HEURIS
         dist = statevector.output_distribution(circ, list(e), modename)
         x0 = progfile.x_of_raw(prog, e)
         norms = [oprog.eval_table(t, x0) for t in prog["chains"]]
+        # a chain's tables share one phase w^j (the scalars its normalisation
+        # restores); the normalisation is real and positive after removing it
+        phases = []
         for pn in norms:
-            assert pn.is_real() and pn.sign() > 0
+            js = [j for j in range(8) if (pn * W(-j)).is_real() and (pn * W(-j)).sign() > 0]
+            assert len(js) == 1, pn
+            phases.append(W(-js[0]))
         for o in itertools.product((0, 1), repeat=n_out):
             x = list(x0)
             pprev = list(norms)
@@ -65,8 +72,9 @@ def check_program(text, mode, tmp_path, max_e=64, seed=0, decomp=T.DECOMP_HEURIS
                     _, xb, ch, tb = out
                     x[xb >> 6] |= 1 << (xb & 63)
                     p1 = oprog.eval_table(tb, x)
-                    assert p1.is_real()
-                    assert p1.sign() >= 0 and compare_real(p1, pprev[ch]) <= 0
+                    p1r, prr = p1 * phases[ch], pprev[ch] * phases[ch]
+                    assert p1r.is_real()
+                    assert p1r.sign() >= 0 and compare_real(p1r, prr) <= 0
                     if o[i]:
                         pprev[ch] = p1
                     else:
@@ -166,6 +174,41 @@ DETECTOR rec[-6] rec[-5] rec[-3] rec[-2]
 DETECTOR rec[-5] rec[-4] rec[-2] rec[-1]
 OBSERVABLE_INCLUDE(0) rec[-7] rec[-6] rec[-3]
 """
+
+
+# a chain whose marginals carry a noise-dependent phase w^j in the program
+# (found by delta-debugging a random mirror circuit)
+PHASED_CHAIN = """
+R 0 1 2 3
+H 3
+H 1
+H 2
+H 0
+S 3
+CZ 0 1
+SQRT_X 0
+CZ 3 2
+H 1
+H 3
+DEPOLARIZE1(0.003) 0 1 3
+T_DAG 1
+SQRT_X 0
+S 1
+S_DAG 3
+H 2
+CZ 1 3
+X_ERROR(0.003) 0 1 2 3
+M 0 1 2 3
+DETECTOR rec[-4]
+DETECTOR rec[-3]
+DETECTOR rec[-2]
+DETECTOR rec[-1]
+OBSERVABLE_INCLUDE(0) rec[-4] rec[-3]
+"""
+
+
+def test_chain_with_noise_dependent_phase(tmp_path):
+    check_program(PHASED_CHAIN, T.MODE_DETECTORS, tmp_path, max_e=1024)
 
 
 def test_steane_t_check(tmp_path):

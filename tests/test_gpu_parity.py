@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 import paper_2604_01059_gb300 as T
 from paper_2604_01059_gb300 import workloads as Wk
 from oracle.evaluator import OracleProgram
-from tests.test_compile_semantics import REPETITION, STEANE_CHECK, WORKED_EXAMPLE, _random_circuit
+from tests.test_compile_semantics import PHASED_CHAIN, REPETITION, STEANE_CHECK, WORKED_EXAMPLE, _random_circuit
 
 pytestmark = pytest.mark.gpu
 
@@ -47,6 +47,7 @@ CASES = [
     ("cfg1", Wk.config1_circuit(), T.MODE_DETECTORS),
     ("cfg1_meas", Wk.config1_circuit(p=2e-3), T.MODE_MEASUREMENTS),
     ("steane_check", STEANE_CHECK, T.MODE_DETECTORS),
+    ("phased_chain", PHASED_CHAIN, T.MODE_DETECTORS),
 ]
 
 
