@@ -85,7 +85,7 @@ def config4_programs(n=256):
     def build(item):
         txt, shots = item
         try:
-            p = T.Program(txt, chi_budget=CFG4_TABLE_BUDGET)
+            p = T.Program(txt, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET)
         except T.TsimError as e:
             if e.code == 3:
                 return None

@@ -73,6 +73,9 @@ typedef struct {
                             by the cut-order network, heuristic as fallback. */
   uint64_t chi_budget;   /* maximum stabilizer terms per marginal; 0 = 1<<20 */
   int channel_reduction; /* 1 = apply the four steps of Appendix "Channel reduction" */
+  uint64_t total_budget; /* maximum stabilizer terms summed over all marginals; 0 = none.
+                            Both budgets fail with TSIM_ERR_CHI_BUDGET as soon as they
+                            are exceeded. */
 } tsim_compile_opts;
 
 typedef struct {

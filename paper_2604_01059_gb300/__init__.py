@@ -39,7 +39,7 @@ class TsimError(RuntimeError):
 
 class CompileOpts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int), ("decomp", ctypes.c_int), ("chi_budget", ctypes.c_uint64),
-                ("channel_reduction", ctypes.c_int)]
+                ("channel_reduction", ctypes.c_int), ("total_budget", ctypes.c_uint64)]
 
 
 class ProgramInfo(ctypes.Structure):
@@ -117,11 +117,12 @@ def tsim_last_error() -> str:
     return load_library().tsim_last_error().decode(errors="replace")
 
 
-def tsim_compile(text: str, mode=MODE_DETECTORS, decomp=DECOMP_HEURISTIC, chi_budget=0, channel_reduction=True):
+def tsim_compile(text: str, mode=MODE_DETECTORS, decomp=DECOMP_HEURISTIC, chi_budget=0, channel_reduction=True,
+                 total_budget=0):
     """Compile a Stim-format circuit; returns an opaque program handle (int)."""
     L = load_library()
     b = text.encode()
-    opts = CompileOpts(mode, decomp, chi_budget, 1 if channel_reduction else 0)
+    opts = CompileOpts(mode, decomp, chi_budget, 1 if channel_reduction else 0, total_budget)
     h = ctypes.c_void_p()
     _check(L.tsim_compile(b, len(b), ctypes.byref(opts), ctypes.byref(h)))
     return h.value

@@ -58,6 +58,7 @@ tsim_status tsim_compile(const char* text, size_t len, const tsim_compile_opts* 
     o.decomp = TSIM_DECOMP_HEURISTIC;
     o.chi_budget = 0;
     o.channel_reduction = 1;
+    o.total_budget = 0;
     if (opts) o = *opts;
     if (o.mode != TSIM_MODE_DETECTORS && o.mode != TSIM_MODE_MEASUREMENTS) tsim::fail(TSIM_ERR_ARG, "bad mode");
     if (o.decomp < 0 || o.decomp > 2) tsim::fail(TSIM_ERR_ARG, "bad decomposition policy");

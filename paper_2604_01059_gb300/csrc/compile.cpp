@@ -25,6 +25,7 @@
 #include <map>
 #include <memory>
 #include <numeric>
+#include <unordered_map>
 
 #include "circuit.h"
 #include "device.h"
@@ -244,6 +245,16 @@ Bits restrict_bits(const Bits& b, size_t lo, size_t hi) {  // bits [lo, hi) shif
   return r;
 }
 
+struct BitsHash {
+  size_t operator()(const Bits& b) const {
+    uint64_t h = 1469598103934665603ull;
+    size_t n = b.w.size();
+    while (n && !b.w[n - 1]) --n;  // equal Bits may differ in trailing zero words
+    for (size_t i = 0; i < n; ++i) h = (h ^ b.w[i]) * 1099511628211ull;
+    return (size_t)h;
+  }
+};
+
 struct RChan {
   std::vector<Bits> cols;  // F-space columns, one per bit
   std::vector<double> p;   // 2^k
@@ -331,6 +342,7 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
   const int nout = opts.mode == TSIM_MODE_MEASUREMENTS ? P.nmeas : P.ndet + P.nobs;
   const size_t np = (size_t)E + (size_t)nout;
   const uint64_t budget = opts.chi_budget ? opts.chi_budget : (1ull << 20);
+  uint64_t total_terms = 0;
 
   // ---- 1-2: joint diagram, Clifford rewriting
   Builder J(C, opts.mode, std::vector<char>((size_t)nout, 1));
@@ -515,6 +527,8 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
       RawTable rt;
       DecompStats st;
       st.budget = budget;
+      st.total = &total_terms;
+      st.total_budget = opts.total_budget;
       decompose(M, opts.decomp, rt.terms, st);
       if (i < 0) P.chain_norm.push_back((int)rtabs.size());
       else { out_table[(size_t)outs[(size_t)i]] = (int)rtabs.size(); out_chain[(size_t)outs[(size_t)i]] = c; }
@@ -525,14 +539,21 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
   // ---- 4a: minimal f basis; table parities first so they occupy low X bits
   FBasis fb;
   auto epart = [&](const Bits& a) { return restrict_bits(a, 0, (size_t)E); };
-  struct FRef { Bits fa, fb; };
-  std::vector<std::vector<std::vector<FRef>>> tmasks(rtabs.size());
-  for (size_t t = 0; t < rtabs.size(); ++t) {
-    tmasks[t].resize(rtabs[t].terms.size());
+  // parities repeat across terms: express each distinct one once (the
+  // first-occurrence order, and so the f numbering, is unchanged)
+  std::unordered_map<Bits, Bits, BitsHash> fm_cache;
+  auto fmask_of = [&](const Bits& a) -> const Bits& {
+    auto it = fm_cache.find(a);
+    if (it != fm_cache.end()) return it->second;
+    Bits fm = fb.express(epart(a));
+    return fm_cache.emplace(a, std::move(fm)).first->second;
+  };
+  for (size_t t = 0; t < rtabs.size(); ++t)
     for (size_t k = 0; k < rtabs[t].terms.size(); ++k)
-      for (const Factor& f : rtabs[t].terms[k].fac)
-        tmasks[t][k].push_back({fb.express(epart(f.a)), fb.express(epart(f.b))});
-  }
+      for (const Factor& f : rtabs[t].terms[k].fac) {
+        fmask_of(f.a);
+        fmask_of(f.b);
+      }
   const int nft = (int)fb.orig.size();
   std::vector<Bits> rule_f((size_t)nout);
   for (int i = 0; i < nout; ++i)
@@ -562,6 +583,13 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
     return to_words(x, W);
   };
 
+  std::unordered_map<Bits, std::vector<uint64_t>, BitsHash> xm_cache;
+  auto xmask_of = [&](const Bits& full) -> const std::vector<uint64_t>& {
+    auto it = xm_cache.find(full);
+    if (it != xm_cache.end()) return it->second;
+    return xm_cache.emplace(full, xmask(fm_cache.at(full), full)).first->second;
+  };
+
   // ---- tables
   P.tables.resize(rtabs.size());
   for (size_t t = 0; t < rtabs.size(); ++t) {
@@ -576,8 +604,8 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
         pf.kind = f.kind;
         pf.alpha = f.alpha & 7;
         pf.beta = f.beta & 7;
-        pf.u = xmask(tmasks[t][k][q].fa, f.a);
-        pf.v = xmask(tmasks[t][k][q].fb, f.b);
+        pf.u = xmask_of(f.a);
+        pf.v = xmask_of(f.b);
         pt.f.push_back(std::move(pf));
       }
       P.tables[t].terms.push_back(std::move(pt));

@@ -400,10 +400,16 @@ struct Decomposer {
     g.fold_phase_factors();
     if (st->budget && out->size() >= st->budget)
       fail(TSIM_ERR_CHI_BUDGET, "stabilizer terms exceed the budget (" + std::to_string(st->budget) + ")");
+    if (st->total && st->total_budget && ++*st->total > st->total_budget)
+      fail(TSIM_ERR_CHI_BUDGET, "stabilizer terms of the program exceed the budget (" +
+                                    std::to_string(st->total_budget) + ")");
     out->push_back(g.as_term());
   }
 
   void run(Graph& g, int depth) {
+    // branches that vanish are pruned without a term; bound the search too
+    if (st->budget && ++st->nodes > 64 * st->budget)
+      fail(TSIM_ERR_CHI_BUDGET, "stabilizer decomposition search exceeds 64x the term budget");
     g.simplify();
     if (g.zero) return;
     std::vector<int> odd;

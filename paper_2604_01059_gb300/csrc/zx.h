@@ -102,8 +102,11 @@ ZW factor_value(const Factor& f, int a, int b);
 
 struct DecompStats {
   uint64_t terms = 0;
-  uint64_t budget = 0;
+  uint64_t budget = 0;         // per decomposition
   uint64_t leaves = 0;
+  uint64_t nodes = 0;          // branches explored
+  uint64_t* total = nullptr;   // running count over all decompositions of a program
+  uint64_t total_budget = 0;
 };
 
 // Decompose into Clifford terms (Appendix "Stabilizer decompositions").
