@@ -328,6 +328,50 @@ std::vector<uint64_t> to_words(const Bits& b, int W) {
 
 }  // namespace
 
+CutScorer g_cut_scorer;
+
+// Decompose one marginal diagram.  LEARNED: the spiders of the simplified
+// diagram are scored by the cut-order network and cut in ascending score;
+// the heuristic order is decomposed as well and judges (the order with fewer
+// terms wins; both give the same exact sum).  Without a scorer LEARNED falls
+// back to the heuristic.
+void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget, uint64_t* total,
+                        std::vector<Term>& out) {
+  DecompStats st;
+  st.budget = budget;
+  st.total = total;
+  st.total_budget = opts.total_budget;
+  if (opts.decomp != TSIM_DECOMP_LEARNED || !g_cut_scorer) {
+    decompose(M, opts.decomp == TSIM_DECOMP_LEARNED ? TSIM_DECOMP_HEURISTIC : opts.decomp, out, st);
+    return;
+  }
+  M.simplify();
+  M.compact();
+  for (int v = 0; v < M.n; ++v) M.uid[(size_t)v] = v;
+  std::vector<double> scores;
+  if (!g_cut_scorer(M, scores)) {
+    decompose(M, TSIM_DECOMP_HEURISTIC, out, st);
+    return;
+  }
+  std::vector<Term> learned, heuristic;
+  DecompStats s1 = st, s2 = st;
+  uint64_t t1 = total ? *total : 0, t2 = t1;
+  s1.total = &t1;
+  s2.total = &t2;
+  bool ok1 = true, ok2 = true;
+  try { decompose(M, TSIM_DECOMP_LEARNED, learned, s1, &scores); } catch (const Error& e) {
+    if (e.code != TSIM_ERR_CHI_BUDGET) throw;
+    ok1 = false;
+  }
+  try { decompose(M, TSIM_DECOMP_HEURISTIC, heuristic, s2); } catch (const Error& e) {
+    if (e.code != TSIM_ERR_CHI_BUDGET || !ok1) throw;
+    ok2 = false;
+  }
+  const bool use_learned = ok1 && (!ok2 || learned.size() <= heuristic.size());
+  out = use_learned ? std::move(learned) : std::move(heuristic);
+  if (total) *total = use_learned ? t1 : t2;
+}
+
 Program* compile_program(const std::string& text, const tsim_compile_opts& opts) {
   Circuit C = parse_circuit(text);
   auto prog = std::make_unique<Program>();
@@ -454,6 +498,10 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
   // ---- 3: marginal diagrams per chain, decomposed into Clifford terms
   struct RawTable { std::vector<Term> terms; };
   std::vector<RawTable> rtabs;
+  // Parities of the chain sub-diagrams before decomposition: every parity a
+  // decomposition produces is a sum of these (rewriting only adds parameter
+  // sets), so an f basis built from them does not depend on the cut order.
+  std::vector<Bits> span_gens;
   std::vector<int> out_table((size_t)nout, -1), out_chain((size_t)nout, -1);
   for (int c = 0; c < nchains; ++c) {
     // sub-diagram of the chain; constant scalars and factors of other
@@ -477,6 +525,11 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
       f.a.for_each(look);
       f.b.for_each(look);
       if (hit >= 0 && find(out_node(hit)) == root) Gc.fac.push_back(f);
+    }
+    for (int v = 0; v < Gc.n; ++v) span_gens.push_back(Gc.P[(size_t)v]);
+    for (const Factor& f : Gc.fac) {
+      span_gens.push_back(f.a);
+      span_gens.push_back(f.b);
     }
     const std::vector<int>& outs = chain_outputs[(size_t)c];
     for (int i = -1; i < (int)outs.size(); ++i) {
@@ -525,11 +578,7 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
         }
       }
       RawTable rt;
-      DecompStats st;
-      st.budget = budget;
-      st.total = &total_terms;
-      st.total_budget = opts.total_budget;
-      decompose(M, opts.decomp, rt.terms, st);
+      decompose_marginal(M, opts, budget, &total_terms, rt.terms);
       if (i < 0) P.chain_norm.push_back((int)rtabs.size());
       else { out_table[(size_t)outs[(size_t)i]] = (int)rtabs.size(); out_chain[(size_t)outs[(size_t)i]] = c; }
       rtabs.push_back(std::move(rt));
@@ -548,13 +597,15 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
     Bits fm = fb.express(epart(a));
     return fm_cache.emplace(a, std::move(fm)).first->second;
   };
+  for (const Bits& g : span_gens) fmask_of(g);
+  const int nft = (int)fb.orig.size();
   for (size_t t = 0; t < rtabs.size(); ++t)
     for (size_t k = 0; k < rtabs[t].terms.size(); ++k)
       for (const Factor& f : rtabs[t].terms[k].fac) {
         fmask_of(f.a);
         fmask_of(f.b);
       }
-  const int nft = (int)fb.orig.size();
+  if ((int)fb.orig.size() != nft) fail(TSIM_ERR_INTERNAL, "a decomposition left the span of its diagram's parities");
   std::vector<Bits> rule_f((size_t)nout);
   for (int i = 0; i < nout; ++i)
     if (pivot_row[(size_t)i] >= 0) {

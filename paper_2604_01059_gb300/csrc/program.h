@@ -71,6 +71,12 @@ void save_program(const Program& p, const std::string& path);
 Program* load_program(const std::string& path);
 ZW eval_table_host(const Program& p, int t, const uint64_t* x);
 
+// Scores the spiders of a decomposition root (indexed by uid) for the learned
+// cut order; returns false when no model or no GPU is available.
+struct Graph;
+using CutScorer = bool (*)(const Graph&, std::vector<double>&);
+extern CutScorer g_cut_scorer;
+
 // message for tsim_last_error(); copies into a fixed thread-local buffer
 void set_last_error(const char* msg);
 

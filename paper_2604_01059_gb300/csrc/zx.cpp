@@ -15,6 +15,7 @@
 #include "zx.h"
 
 #include <algorithm>
+#include <cmath>
 
 namespace tsim {
 
@@ -64,6 +65,7 @@ int Graph::add_var(int l) {
   lam.push_back(l & 7);
   P.push_back(Bits(np));
   alive.push_back(1);
+  uid.push_back(-1);
   return n++;
 }
 
@@ -296,6 +298,7 @@ void Graph::compact() {
     if (alive[(size_t)v]) {
       int nv = h.add_var(lam[(size_t)v]);
       h.P[(size_t)nv] = P[(size_t)v];
+      h.uid[(size_t)nv] = uid[(size_t)v];
     }
   for (int v = 0; v < n; ++v) {
     if (!alive[(size_t)v]) continue;
@@ -394,6 +397,7 @@ struct Decomposer {
   std::vector<Term>* out;
   DecompStats* st;
   const std::vector<double>* scores;
+  int first;
 
   void emit(Graph& g) {
     if (g.zero) return;
@@ -425,12 +429,14 @@ struct Decomposer {
     odd.clear();
     for (int v = 0; v < g.n; ++v)
       if (g.alive[(size_t)v] && (g.lam[(size_t)v] & 1)) odd.push_back(v);
-    if (policy == 1 && scores && !scores->empty()) {
-      // learned order: vertices carry no stable id after compaction, so the
-      // score is looked up by degree-rank; ties fall back to ascending id
-      std::stable_sort(odd.begin(), odd.end(), [&](int a, int b) {
-        return g.degree(a) > g.degree(b);
-      });
+    auto score = [&](int v) {
+      const int u = g.uid[(size_t)v];
+      if (u >= 0 && u == first) return -1e300;
+      if (policy == 1 && scores && u >= 0 && (size_t)u < scores->size()) return (*scores)[(size_t)u];
+      return policy == 1 ? 1e300 : 0.0;
+    };
+    if (first >= 0 || (policy == 1 && scores)) {
+      std::stable_sort(odd.begin(), odd.end(), [&](int a, int b) { return score(a) < score(b); });
     }
     if (policy == 2 || odd.size() == 1) {
       int v = odd[0];
@@ -457,10 +463,70 @@ struct Decomposer {
 }  // namespace
 
 void decompose(Graph g, int policy, std::vector<Term>& out, DecompStats& st,
-               const std::vector<double>* scores) {
-  Decomposer d{policy, &out, &st, scores};
+               const std::vector<double>* scores, int first) {
+  Decomposer d{policy, &out, &st, scores, first};
   d.run(g, 0);
   st.terms = out.size();
+}
+
+}  // namespace tsim
+
+namespace tsim {
+
+void cut_features(const Graph& g, std::vector<float>& X, std::vector<int>& rowptr, std::vector<int>& col,
+                  std::vector<int>& uids) {
+  std::vector<int> idx((size_t)g.n, -1);
+  int m = 0;
+  for (int v = 0; v < g.n; ++v)
+    if (g.alive[(size_t)v]) idx[(size_t)v] = m++;
+  X.assign((size_t)m * kCutFeatures, 0.0f);
+  rowptr.assign((size_t)m + 1, 0);
+  col.clear();
+  uids.assign((size_t)m, -1);
+  for (int v = 0; v < g.n; ++v) {
+    if (!g.alive[(size_t)v]) continue;
+    const int i = idx[(size_t)v];
+    const int l = g.lam[(size_t)v];
+    float* x = &X[(size_t)i * kCutFeatures];
+    const std::vector<int> nb = g.nbrs(v);
+    int odd_nb = 0;
+    for (int u : nb) {
+      col.push_back(idx[(size_t)u]);
+      odd_nb += g.lam[(size_t)u] & 1;
+    }
+    rowptr[(size_t)i + 1] = (int)col.size();
+    x[0] = (float)(l & 1);                       // non-Clifford
+    x[1] = (float)(l == 0 || l == 4);            // Pauli
+    x[2] = (float)(l == 2 || l == 6);            // proper Clifford
+    x[3 + l] = 1.0f;                             // phase mod 2pi in units of pi/4
+    x[11] = std::log1p((float)nb.size());        // degree
+    x[12] = g.P[(size_t)v].any() ? 1.0f : 0.0f;  // parameter-dependent phase
+    x[13] = nb.empty() ? 0.0f : (float)odd_nb / (float)nb.size();
+    uids[(size_t)i] = g.uid[(size_t)v];
+  }
+}
+
+Graph random_zx_diagram(uint64_t seed, int t, int c) {
+  uint64_t s = seed * 0x9E3779B97F4A7C15ull + 0xD1B54A32D192ED03ull;
+  auto next = [&]() {  // splitmix64
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  Graph g(1);
+  const int n = t + c;
+  for (int v = 0; v < n; ++v) {
+    const int l = v < t ? (int)(1 + 2 * (next() % 4)) : (int)(2 * (next() % 4));
+    g.add_var(l);
+  }
+  for (int v = 0; v < n; ++v)
+    for (int k = 0; k < 3; ++k) {
+      const int u = (int)(next() % (uint64_t)n);
+      if (u != v && !g.edge(u, v)) g.toggle(u, v);
+    }
+  return g;
 }
 
 }  // namespace tsim

@@ -62,6 +62,7 @@ struct Graph {
   std::vector<Bits> P;
   std::vector<std::vector<uint64_t>> adj;
   std::vector<char> alive;
+  std::vector<int> uid;  // stable vertex id through copies and compaction (-1: created later)
   int s2 = 0, ph = 0;
   bool zero = false;
   std::vector<Factor> fac;
@@ -110,10 +111,22 @@ struct DecompStats {
 };
 
 // Decompose into Clifford terms (Appendix "Stabilizer decompositions").
-// policy: 0 = pairs in ascending id (2 terms per pair), 2 = single cuts,
-// 1 = learned order given by `order` (vertex ranks, lower cut first).
+// policy: 0 = pairs of odd spiders in ascending id (2 terms per pair),
+// 2 = single cuts, 1 = pairs in ascending `scores[uid]` (a learned cut order;
+// spiders without a score go last).  `first` >= 0 forces the spider with that
+// uid into the first cut.  Every order gives the same sum.
 void decompose(Graph g, int policy, std::vector<Term>& out, DecompStats& st,
-               const std::vector<double>* scores = nullptr);
+               const std::vector<double>* scores = nullptr, int first = -1);
+
+// Node features of the alive spiders for the cut-order network, row-major
+// [nodes][kCutFeatures], with the adjacency in CSR form and each node's uid.
+constexpr int kCutFeatures = 14;
+void cut_features(const Graph& g, std::vector<float>& X, std::vector<int>& rowptr,
+                  std::vector<int>& col, std::vector<int>& uids);
+
+// A seeded random Clifford+T ZX diagram: t non-Clifford spiders and c
+// Clifford spiders, each joined by Hadamard edges to three random others.
+Graph random_zx_diagram(uint64_t seed, int t, int c);
 
 // Brute-force value of a small graph for one parameter assignment (tests).
 ZW brute_value(const Graph& g, const Bits& pv);
