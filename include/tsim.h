@@ -239,6 +239,73 @@ tsim_status tsim_program_device_table_stats(const tsim_program* prog, int t, uin
  * random small parameterised graphs (no GPU).  Returns TSIM_OK when all pass. */
 tsim_status tsim_selftest_rules(uint64_t seed, int iterations);
 
+
+/* ---- Learned cut order (compile time).  The paper names better cutting
+ * decompositions as open work (Sec. "Discussion"); any cut order yields the
+ * same sum of stabilizer terms (Appendix "Stabilizer decompositions"), so a
+ * learned order changes table sizes only.  The network: node features
+ * [non-Clifford, Pauli, proper Clifford, phase one-hot (8), log(1 + degree),
+ * parameter-dependent phase, fraction of non-Clifford neighbours]
+ * (TSIM_CUT_FEATURES), H0 = relu(X W_in + b_in), three layers
+ * H' = relu(H Ws + mean_nbrs(H) Wn + b) of width 64, score s = H3 w_o + b_o.
+ * Weights are applied in BF16 (round to nearest even of the FP32 master
+ * copy), products accumulate in FP32.  Parameter vector layout (FP32):
+ * [W_in (14 x 64 row-major), b_in (64)], 3 x [Ws (64x64), Wn (64x64), b (64)],
+ * [w_o (64), b_o (1)].  Graph arguments are host arrays: x [n][14] row-major,
+ * CSR rowptr [n + 1], col [rowptr[n]] (neighbour ids; symmetric for the
+ * gradient), graph_off [n_graphs + 1] node offsets, y [n] labels (NaN = no
+ * label).  Entry points that compute run on the current CUDA device and
+ * allocate their own device memory; they return TSIM_ERR_ARG on inconsistent
+ * arrays and TSIM_ERR_CUDA when the device fails. */
+#define TSIM_CUT_FEATURES 14
+int tsim_cut_num_params(void);
+
+/* He-uniform weights, zero biases, from a splitmix64 stream of seed (host). */
+tsim_status tsim_cut_init_params(uint64_t seed, float* params);
+
+/* Training graphs: n_graphs seeded random Clifford+T ZX diagrams with
+ * t_min..t_max non-Clifford spiders, reduced by the Clifford rewrites; up to
+ * max_candidates non-Clifford spiders per graph are labelled with log2 of the
+ * exact number of stabilizer terms the decomposition produces when that
+ * spider is cut first (log2(2 budget) when it exceeds budget).  Written to
+ * path in a binary format read by tsim_cut_train (host only, multithreaded). */
+tsim_status tsim_cut_dataset(uint64_t seed, int n_graphs, int t_min, int t_max, uint64_t budget,
+                             int max_candidates, const char* path);
+
+/* Scores of all nodes of a graph batch. */
+tsim_status tsim_cut_forward(const float* params, int n_nodes, const float* x, const int* rowptr,
+                             const int* col, float* scores);
+
+/* Loss (centred squared error per graph, averaged over graphs with two or
+ * more labels) and its gradient with respect to the BF16 weights, written in
+ * the parameter layout. */
+tsim_status tsim_cut_loss_grad(const float* params, int n_nodes, const float* x, const int* rowptr,
+                               const int* col, const float* y, int n_graphs, const int* graph_off,
+                               float* loss, float* grad);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8; step >= 1 counts from 1)
+ * on host arrays of tsim_cut_num_params() floats, updated in place. */
+tsim_status tsim_cut_adam_step(float* params, const float* grad, float* m, float* v, int step, float lr);
+
+/* Adam training on a dataset file over minibatches of batch_graphs
+ * consecutive graphs, visited in a seeded order each epoch; params holds the
+ * initial values and receives the trained ones; loss_per_epoch (may be NULL)
+ * receives each epoch's mean minibatch loss. */
+tsim_status tsim_cut_train(const char* dataset_path, int epochs, int batch_graphs, float lr, uint64_t seed,
+                           float* params, float* loss_per_epoch);
+
+/* Register (params != NULL) the network used by TSIM_DECOMP_LEARNED on the
+ * current device, or remove it (NULL).  Without a model, or when scoring
+ * fails, LEARNED compiles with the heuristic order.  With a model the
+ * compiler decomposes each marginal in both orders and keeps the one with
+ * fewer terms. */
+tsim_status tsim_cut_model_set(const float* params);
+
+/* out[0] = scorer calls, out[1] = calls that produced scores, out[2] =
+ * marginals that kept the learned order, out[3] = marginals where the
+ * heuristic order had fewer terms (counts since the library was loaded). */
+tsim_status tsim_cut_policy_stats(uint64_t out[4]);
+
 #ifdef __cplusplus
 }
 #endif

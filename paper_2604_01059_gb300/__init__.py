@@ -98,11 +98,22 @@ def load_library(path: str | None = None):
     L.tsim_selftest_rules.argtypes = [u64, i32]
     L.tsim_measure_int_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
     L.tsim_program_device_table_stats.argtypes = [vp, i32, ctypes.POINTER(u64)]
+    L.tsim_cut_num_params.argtypes = []
+    L.tsim_cut_init_params.argtypes = [u64, vp]
+    L.tsim_cut_dataset.argtypes = [u64, i32, i32, i32, u64, i32, ctypes.c_char_p]
+    L.tsim_cut_forward.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.tsim_cut_loss_grad.argtypes = [vp, i32, vp, vp, vp, vp, i32, vp, vp, vp]
+    L.tsim_cut_adam_step.argtypes = [vp, vp, vp, vp, i32, ctypes.c_float]
+    L.tsim_cut_train.argtypes = [ctypes.c_char_p, i32, i32, ctypes.c_float, u64, vp, vp]
+    L.tsim_cut_model_set.argtypes = [vp]
+    L.tsim_cut_policy_stats.argtypes = [vp]
     for n in ("tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_program_table_stats", "tsim_sample",
               "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_batch_create",
               "tsim_batch_launch", "tsim_batch_info", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
               "tsim_program_save", "tsim_program_load", "tsim_selftest_rules", "tsim_measure_int_peak",
-              "tsim_program_device_table_stats"):
+              "tsim_program_device_table_stats", "tsim_cut_num_params", "tsim_cut_init_params",
+              "tsim_cut_dataset", "tsim_cut_forward", "tsim_cut_loss_grad", "tsim_cut_adam_step", "tsim_cut_train",
+              "tsim_cut_model_set", "tsim_cut_policy_stats"):
         getattr(L, n).restype = ctypes.c_int
     _lib = L
     return L
@@ -270,6 +281,132 @@ def tsim_program_device_table_stats(h, t):
 
 def tsim_selftest_rules(seed=0, iterations=200):
     _check(load_library().tsim_selftest_rules(seed, iterations))
+
+
+# ---- learned cut order (compile time)
+
+CUT_FEATURES = 14
+
+
+def _f32(a, n=None):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} floats, got {a.size}")
+    return a
+
+
+def _i32(a):
+    import numpy as np
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def tsim_cut_num_params() -> int:
+    return load_library().tsim_cut_num_params()
+
+
+def tsim_cut_init_params(seed=0):
+    import numpy as np
+    p = np.zeros(tsim_cut_num_params(), dtype=np.float32)
+    _check(load_library().tsim_cut_init_params(seed, _p(p)))
+    return p
+
+
+def tsim_cut_dataset(seed, n_graphs, t_min, t_max, budget, max_candidates, path):
+    _check(load_library().tsim_cut_dataset(seed, n_graphs, t_min, t_max, budget, max_candidates,
+                                           str(path).encode()))
+
+
+def tsim_cut_forward(params, x, rowptr, col):
+    """Scores of every node (runs on the current CUDA device)."""
+    import numpy as np
+    params = _f32(params, tsim_cut_num_params())
+    x, rowptr, col = _f32(x), _i32(rowptr), _i32(col)
+    n = len(rowptr) - 1
+    out = np.zeros(n, dtype=np.float32)
+    _check(load_library().tsim_cut_forward(_p(params), n, _p(x), _p(rowptr), _p(col), _p(out)))
+    return out
+
+
+def tsim_cut_loss_grad(params, x, rowptr, col, y, graph_off):
+    import numpy as np
+    params = _f32(params, tsim_cut_num_params())
+    x, rowptr, col, y, goff = _f32(x), _i32(rowptr), _i32(col), _f32(y), _i32(graph_off)
+    n = len(rowptr) - 1
+    loss = np.zeros(1, dtype=np.float32)
+    grad = np.zeros_like(params)
+    _check(load_library().tsim_cut_loss_grad(_p(params), n, _p(x), _p(rowptr), _p(col), _p(y), len(goff) - 1,
+                                             _p(goff), _p(loss), _p(grad)))
+    return float(loss[0]), grad
+
+
+def tsim_cut_adam_step(params, grad, m, v, step, lr):
+    """One Adam step; returns new (params, m, v)."""
+    n = tsim_cut_num_params()
+    params, grad, m, v = (_f32(a, n).copy() for a in (params, grad, m, v))
+    _check(load_library().tsim_cut_adam_step(_p(params), _p(grad), _p(m), _p(v), step, lr))
+    return params, m, v
+
+
+def tsim_cut_train(dataset_path, params, epochs=50, batch_graphs=32, lr=1e-3, seed=0):
+    """Train on a dataset file; returns (trained params, loss per epoch)."""
+    import numpy as np
+    params = _f32(params, tsim_cut_num_params()).copy()
+    hist = np.zeros(epochs, dtype=np.float32)
+    _check(load_library().tsim_cut_train(str(dataset_path).encode(), epochs, batch_graphs, lr, seed, _p(params),
+                                         _p(hist)))
+    return params, hist
+
+
+def tsim_cut_model_set(params):
+    """Register the network for DECOMP_LEARNED (None removes it)."""
+    if params is None:
+        _check(load_library().tsim_cut_model_set(None))
+        return
+    params = _f32(params, tsim_cut_num_params())
+    _check(load_library().tsim_cut_model_set(_p(params)))
+
+
+def tsim_cut_policy_stats():
+    out = (ctypes.c_uint64 * 4)()
+    _check(load_library().tsim_cut_policy_stats(out))
+    return tuple(out)
+
+
+def read_cut_dataset(path):
+    """Parse a dataset file into (x, rowptr, col, y, graph_off) numpy arrays."""
+    import numpy as np
+    raw = open(path, "rb").read()
+    if raw[:8] != b"TSIMCUTD":
+        raise ValueError("not a cut-order dataset")
+    ng, nf = np.frombuffer(raw, dtype=np.int32, count=2, offset=8)
+    if nf != CUT_FEATURES:
+        raise ValueError("feature count differs")
+    off = 16
+    xs, rps, cols, ys, goff = [], [], [], [], [0]
+    n_tot = e_tot = 0
+    for _ in range(int(ng)):
+        n, nnz = (int(v) for v in np.frombuffer(raw, dtype=np.int32, count=2, offset=off))
+        off += 8
+        if n:
+            xs.append(np.frombuffer(raw, dtype=np.float32, count=n * nf, offset=off).reshape(n, nf)); off += 4 * n * nf
+            rp = np.frombuffer(raw, dtype=np.int32, count=n + 1, offset=off); off += 4 * (n + 1)
+            c = np.frombuffer(raw, dtype=np.int32, count=nnz, offset=off); off += 4 * nnz
+            ys.append(np.frombuffer(raw, dtype=np.float32, count=n, offset=off)); off += 4 * n
+            rps.append(rp[1:] + e_tot)
+            cols.append(c + n_tot)
+            n_tot += n
+            e_tot += nnz
+        goff.append(n_tot)
+    x = np.concatenate(xs) if xs else np.zeros((0, nf), np.float32)
+    rowptr = np.concatenate([[0]] + rps).astype(np.int32)
+    col = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
+    y = np.concatenate(ys) if ys else np.zeros(0, np.float32)
+    return x, rowptr, col, y, np.array(goff, dtype=np.int32)
 
 
 class Program:

@@ -1,10 +1,12 @@
 // extern "C" boundary: argument checks, exception -> status conversion.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <random>
 #include <string>
 
 #include "circuit.h"
+#include "cutnet.h"
 #include "device.h"
 #include "program.h"
 #include "zx.h"
@@ -357,6 +359,18 @@ tsim_status tsim_selftest_rules(uint64_t seed, int iterations) {
         tsim::decompose(g, policy, terms, st);
         check(terms, policy == 0 ? "pairs" : "single cuts");
       }
+      {
+        // a score-ordered cut sequence (random scores, a forced first cut)
+        // must give the same sum as any other order
+        tsim::Graph h = g;
+        for (int v = 0; v < h.n; ++v) h.uid[(size_t)v] = v;
+        std::vector<double> scores((size_t)h.n);
+        for (auto& x : scores) x = (double)(rng() % 1000);
+        std::vector<tsim::Term> terms;
+        tsim::DecompStats st;
+        tsim::decompose(h, TSIM_DECOMP_LEARNED, terms, st, &scores, (int)(rng() % (uint64_t)std::max(1, h.n)));
+        check(terms, "score order");
+      }
       // single steps on a copy: each must preserve the brute-force value
       tsim::Graph h = g;
       for (int v = 0; v < h.n; ++v) {
@@ -376,6 +390,126 @@ tsim_status tsim_selftest_rules(uint64_t seed, int iterations) {
         }
       }
     }
+  });
+}
+
+}  // extern "C"
+
+namespace {
+
+// Copies and checks a graph batch given through the C ABI.
+tsim::cutnet::Batch make_batch(int n, const float* x, const int* rowptr, const int* col, const float* y,
+                               int n_graphs, const int* goff, bool symmetric) {
+  using tsim::fail;
+  tsim::cutnet::Batch b;
+  if (n < 0 || (n && (!x || !rowptr)) || n_graphs < 1 || (goff == nullptr && n_graphs != 1))
+    fail(TSIM_ERR_ARG, "bad graph batch sizes or NULL arrays");
+  b.n = n;
+  b.X.assign(x, x + (size_t)n * TSIM_CUT_FEATURES);
+  if (n) b.rowptr.assign(rowptr, rowptr + n + 1);
+  else b.rowptr = {0};
+  if (b.rowptr[0] != 0) fail(TSIM_ERR_ARG, "rowptr[0] must be 0");
+  for (int i = 0; i < n; ++i)
+    if (b.rowptr[(size_t)i + 1] < b.rowptr[(size_t)i]) fail(TSIM_ERR_ARG, "rowptr is not monotone");
+  const int nnz = b.rowptr[(size_t)n];
+  if (nnz && !col) fail(TSIM_ERR_ARG, "NULL col");
+  b.col.assign(col ? col : nullptr, col ? col + nnz : nullptr);
+  for (int c : b.col)
+    if (c < 0 || c >= n) fail(TSIM_ERR_ARG, "neighbour id out of range");
+  if (goff) b.goff.assign(goff, goff + n_graphs + 1);
+  else b.goff = {0, n};
+  if (b.goff.front() != 0 || b.goff.back() != n) fail(TSIM_ERR_ARG, "graph offsets must run from 0 to n");
+  for (int g = 0; g < n_graphs; ++g)
+    if (b.goff[(size_t)g + 1] < b.goff[(size_t)g]) fail(TSIM_ERR_ARG, "graph offsets are not monotone");
+  if (y) b.y.assign(y, y + n);
+  if (symmetric) {
+    std::vector<std::vector<int>> adj((size_t)n);
+    for (int v = 0; v < n; ++v) {
+      for (int e = b.rowptr[(size_t)v]; e < b.rowptr[(size_t)v + 1]; ++e) {
+        const int u = b.col[(size_t)e];
+        if (u == v) fail(TSIM_ERR_ARG, "self loop in the adjacency");
+        adj[(size_t)v].push_back(u);
+      }
+      std::sort(adj[(size_t)v].begin(), adj[(size_t)v].end());
+      if (std::adjacent_find(adj[(size_t)v].begin(), adj[(size_t)v].end()) != adj[(size_t)v].end())
+        fail(TSIM_ERR_ARG, "repeated edge in the adjacency");
+    }
+    for (int v = 0; v < n; ++v)
+      for (int u : adj[(size_t)v])
+        if (!std::binary_search(adj[(size_t)u].begin(), adj[(size_t)u].end(), v))
+          fail(TSIM_ERR_ARG, "the adjacency is not symmetric");
+    for (int g = 0; g < n_graphs; ++g)
+      for (int v = b.goff[(size_t)g]; v < b.goff[(size_t)g + 1]; ++v)
+        for (int u : adj[(size_t)v])
+          if (u < b.goff[(size_t)g] || u >= b.goff[(size_t)g + 1]) fail(TSIM_ERR_ARG, "an edge joins two graphs");
+  }
+  return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tsim_cut_num_params(void) { return tsim::cutnet::num_params(); }
+
+tsim_status tsim_cut_init_params(uint64_t seed, float* params) {
+  return guard([&] {
+    if (!params) tsim::fail(TSIM_ERR_ARG, "NULL params");
+    tsim::cutnet::init_params(seed, params);
+  });
+}
+
+tsim_status tsim_cut_dataset(uint64_t seed, int n_graphs, int t_min, int t_max, uint64_t budget,
+                             int max_candidates, const char* path) {
+  return guard([&] {
+    if (!path) tsim::fail(TSIM_ERR_ARG, "NULL path");
+    tsim::cutnet::write_dataset(seed, n_graphs, t_min, t_max, budget, max_candidates, path);
+  });
+}
+
+tsim_status tsim_cut_forward(const float* params, int n_nodes, const float* x, const int* rowptr,
+                             const int* col, float* scores) {
+  return guard([&] {
+    if (!params || (n_nodes && !scores)) tsim::fail(TSIM_ERR_ARG, "NULL params or scores");
+    tsim::cutnet::Batch b = make_batch(n_nodes, x, rowptr, col, nullptr, 1, nullptr, false);
+    tsim::cutnet::forward(params, b, scores);
+  });
+}
+
+tsim_status tsim_cut_loss_grad(const float* params, int n_nodes, const float* x, const int* rowptr,
+                               const int* col, const float* y, int n_graphs, const int* graph_off,
+                               float* loss, float* grad) {
+  return guard([&] {
+    if (!params || !grad || !loss || (n_nodes && !y)) tsim::fail(TSIM_ERR_ARG, "NULL argument");
+    tsim::cutnet::Batch b = make_batch(n_nodes, x, rowptr, col, y, n_graphs, graph_off, true);
+    *loss = (float)tsim::cutnet::loss_grad(params, b, grad);
+  });
+}
+
+tsim_status tsim_cut_adam_step(float* params, const float* grad, float* m, float* v, int step, float lr) {
+  return guard([&] {
+    if (!params || !grad || !m || !v) tsim::fail(TSIM_ERR_ARG, "NULL argument");
+    tsim::cutnet::adam_step(params, grad, m, v, tsim::cutnet::num_params(), step, lr);
+  });
+}
+
+tsim_status tsim_cut_train(const char* dataset_path, int epochs, int batch_graphs, float lr, uint64_t seed,
+                           float* params, float* loss_per_epoch) {
+  return guard([&] {
+    if (!dataset_path || !params) tsim::fail(TSIM_ERR_ARG, "NULL argument");
+    tsim::cutnet::Batch b = tsim::cutnet::read_dataset(dataset_path);
+    tsim::cutnet::train(b, epochs, batch_graphs, lr, seed, params, loss_per_epoch);
+  });
+}
+
+tsim_status tsim_cut_model_set(const float* params) {
+  return guard([&] { tsim::cutnet::set_model(params); });
+}
+
+tsim_status tsim_cut_policy_stats(uint64_t out[4]) {
+  return guard([&] {
+    if (!out) tsim::fail(TSIM_ERR_ARG, "NULL out");
+    for (int i = 0; i < 4; ++i) out[i] = tsim::g_cut_stats[i].load();
   });
 }
 

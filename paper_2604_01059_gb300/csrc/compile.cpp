@@ -328,20 +328,33 @@ std::vector<uint64_t> to_words(const Bits& b, int W) {
 
 }  // namespace
 
-CutScorer g_cut_scorer;
+std::atomic<CutScorer> g_cut_scorer{nullptr};
+std::atomic<uint64_t> g_cut_stats[4];
 
 // Decompose one marginal diagram.  LEARNED: the spiders of the simplified
 // diagram are scored by the cut-order network and cut in ascending score;
 // the heuristic order is decomposed as well and judges (the order with fewer
 // terms wins; both give the same exact sum).  Without a scorer LEARNED falls
 // back to the heuristic.
+// When set, compile_program records each marginal's diagram after the
+// Clifford rewrites and stops before decomposing anything.
+thread_local std::vector<Graph>* g_marginal_capture = nullptr;
+struct CaptureDone {};
+
 void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget, uint64_t* total,
                         std::vector<Term>& out) {
+  if (g_marginal_capture) {
+    M.simplify();
+    M.compact();
+    g_marginal_capture->push_back(std::move(M));
+    return;
+  }
   DecompStats st;
   st.budget = budget;
   st.total = total;
   st.total_budget = opts.total_budget;
-  if (opts.decomp != TSIM_DECOMP_LEARNED || !g_cut_scorer) {
+  const CutScorer scorer = g_cut_scorer.load();
+  if (opts.decomp != TSIM_DECOMP_LEARNED || !scorer) {
     decompose(M, opts.decomp == TSIM_DECOMP_LEARNED ? TSIM_DECOMP_HEURISTIC : opts.decomp, out, st);
     return;
   }
@@ -349,7 +362,8 @@ void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget,
   M.compact();
   for (int v = 0; v < M.n; ++v) M.uid[(size_t)v] = v;
   std::vector<double> scores;
-  if (!g_cut_scorer(M, scores)) {
+  g_cut_stats[0]++;
+  if (!scorer(M, scores)) {
     decompose(M, TSIM_DECOMP_HEURISTIC, out, st);
     return;
   }
@@ -367,7 +381,9 @@ void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget,
     if (e.code != TSIM_ERR_CHI_BUDGET || !ok1) throw;
     ok2 = false;
   }
+  g_cut_stats[1]++;
   const bool use_learned = ok1 && (!ok2 || learned.size() <= heuristic.size());
+  g_cut_stats[use_learned ? 2 : 3]++;
   out = use_learned ? std::move(learned) : std::move(heuristic);
   if (total) *total = use_learned ? t1 : t2;
 }
@@ -584,6 +600,8 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
       rtabs.push_back(std::move(rt));
     }
   }
+
+  if (g_marginal_capture) throw CaptureDone{};
 
   // ---- 4a: minimal f basis; table parities first so they occupy low X bits
   FBasis fb;
@@ -834,6 +852,24 @@ ZW eval_table_host(const Program& p, int t, const uint64_t* x) {
     sum = zw_add(sum, v);
   }
   return sum;
+}
+
+std::vector<Graph> marginal_diagrams(const std::string& text, int mode) {
+  std::vector<Graph> out;
+  tsim_compile_opts opts{};
+  opts.mode = mode;
+  opts.decomp = TSIM_DECOMP_HEURISTIC;
+  opts.channel_reduction = 1;
+  g_marginal_capture = &out;
+  try {
+    delete compile_program(text, opts);
+  } catch (const CaptureDone&) {
+  } catch (...) {
+    g_marginal_capture = nullptr;
+    throw;
+  }
+  g_marginal_capture = nullptr;
+  return out;
 }
 
 }  // namespace tsim

@@ -7,6 +7,7 @@
 // where f = T e mod 2 (Eq. detector_sampling) and "random outputs" are the
 // outputs drawn by Algorithm 1.  Every parity of the program is a mask over X.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -71,11 +72,18 @@ void save_program(const Program& p, const std::string& path);
 Program* load_program(const std::string& path);
 ZW eval_table_host(const Program& p, int t, const uint64_t* x);
 
+struct Graph;
+// The diagram of every marginal of a circuit after the Clifford rewrites, in
+// the order the compiler decomposes them (nothing is decomposed).
+std::vector<Graph> marginal_diagrams(const std::string& text, int mode);
+
 // Scores the spiders of a decomposition root (indexed by uid) for the learned
 // cut order; returns false when no model or no GPU is available.
-struct Graph;
 using CutScorer = bool (*)(const Graph&, std::vector<double>&);
-extern CutScorer g_cut_scorer;
+extern std::atomic<CutScorer> g_cut_scorer;
+// learned-order bookkeeping: [0] scorer calls, [1] calls that returned scores,
+// [2] marginals where the learned order was kept, [3] where the heuristic won
+extern std::atomic<uint64_t> g_cut_stats[4];
 
 // message for tsim_last_error(); copies into a fixed thread-local buffer
 void set_last_error(const char* msg);

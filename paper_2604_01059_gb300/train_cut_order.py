@@ -1,0 +1,80 @@
+"""Train the cut-order network and write its weights next to this file.
+
+    python -m paper_2604_01059_gb300.train_cut_order [--dataset PATH] [--epochs N] ...
+
+Training data: marginal diagrams of seeded random Clifford+T circuits with 20
+to 80 T/T_DAG gates, each labelled with the exact stabilizer-term counts the
+compiler measures when a candidate spider is cut first (written by
+``tsim_cut_dataset``; the file is reused when it exists).  Training runs the
+library's CUDA kernels (BF16 weights, FP32 accumulation, Adam).  Output:
+``cut_order.f32`` (the parameter vector, little-endian float32, in the layout
+``tsim_cut_num_params`` documents) and ``cut_order.json`` (how it was made).
+"""
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import (read_cut_dataset, tsim_cut_dataset, tsim_cut_init_params, tsim_cut_loss_grad, tsim_cut_num_params,
+               tsim_cut_train)
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+WEIGHTS = os.path.join(HERE, "cut_order.f32")
+
+
+def load_weights(path=WEIGHTS):
+    """The trained parameter vector (float32), or None when absent."""
+    if not os.path.exists(path):
+        return None
+    p = np.fromfile(path, dtype="<f4")
+    if p.size != tsim_cut_num_params():
+        raise ValueError(f"{path}: {p.size} parameters, the library expects {tsim_cut_num_params()}")
+    return p
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--dataset", default=None, help="dataset file (generated when missing)")
+    ap.add_argument("--graphs", type=int, default=2000)
+    ap.add_argument("--t-min", type=int, default=20)
+    ap.add_argument("--t-max", type=int, default=80)
+    ap.add_argument("--budget", type=int, default=1024, help="term budget of one label")
+    ap.add_argument("--candidates", type=int, default=8, help="labelled spiders per graph")
+    ap.add_argument("--data-seed", type=int, default=0)
+    ap.add_argument("--epochs", type=int, default=150)
+    ap.add_argument("--batch", type=int, default=32, help="graphs per minibatch")
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default=WEIGHTS)
+    a = ap.parse_args(argv)
+    ds = a.dataset or os.path.join(os.path.dirname(os.path.abspath(a.out)), "cut_order_dataset.bin")
+    t0 = time.time()
+    if not os.path.exists(ds):
+        tsim_cut_dataset(a.data_seed, a.graphs, a.t_min, a.t_max, a.budget, a.candidates, ds)
+    t_data = time.time() - t0
+    x, rp, col, y, go = read_cut_dataset(ds)
+    lab = ~np.isnan(y)
+    p0 = tsim_cut_init_params(a.seed)
+    L0, _ = tsim_cut_loss_grad(p0, x, rp, col, y, go)
+    t1 = time.time()
+    p, hist = tsim_cut_train(ds, p0, epochs=a.epochs, batch_graphs=a.batch, lr=a.lr, seed=a.seed)
+    t_train = time.time() - t1
+    L1, _ = tsim_cut_loss_grad(p, x, rp, col, y, go)
+    p.astype("<f4").tofile(a.out)
+    rec = {
+        "dataset": {"graphs": int(len(go) - 1), "nodes": int(len(rp) - 1), "labelled": int(lab.sum()),
+                    "t_min": a.t_min, "t_max": a.t_max, "budget": a.budget, "candidates": a.candidates,
+                    "seed": a.data_seed, "seconds": round(t_data, 1)},
+        "training": {"epochs": a.epochs, "batch_graphs": a.batch, "lr": a.lr, "seed": a.seed,
+                     "seconds": round(t_train, 2), "loss_init": L0, "loss_final": L1,
+                     "loss_per_epoch": [round(float(v), 5) for v in hist]},
+    }
+    with open(os.path.splitext(a.out)[0] + ".json", "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps({k: v for k, v in rec["training"].items() if k != "loss_per_epoch"}))
+
+
+if __name__ == "__main__":
+    main()
