@@ -257,18 +257,30 @@ __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict
   if (i < n) w[i] = __float2bfloat16_rn(p[i]);
 }
 
+// Adam constants for step t (beta1 0.9, beta2 0.999, eps 1e-8): the
+// complements 1 - beta and the bias corrections 1 - beta^t are formed in
+// double and rounded once (1 - 0.999f in float would be 1.3e-5 off 0.001).
+struct AdamConsts {
+  float b1, omb1, b2, omb2, eps, bc1, bc2;
+};
+
+AdamConsts adam_consts(int step) {
+  const double b1 = 0.9, b2 = 0.999;
+  return {(float)b1, (float)(1.0 - b1), (float)b2, (float)(1.0 - b2), 1e-8f,
+          (float)(1.0 - std::pow(b1, (double)step)), (float)(1.0 - std::pow(b2, (double)step))};
+}
+
 // Adam (Kingma and Ba, 2015) on the FP32 master copy; refreshes the BF16 copy.
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                       float* __restrict__ v, __nv_bfloat16* __restrict__ w, int n, float lr, float b1,
-                       float b2, float eps, float bc1, float bc2) {
+                       float* __restrict__ v, __nv_bfloat16* __restrict__ w, int n, float lr, AdamConsts k) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float gi = g[i];
-  const float mi = b1 * m[i] + (1.f - b1) * gi;
-  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  const float mi = k.b1 * m[i] + k.omb1 * gi;
+  const float vi = k.b2 * v[i] + k.omb2 * gi * gi;
   m[i] = mi;
   v[i] = vi;
-  const float pi = p[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  const float pi = p[i] - lr * (mi / k.bc1) / (sqrtf(vi / k.bc2) + k.eps);
   p[i] = pi;
   w[i] = __float2bfloat16_rn(pi);
 }
@@ -539,10 +551,8 @@ void adam_step(float* params, const float* grad, float* m, float* v, int n, int 
   CN_CK(cudaMemcpyAsync(net.G.p, grad, by, cudaMemcpyHostToDevice, net.st));
   CN_CK(cudaMemcpyAsync(net.Mo.p, m, by, cudaMemcpyHostToDevice, net.st));
   CN_CK(cudaMemcpyAsync(net.Vo.p, v, by, cudaMemcpyHostToDevice, net.st));
-  const float b1 = 0.9f, b2 = 0.999f;
-  k_adam<<<(NPARAM + 255) / 256, 256, 0, net.st>>>(net.P.p, net.G.p, net.Mo.p, net.Vo.p, net.Wb.p, NPARAM, lr, b1,
-                                                   b2, 1e-8f, 1.0f - std::pow(b1, (float)step),
-                                                   1.0f - std::pow(b2, (float)step));
+  k_adam<<<(NPARAM + 255) / 256, 256, 0, net.st>>>(net.P.p, net.G.p, net.Mo.p, net.Vo.p, net.Wb.p, NPARAM, lr,
+                                                   adam_consts(step));
   CN_CK(cudaGetLastError());
   CN_CK(cudaMemcpyAsync(params, net.P.p, by, cudaMemcpyDeviceToHost, net.st));
   CN_CK(cudaMemcpyAsync(m, net.Mo.p, by, cudaMemcpyDeviceToHost, net.st));
@@ -579,7 +589,6 @@ void train(const Batch& b, int epochs, int batch_graphs, float lr, uint64_t seed
     return z ^ (z >> 31);
   };
   std::vector<float> gl((size_t)G);
-  const float b1 = 0.9f, b2 = 0.999f;
   int step = 0;
   for (int ep = 0; ep < epochs; ++ep) {
     for (size_t i = order.size(); i > 1; --i) std::swap(order[i - 1], order[(size_t)(rnd() % i)]);
@@ -590,8 +599,7 @@ void train(const Batch& b, int epochs, int batch_graphs, float lr, uint64_t seed
       net.backward(g0, g1, n0, n1, invg[(size_t)bi]);
       ++step;
       k_adam<<<(NPARAM + 255) / 256, 256, 0, net.st>>>(net.P.p, net.G.p, net.Mo.p, net.Vo.p, net.Wb.p, NPARAM, lr,
-                                                       b1, b2, 1e-8f, 1.0f - std::pow(b1, (float)step),
-                                                       1.0f - std::pow(b2, (float)step));
+                                                       adam_consts(step));
       CN_CK(cudaGetLastError());
     }
     CN_CK(cudaMemcpyAsync(gl.data(), net.gl.p, (size_t)G * sizeof(float), cudaMemcpyDeviceToHost, net.st));

@@ -52,10 +52,16 @@ def test_loss_grad_matches_oracle(seed, n_graphs):
     L, g = T.tsim_cut_loss_grad(p, x, rp, col, y, go)
     Lo, go_ = O.loss_grad(p, x, rp, col, y, go)
     assert L == pytest.approx(Lo, rel=1e-4)
+    # a block whose exact gradient is (near) zero is held to a floor scaled by
+    # the whole gradient: the output bias b_o has gradient exactly 0, since the
+    # per-graph centred loss does not change when every score shifts by b_o
+    floor = 1e-6 * np.linalg.norm(go_)
     for name, a, b in BLOCKS:
         ref = go_[a:b]
         err = np.linalg.norm(g[a:b] - ref)
-        assert err <= 1e-4 * (np.linalg.norm(ref) + 1e-12), name
+        assert err <= 1e-4 * np.linalg.norm(ref) + floor, name
+    assert abs(go_[O.OFF_WO + O.H]) <= 1e-12 * np.linalg.norm(go_)
+    assert abs(g[O.OFF_WO + O.H]) <= floor
     assert np.abs(g - go_).max() <= 1e-2 * np.abs(go_).max()
 
 
@@ -65,9 +71,17 @@ def test_adam_step_matches_oracle():
     m, v = random_params(32, n, 0.01), np.abs(random_params(33, n, 0.01))
     p1, m1, v1 = T.tsim_cut_adam_step(p, g, m, v, 7, 1e-3)
     p2, m2, v2 = O.adam_step(p, g, m, v, 7, 1e-3)
-    np.testing.assert_allclose(m1, m2, rtol=1e-6, atol=1e-9)
-    np.testing.assert_allclose(v1, v2, rtol=1e-6, atol=1e-12)
-    np.testing.assert_allclose(p1 - p, p2 - p, rtol=1e-4, atol=1e-7)
+    # float32 moments: the constants 0.9, 0.1, 0.999, 0.001 and each product
+    # and sum round at 2^-24 relative to its summands, and the two summands
+    # can cancel, so the bound scales with them rather than with the result
+    eps = np.finfo(np.float32).eps
+    g64, m64, v64 = (np.asarray(a, np.float64) for a in (g, m, v))
+    assert (np.abs(m1 - m2) <= 4 * eps * (0.9 * np.abs(m64) + 0.1 * np.abs(g64)) + 1e-30).all()
+    assert (np.abs(v1 - v2) <= 4 * eps * (0.999 * v64 + 0.001 * g64 * g64) + 1e-30).all()
+    # the kernel returns float32 parameters: beyond the step's own relative
+    # error, each updated value carries its rounding to float32, half an ulp
+    err = np.abs(p1.astype(np.float64) - p2)
+    assert (err <= 1e-4 * np.abs(p2 - p) + 0.5 * np.finfo(np.float32).eps * np.abs(p2) + 1e-30).all()
 
 
 @pytest.fixture(scope="module")
