@@ -235,6 +235,32 @@ tsim_status tsim_measure_int_peak(int op, double* ops_per_s);
  * over those classes, out[2] = distinct factor parities. */
 tsim_status tsim_program_device_table_stats(const tsim_program* prog, int t, uint64_t out[3]);
 
+/* Device table layout.  Every marginal table is packed for the GPU in one
+ * of three layouts: 0 = SCALAR (one thread per shot; the table's distinct
+ * factor parities (Eq. parities) are evaluated once per shot and indexed per
+ * factor), 1 = BASIS (as SCALAR, with parities given by their coordinates in
+ * a GF(2) basis of their span, for tables with many distinct parities),
+ * 2 = SLICED (warp-cooperative and bit-sliced: a warp evaluates 32 shots at
+ * once, bit s of a 32-bit word belonging to shot s; lane l of the warp carries
+ * term l of a batch of 32 terms, and each factor of Table "Types of
+ * parameterized phase terms" acts as one or two word operations on the term's
+ * phase exponent J mod 8 and its vanishing flag).  SLICED applies to tables
+ * whose terms are monomials of shot-independent magnitude (Node, phase and
+ * pi-pair factors at Clifford angles).  All layouts give identical records.
+ *
+ * tsim_program_set_table_layout re-packs the program: tables with at least
+ * sliced_min_terms terms (after merging terms with equal factor lists) use
+ * SLICED when they qualify; sliced_min_terms < 0 disables SLICED.  The
+ * default at compile / load time is 64.  It frees the program's uploaded
+ * device copy, so it must not be called while a launch of the program is in
+ * flight or while a batch created from it (tsim_batch_create) exists.
+ *
+ * tsim_program_device_table_layout: out[0] = layout of table t, out[1] =
+ * batches of 32 terms, out[2] = padded operation rows over those batches,
+ * out[3] = operations before padding (out[1..3] are 0 unless SLICED). */
+tsim_status tsim_program_set_table_layout(tsim_program* prog, int64_t sliced_min_terms);
+tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[4]);
+
 /* Self-check of the compiler's rewrite rules against brute-force summation on
  * random small parameterised graphs (no GPU).  Returns TSIM_OK when all pass. */
 tsim_status tsim_selftest_rules(uint64_t seed, int iterations);

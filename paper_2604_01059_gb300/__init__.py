@@ -19,7 +19,7 @@ __all__ = [
     "tsim_batch_launch", "tsim_batch_info", "tsim_batch_free", "tsim_sync", "tsim_eval_table",
     "tsim_raw_to_x", "tsim_program_save", "tsim_program_load", "tsim_program_free",
     "tsim_last_error", "tsim_selftest_rules", "tsim_measure_int_peak", "tsim_program_device_table_stats",
-    "load_library",
+    "tsim_program_set_table_layout", "tsim_program_device_table_layout", "load_library",
     "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T",
 ]
 
@@ -98,6 +98,8 @@ def load_library(path: str | None = None):
     L.tsim_selftest_rules.argtypes = [u64, i32]
     L.tsim_measure_int_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
     L.tsim_program_device_table_stats.argtypes = [vp, i32, ctypes.POINTER(u64)]
+    L.tsim_program_set_table_layout.argtypes = [vp, i64]
+    L.tsim_program_device_table_layout.argtypes = [vp, i32, ctypes.POINTER(u64)]
     L.tsim_cut_num_params.argtypes = []
     L.tsim_cut_init_params.argtypes = [u64, vp]
     L.tsim_cut_dataset.argtypes = [u64, i32, i32, i32, u64, i32, ctypes.c_char_p]
@@ -111,7 +113,8 @@ def load_library(path: str | None = None):
               "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_batch_create",
               "tsim_batch_launch", "tsim_batch_info", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
               "tsim_program_save", "tsim_program_load", "tsim_selftest_rules", "tsim_measure_int_peak",
-              "tsim_program_device_table_stats", "tsim_cut_num_params", "tsim_cut_init_params",
+              "tsim_program_device_table_stats", "tsim_program_set_table_layout",
+              "tsim_program_device_table_layout", "tsim_cut_num_params", "tsim_cut_init_params",
               "tsim_cut_dataset", "tsim_cut_forward", "tsim_cut_loss_grad", "tsim_cut_adam_step", "tsim_cut_train",
               "tsim_cut_model_set", "tsim_cut_policy_stats"):
         getattr(L, n).restype = ctypes.c_int
@@ -279,6 +282,22 @@ def tsim_program_device_table_stats(h, t):
     return tuple(out)
 
 
+TABLE_SCALAR, TABLE_BASIS, TABLE_SLICED = 0, 1, 2
+
+
+def tsim_program_set_table_layout(h, sliced_min_terms):
+    """Re-pack the device tables: tables with at least sliced_min_terms terms
+    use the bit-sliced warp layout where they qualify (< 0: never)."""
+    _check(load_library().tsim_program_set_table_layout(h, int(sliced_min_terms)))
+
+
+def tsim_program_device_table_layout(h, t):
+    """(layout, batches of 32 terms, padded operation rows, operations) of table t."""
+    out = (ctypes.c_uint64 * 4)()
+    _check(load_library().tsim_program_device_table_layout(h, t, out))
+    return tuple(out)
+
+
 def tsim_selftest_rules(seed=0, iterations=200):
     _check(load_library().tsim_selftest_rules(seed, iterations))
 
@@ -428,6 +447,13 @@ class Program:
 
     def device_table_stats(self, t):
         return tsim_program_device_table_stats(self.h, t)
+
+    def set_table_layout(self, sliced_min_terms):
+        tsim_program_set_table_layout(self.h, sliced_min_terms)
+        self.info = tsim_program_info(self.h)
+
+    def device_table_layout(self, t):
+        return tsim_program_device_table_layout(self.h, t)
 
     def table_terms(self):
         return [tsim_program_table_terms(self.h, t) for t in range(self.info["num_tables"])]

@@ -133,6 +133,29 @@ tsim_status tsim_program_device_table_stats(const tsim_program* prog, int t, uin
   });
 }
 
+tsim_status tsim_program_set_table_layout(tsim_program* prog, int64_t sliced_min_terms) {
+  return guard([&] {
+    tsim::Program& p = const_cast<tsim::Program&>(prog_of(prog));
+    tsim::device_release(p.dev);  // the uploaded copy of the old layout
+    p.dev = nullptr;
+    tsim::prepare_device_tables(p, sliced_min_terms);
+    if (p.devtab->status != TSIM_OK) tsim::fail(p.devtab->status, p.devtab->message);
+  });
+}
+
+tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[4]) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!out || t < 0 || t >= (int)p.tables.size()) tsim::fail(TSIM_ERR_ARG, "bad table index");
+    if (!p.devtab || p.devtab->status != TSIM_OK) tsim::fail(TSIM_ERR_ARG, "program has no device tables");
+    const auto& L = p.devtab->layout;
+    out[0] = L.table_mode[(size_t)t];
+    out[1] = L.table_batches[(size_t)t];
+    out[2] = L.table_rows[(size_t)t];
+    out[3] = L.table_ops[(size_t)t];
+  });
+}
+
 tsim_status tsim_sample(const tsim_program* prog, uint64_t shots, uint64_t seed, uint64_t shot_offset,
                         uint64_t* d_meas, uint64_t* d_det, uint64_t* d_obs, uint8_t* d_accept,
                         void* cuda_stream) {

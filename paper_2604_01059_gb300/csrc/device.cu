@@ -25,6 +25,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 
@@ -53,8 +54,37 @@ enum : int { OUT_MASK = 0, OUT_BIT = 1, OUT_RANDOM = 2 };
 
 struct DChan { uint32_t n_out, thr_off, sig_off, thr0; };
 struct DOut { int32_t kind, cst, a, chain, table, pad; };
-struct DTable { uint32_t par_off, n_par, cls_off, n_cls; int32_t base, basis, pad1, pad2; };
+// Table layouts: SCALAR = distinct parities indexed per factor (one thread
+// per shot), BASIS = parities as coordinates in a GF(2) basis of their span,
+// SLICED = warp-cooperative bit-sliced evaluation (below).
+enum : int { TAB_SCALAR = 0, TAB_BASIS = 1, TAB_SLICED = 2 };
+struct DTable { uint32_t par_off, n_par, cls_off, n_cls; int32_t base, mode, sb_off, n_sb; };
 struct DClass { uint32_t fac_off, n_fac; int32_t mono, j0, d0, pad; long long c[4]; };
+
+// Bit-sliced tables.  A warp evaluates 32 shots at once: bit s of every
+// 32-bit word below belongs to shot (lane) s.  Per table the warp forms the
+// words Par[q] of all distinct factor parities q (Eq. parities), then walks
+// the terms in batches of 32, lane l carrying term l of the batch.  Every
+// factor of a Clifford term whose value is a monomial of fixed magnitude
+// reduces to operations on the term's phase exponent J (mod 8, three bit
+// planes J0 J1 J2) and vanishing flag Z:
+enum : int {
+  SL_XOR4 = 0,   // J += 4a          (a sign (-1)^a)
+  SL_ADD2 = 1,   // J += 2a          (i^a)
+  SL_ADD6 = 2,   // J += 6a          ((-i)^a)
+  SL_XOR4AB = 3, // J += 4ab         (pi-pair (-1)^(ab)); row = qa | qb << 16
+  SL_ZERO = 4,   // vanishes if a = 1 (Node 1 + (-1)^a)
+  SL_ZEROC = 5,  // vanishes if a = 0 (Node 1 - (-1)^a)
+  SL_ADD1 = 6,   // J += a           (w^a, odd phase)
+  kSlCodes = 7
+};
+constexpr uint32_t kSlOnes = 1;        // parity index whose word is all ones
+constexpr int kSlMaxPar = 16384;       // distinct parities of one sliced table
+// One batch of 32 terms: rows of operation code c are cnt[c] x 32 parity
+// indices (lane-interleaved, padded with no-op indices), starting at row_off.
+// All terms of a batch share the magnitude sqrt2^d; j0m[b] holds bit b of
+// each lane's constant phase; valid marks lanes that carry a term.
+struct DSBatch { uint32_t row_off; uint16_t cnt[8]; int32_t d; uint32_t j0m[3]; uint32_t valid; };
 
 struct DevView {
   int W;
@@ -72,6 +102,9 @@ struct DevView {
   const uint32_t* fidx;   // per factor: parity index of a | parity index of b << 8
   const uint32_t* finc;   // per factor: 4 packed increments
   const uint64_t* fcoord; // basis tables: per factor the coordinates of a and b (2 words)
+  const DSBatch* sb;      // sliced tables: batches
+  const uint32_t* rows;   // sliced tables: operation rows
+  int sl_words;           // 32-bit shared-memory words one warp needs (0: no sliced table)
   const int32_t* dmap_off;
   const int32_t* dmap_idx;
   const int32_t* omap_off;
@@ -252,12 +285,146 @@ __device__ __forceinline__ void accumulate(const DClass& C, uint32_t acc, long l
   }
 }
 
+// 32 x 32 bit-matrix transpose across the warp: on entry lane r holds row r
+// (bit c = column c), on exit lane c holds column c (bit r = row r).  Five
+// stages exchange the off-diagonal blocks of size 16, 8, 4, 2, 1.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
+  const uint32_t keep[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int j = 16 >> st;
+    const uint32_t m = keep[st];  // bit positions c with (c & j) == 0
+    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
+    x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+  }
+  return x;
+}
+
+// Warp-cooperative exact value of a sliced table for the 32 shots of the
+// warp (every lane must call it; lane s receives shot s's value).
+// sm: this warp's shared words, 64 W for the transposed X, then Par.
 template <int W>
-__device__ ZC eval_table(const DevView& V, int t, const uint64_t (&X)[W]) {
-  const DTable tb = V.tab[t];
+__device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64_t (&X)[W], uint32_t* sm) {
+  const int lane = threadIdx.x & 31;
+  uint32_t* Xs = sm;           // Xs[i]: bit s = bit i of shot s's X
+  uint32_t* Par = sm + 64 * W; // Par[q]: bit s = parity q of shot s
+  __syncwarp();
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    Xs[64 * w + lane] = transpose32((uint32_t)X[w], lane);
+    Xs[64 * w + 32 + lane] = transpose32((uint32_t)(X[w] >> 32), lane);
+  }
+  __syncwarp();
+  // every distinct parity as the XOR of the X bits in its mask, 32 shots at once
+  // (masks have V.W <= W words; a batched launch may run with a larger W)
+  const int ws = V.W;
+  const uint64_t* pm = V.par + (size_t)tb.par_off * ws;
+  for (uint32_t q = lane; q < tb.n_par; q += 32) {
+    uint32_t acc = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      uint64_t m = w < ws ? __ldg(pm + (size_t)q * ws + w) : 0ull;
+      while (m) {
+        acc ^= Xs[64 * w + (__ffsll((long long)m) - 1)];
+        m &= m - 1;
+      }
+    }
+    Par[q] = q == kSlOnes ? 0xFFFFFFFFu : acc;
+  }
+  __syncwarp();
   ZC z{{0, 0, 0, 0}, tb.base};
   long long (&c)[4] = z.c;
-  if (tb.basis) {
+  const DSBatch* bt = V.sb + tb.sb_off;
+  for (int b = 0; b < tb.n_sb; ++b) {
+    const DSBatch B = bt[b];
+    const uint32_t* R = V.rows + B.row_off + lane;
+    uint32_t J0 = 0u - ((B.j0m[0] >> lane) & 1u);
+    uint32_t J1 = 0u - ((B.j0m[1] >> lane) & 1u);
+    uint32_t J2 = 0u - ((B.j0m[2] >> lane) & 1u);
+    uint32_t Z = 0u - ((~B.valid >> lane) & 1u);
+    uint32_t K2 = 0, K2b = 0, Zb = 0;  // J2 flips and vanishing flags commute with the additions
+    {
+      const int n = B.cnt[SL_XOR4];
+      int k = 0;
+      for (; k + 1 < n; k += 2, R += 64) {
+        K2 ^= Par[__ldg(R)];
+        K2b ^= Par[__ldg(R + 32)];
+      }
+      if (k < n) { K2 ^= Par[__ldg(R)]; R += 32; }
+    }
+    for (int k = 0; k < B.cnt[SL_ADD2]; ++k, R += 32) {
+      const uint32_t A = Par[__ldg(R)];
+      J2 ^= J1 & A;
+      J1 ^= A;
+    }
+    for (int k = 0; k < B.cnt[SL_ADD6]; ++k, R += 32) {
+      const uint32_t A = Par[__ldg(R)];
+      J2 ^= ~J1 & A;
+      J1 ^= A;
+    }
+    {
+      const int n = B.cnt[SL_XOR4AB];
+      int k = 0;
+      for (; k + 1 < n; k += 2, R += 64) {
+        const uint32_t r0 = __ldg(R), r1 = __ldg(R + 32);
+        K2 ^= Par[r0 & 0xFFFFu] & Par[r0 >> 16];
+        K2b ^= Par[r1 & 0xFFFFu] & Par[r1 >> 16];
+      }
+      if (k < n) {
+        const uint32_t r0 = __ldg(R);
+        K2 ^= Par[r0 & 0xFFFFu] & Par[r0 >> 16];
+        R += 32;
+      }
+    }
+    {
+      const int n = B.cnt[SL_ZERO];
+      int k = 0;
+      for (; k + 1 < n; k += 2, R += 64) {
+        Z |= Par[__ldg(R)];
+        Zb |= Par[__ldg(R + 32)];
+      }
+      if (k < n) { Z |= Par[__ldg(R)]; R += 32; }
+    }
+    for (int k = 0; k < B.cnt[SL_ZEROC]; ++k, R += 32) Z |= ~Par[__ldg(R)];
+    for (int k = 0; k < B.cnt[SL_ADD1]; ++k, R += 32) {
+      const uint32_t A = Par[__ldg(R)];
+      const uint32_t cy = J0 & A;
+      J0 ^= A;
+      J2 ^= J1 & cy;
+      J1 ^= cy;
+    }
+    J2 ^= K2 ^ K2b;
+    Z |= Zb;
+    // lane s now needs, for each of the 32 terms, its phase and flag at shot s
+    const uint32_t T0 = transpose32(J0, lane), T1 = transpose32(J1, lane);
+    const uint32_t T2 = transpose32(J2, lane), TZ = transpose32(Z, lane);
+    const uint32_t nz = ~TZ;
+    const uint32_t M[4] = {~T0 & ~T1 & nz, T0 & ~T1 & nz, ~T0 & T1 & nz, T0 & T1 & nz};
+    long long r[4];
+    const int sh = B.d >> 1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)  // terms with J = q count +1, with J = q + 4 count -1
+      r[q] = (long long)(__popc(M[q]) - 2 * __popc(M[q] & T2)) << sh;
+    if (B.d & 1) {  // times sqrt2 = w - w^3
+      c[0] += r[1] - r[3];
+      c[1] += r[0] + r[2];
+      c[2] += r[1] + r[3];
+      c[3] += r[2] - r[0];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c[q] += r[q];
+    }
+  }
+  return z;
+}
+
+template <int W>
+__device__ ZC eval_table(const DevView& V, int t, const uint64_t (&X)[W], uint32_t* sm) {
+  const DTable tb = V.tab[t];
+  if (tb.mode == TAB_SLICED) return eval_table_sliced<W>(V, tb, X, sm);
+  ZC z{{0, 0, 0, 0}, tb.base};
+  long long (&c)[4] = z.c;
+  if (tb.mode == TAB_BASIS) {
     // parities in a GF(2) basis of the table's mask span: Y holds the basis
     // parities and every factor parity is <coordinates, Y>
     uint64_t Y = 0;
@@ -339,10 +506,13 @@ __device__ __forceinline__ int get_xbit(const uint64_t (&X)[W], int b) {
 }
 
 // One shot s of a launch (global shot index shot0 + s), records at row s.
+// Every lane of a warp calls it together (sliced tables are evaluated by the
+// whole warp); lanes past the end of the launch have valid = false and
+// compute a shot whose records are not written.  sm: the warp's shared words.
 template <int W>
-__device__ void sample_one(const DevView& V, uint64_t s, uint64_t seed, uint64_t shot0,
+__device__ void sample_one(const DevView& V, uint64_t s, bool valid, uint64_t seed, uint64_t shot0,
                            uint64_t* __restrict__ meas, uint64_t* __restrict__ det,
-                           uint64_t* __restrict__ obs, uint8_t* __restrict__ accept) {
+                           uint64_t* __restrict__ obs, uint8_t* __restrict__ accept, uint32_t* sm) {
   const uint64_t shot = shot0 + s;
   RoundKeys rk;
   {
@@ -387,7 +557,7 @@ __device__ void sample_one(const DevView& V, uint64_t s, uint64_t seed, uint64_t
   RV pp[kMaxChains];
   int rot[kMaxChains];
   for (int c = 0; c < V.n_chains; ++c) {
-    const ZC z = eval_table<W>(V, V.chain_norm[c], X);
+    const ZC z = eval_table<W>(V, V.chain_norm[c], X, sm);
     rot[c] = chain_rotation(z, &st);
     pp[c] = to_real_rot(z, rot[c], &st);
   }
@@ -404,7 +574,7 @@ __device__ void sample_one(const DevView& V, uint64_t s, uint64_t seed, uint64_t
       bit = parity_w<W>(V.omask + o.a, X, V.W) ^ o.cst;
     } else {
       set_xbit<W>(X, o.a, true);
-      const RV p1 = to_real_rot(eval_table<W>(V, o.table, X), rot[o.chain], &st);
+      const RV p1 = to_real_rot(eval_table<W>(V, o.table, X, sm), rot[o.chain], &st);
       const RV pv = pp[o.chain];
       if (sign_xy(pv.A, pv.B, &st) <= 0) st |= ST_ZERO_PROB;
       uint32_t u[4];
@@ -438,8 +608,8 @@ __device__ void sample_one(const DevView& V, uint64_t s, uint64_t seed, uint64_t
       if ((j & 63) == 63 || last) {
         if (is_det) {
           any_det |= cur != 0;
-          if (det) det[s * dw + (j >> 6)] = cur;
-        } else if (obs) {
+          if (det && valid) det[s * dw + (j >> 6)] = cur;
+        } else if (obs && valid) {
           obs[s * ow + (j >> 6)] = cur;
         }
         cur = 0;
@@ -452,7 +622,7 @@ __device__ void sample_one(const DevView& V, uint64_t s, uint64_t seed, uint64_t
 
   // 4. measurement-mode records
   if (V.mode != 0) {
-    if (meas)
+    if (meas && valid)
       for (int w = 0; w < mw; ++w) meas[s * mw + w] = ob[w];
     for (int w = 0; w < dw; ++w) {
       uint64_t v = 0;
@@ -466,9 +636,9 @@ __device__ void sample_one(const DevView& V, uint64_t s, uint64_t seed, uint64_t
         v |= (uint64_t)x << b;
       }
       any_det |= v != 0;
-      if (det) det[s * dw + w] = v;
+      if (det && valid) det[s * dw + w] = v;
     }
-    if (obs)
+    if (obs && valid)
       for (int w = 0; w < ow; ++w) {
         uint64_t v = 0;
         for (int b = 0; b < 64 && 64 * w + b < V.nobs; ++b) {
@@ -483,9 +653,13 @@ __device__ void sample_one(const DevView& V, uint64_t s, uint64_t seed, uint64_t
         obs[s * ow + w] = v;
       }
   }
+  if (!valid) return;
   if (accept) accept[s] = any_det ? 0 : 1;
   if (st) atomicOr(&g_status, st);
 }
+
+// dynamic shared memory: sl_words per warp for programs with sliced tables
+extern __shared__ uint32_t g_warp_smem[];
 
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, uint64_t shot0,
@@ -494,7 +668,8 @@ __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, u
                                                      uint64_t* __restrict__ obs,
                                                      uint8_t* __restrict__ accept) {
   const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < nshots) sample_one<W>(V, s, seed, shot0, meas, det, obs, accept);
+  uint32_t* sm = g_warp_smem + (threadIdx.x >> 5) * V.sl_words;
+  sample_one<W>(V, s, s < nshots, seed, shot0, meas, det, obs, accept, sm);
 }
 
 // ------------------------------------------------------- batched launch
@@ -515,8 +690,9 @@ template <int W>
 __global__ void __launch_bounds__(kThreads) k_batch(const BatchProg* __restrict__ progs, int n,
                                                     const uint64_t* __restrict__ item_start,
                                                     uint64_t total_items, uint32_t sb,
-                                                    unsigned long long* counter) {
+                                                    unsigned long long* counter, int sl_stride) {
   __shared__ unsigned long long item;
+  uint32_t* sm = g_warp_smem + (threadIdx.x >> 5) * sl_stride;
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(counter, 1ull);
     __syncthreads();
@@ -532,8 +708,10 @@ __global__ void __launch_bounds__(kThreads) k_batch(const BatchProg* __restrict_
     const BatchProg& P = progs[lo];
     const uint64_t first = (it - item_start[lo]) * sb;
     const uint64_t last = min(first + sb, P.shots);
-    for (uint64_t s = first + threadIdx.x; s < last; s += blockDim.x)
-      sample_one<W>(P.v, s, P.seed, P.shot_offset, P.meas, P.det, P.obs, P.accept);
+    for (uint64_t s0 = first; s0 < last; s0 += blockDim.x) {
+      const uint64_t s = s0 + threadIdx.x;
+      sample_one<W>(P.v, s, s < last, P.seed, P.shot_offset, P.meas, P.det, P.obs, P.accept, sm);
+    }
   }
 }
 
@@ -603,7 +781,147 @@ struct Lut {
   int smin, spread;
 };
 
-void pack(const Program& p, DeviceTables& out) {
+struct FacKey {
+  int kind, alpha, beta, ia, ib;
+  bool operator<(const FacKey& o) const {
+    return std::tie(kind, alpha, beta, ia, ib) < std::tie(o.kind, o.alpha, o.beta, o.ia, o.ib);
+  }
+  bool operator==(const FacKey& o) const {
+    return kind == o.kind && alpha == o.alpha && beta == o.beta && ia == o.ia && ib == o.ib;
+  }
+};
+
+// A term of a sliced table: constant phase j, magnitude exponent d, and the
+// parity indices of each operation code (sorted); dead terms vanish for
+// every shot.
+struct SlTerm {
+  int d = 0, j = 0;
+  bool dead = false;
+  std::vector<uint32_t> ops[kSlCodes];
+};
+
+// How one factor acts on (J, Z): J += j00 + da a + db b + dab ab (mod 8) on
+// the (a, b) where it does not vanish, and the vanishing condition zop
+// (0 never, 1 a = 1, 2 a = 0, 3 b = 1, 4 b = 0).  za / zb: a / b is the zero
+// parity; same: a and b are the same parity.
+struct SlDec {
+  bool ok = false, dead = false;
+  int j00 = 0, da = 0, db = 0, dab = 0, zop = 0;
+};
+
+SlDec sliced_decompose(const Lut& l, bool za, bool zb, bool same) {
+  SlDec r;
+  if (l.spread != 0) return r;  // magnitude depends on the shot
+  bool reach[2][2], zero[2][2];
+  int jv[2][2];
+  int nreach = 0, nzero = 0;
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      reach[a][b] = (!za || a == 0) && (!zb || b == 0) && (!same || a == b);
+      const uint32_t inc = l.inc[a | (b << 1)];
+      zero[a][b] = (inc >> 21) != 0;
+      jv[a][b] = (int)(inc & 0x7FF) & 7;
+      nreach += reach[a][b];
+      nzero += reach[a][b] && zero[a][b];
+    }
+  r.ok = true;
+  if (nzero == nreach) { r.dead = true; return r; }
+  if (nzero) {
+    auto fits = [&](int op) {
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          if (!reach[a][b]) continue;
+          const bool want = op == 1 ? a == 1 : op == 2 ? a == 0 : op == 3 ? b == 1 : b == 0;
+          if (zero[a][b] != want) return false;
+        }
+      return true;
+    };
+    r.zop = 0;
+    for (int op = 1; op <= 4 && !r.zop; ++op) {
+      if ((op <= 2 && za) || (op >= 3 && zb)) continue;
+      if (fits(op)) r.zop = op;
+    }
+    if (!r.zop) { r.ok = false; return r; }
+  }
+  // fewest nonzero increments that reproduce J on the non-vanishing entries
+  int best = 99;
+  for (int dab = 0; dab <= 4; dab += 4)
+    for (int da = 0; da < 8; ++da)
+      for (int db = 0; db < 8; ++db)
+        for (int j00 = 0; j00 < 8; ++j00) {
+          if (za && (da || dab)) continue;           // a is always 0
+          if (zb && (db || dab)) continue;           // b is always 0
+          if (same && (db || dab)) continue;         // a = b: all of it in da
+          bool ok = true;
+          for (int a = 0; a < 2 && ok; ++a)
+            for (int b = 0; b < 2 && ok; ++b)
+              if (reach[a][b] && !zero[a][b]) ok = ((j00 + da * a + db * b + dab * a * b) & 7) == jv[a][b];
+          const int cost = (da != 0) + (db != 0) + (dab != 0);
+          if (ok && cost < best) {
+            best = cost;
+            r.j00 = j00;
+            r.da = da;
+            r.db = db;
+            r.dab = dab;
+          }
+        }
+  if (best == 99) r.ok = false;
+  return r;
+}
+
+// Sliced form of one term (factor list f, coefficient phase j, magnitude
+// exponent d); false when some factor has no such form.
+template <class LutFn>
+bool sliced_term(const std::vector<FacKey>& f, int j, int d, LutFn& lut, SlTerm& t) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, SlDec> cache;
+  t.d = d;
+  int jc = j;
+  std::map<uint32_t, int> delta;
+  std::set<uint32_t> pairs, zp, zn;
+  for (const FacKey& k : f) {
+    const uint32_t qa = k.ia ? (uint32_t)k.ia + 1 : 0u, qb = k.ib ? (uint32_t)k.ib + 1 : 0u;
+    const bool za = qa == 0, zb = qb == 0, same = qa != 0 && qa == qb;
+    const int flags = (int)za | ((int)zb << 1) | ((int)same << 2);
+    SlDec dec;
+    {
+      const auto key = std::make_tuple(k.kind, k.alpha & 7, k.beta & 7, flags);
+      std::lock_guard<std::mutex> g(mu);
+      auto it = cache.find(key);
+      if (it == cache.end()) it = cache.emplace(key, sliced_decompose(lut(k.kind, k.alpha, k.beta), za, zb, same)).first;
+      dec = it->second;
+    }
+    if (!dec.ok) return false;
+    if (dec.dead) { t.dead = true; return true; }
+    jc += dec.j00;
+    if (dec.da) delta[qa] = (delta[qa] + dec.da) & 7;
+    if (dec.db) delta[qb] = (delta[qb] + dec.db) & 7;
+    if (dec.dab) {
+      const uint32_t key = std::min(qa, qb) | (std::max(qa, qb) << 16);
+      if (!pairs.erase(key)) pairs.insert(key);  // (-1)^(ab) twice is 1
+    }
+    if (dec.zop == 1) zp.insert(qa);
+    if (dec.zop == 2) zn.insert(qa);
+    if (dec.zop == 3) zp.insert(qb);
+    if (dec.zop == 4) zn.insert(qb);
+  }
+  for (uint32_t q : zp)
+    if (zn.count(q)) { t.dead = true; return true; }
+  t.j = jc & 7;
+  for (const auto& [q, dl] : delta) {
+    if (dl & 1) t.ops[SL_ADD1].push_back(q);
+    const int rem = dl & 6;
+    if (rem == 2) t.ops[SL_ADD2].push_back(q);
+    if (rem == 4) t.ops[SL_XOR4].push_back(q);
+    if (rem == 6) t.ops[SL_ADD6].push_back(q);
+  }
+  t.ops[SL_XOR4AB].assign(pairs.begin(), pairs.end());
+  t.ops[SL_ZERO].assign(zp.begin(), zp.end());
+  t.ops[SL_ZEROC].assign(zn.begin(), zn.end());
+  return true;
+}
+
+void pack(const Program& p, DeviceTables& out, int64_t sliced_min) {
   std::map<std::tuple<int, int, int>, Lut> lut_cache;
   auto lut = [&](int kind, int alpha, int beta) -> const Lut& {
     auto key = std::make_tuple(kind, alpha & 7, beta & 7);
@@ -678,15 +996,6 @@ void pack(const Program& p, DeviceTables& out) {
   { int32_t z = 0; s.put(&z, 4); }
 
   // tables: distinct parities, then terms merged into classes with equal factors
-  struct FacKey {
-    int kind, alpha, beta, ia, ib;
-    bool operator<(const FacKey& o) const {
-      return std::tie(kind, alpha, beta, ia, ib) < std::tie(o.kind, o.alpha, o.beta, o.ia, o.ib);
-    }
-    bool operator==(const FacKey& o) const {
-      return kind == o.kind && alpha == o.alpha && beta == o.beta && ia == o.ia && ib == o.ib;
-    }
-  };
   struct Cls {
     std::vector<FacKey> f;
     ZW coef;
@@ -696,6 +1005,8 @@ void pack(const Program& p, DeviceTables& out) {
   std::vector<DClass> cls;
   std::vector<uint32_t> fidx, finc;
   std::vector<uint64_t> fcoord;
+  std::vector<DSBatch> sbs;
+  std::vector<uint32_t> rows;
   for (const ProgTable& tb : p.tables) {
     DTable dt{};
     dt.par_off = (uint32_t)(par.size() / (size_t)W);
@@ -731,41 +1042,6 @@ void pack(const Program& p, DeviceTables& out) {
         cl[it->second].coef = zw_add(cl[it->second].coef, c);
       }
     }
-    // few distinct parities: evaluate each once per shot and index them;
-    // many: evaluate a GF(2) basis of their span and give every parity its
-    // coordinates in that basis
-    std::vector<uint64_t> coords(plist.size(), 0);
-    if (plist.size() <= (size_t)kMaxParities) {
-      for (const auto& m : plist) par.insert(par.end(), m.begin(), m.end());
-      dt.n_par = (uint32_t)plist.size();
-    } else {
-      dt.basis = 1;
-      std::vector<std::vector<uint64_t>> bvec, borig;
-      std::vector<uint64_t> bcomb;
-      std::vector<int> bpiv;
-      for (size_t i = 1; i < plist.size(); ++i) {
-        std::vector<uint64_t> v = plist[i];
-        uint64_t comb = 0;
-        for (size_t j = 0; j < bvec.size(); ++j)
-          if ((v[(size_t)bpiv[j] >> 6] >> (bpiv[j] & 63)) & 1) {
-            for (int w = 0; w < W; ++w) v[(size_t)w] ^= bvec[j][(size_t)w];
-            comb ^= bcomb[j];
-          }
-        int piv = -1;
-        for (int w = 0; w < W && piv < 0; ++w)
-          if (v[(size_t)w]) piv = w * 64 + __builtin_ctzll(v[(size_t)w]);
-        if (piv < 0) { coords[i] = comb; continue; }
-        if (borig.size() >= 64) throw PackError{TSIM_ERR_ARG, "table parities span more than 64 dimensions"};
-        const uint64_t me = 1ull << borig.size();
-        borig.push_back(plist[i]);
-        bvec.push_back(v);
-        bcomb.push_back(comb ^ me);
-        bpiv.push_back(piv);
-        coords[i] = me;
-      }
-      for (const auto& m : borig) par.insert(par.end(), m.begin(), m.end());
-      dt.n_par = (uint32_t)borig.size();
-    }
     // per class: exponent of its smallest possible magnitude
     struct Prep { size_t i; int raw, spread, mono, j, zero; };
     std::vector<Prep> prep;
@@ -792,43 +1068,150 @@ void pack(const Program& p, DeviceTables& out) {
     int base = 0;
     for (size_t q = 0; q < prep.size(); ++q) base = q ? std::min(base, prep[q].raw) : prep[q].raw;
     dt.base = base;
-    dt.cls_off = (uint32_t)cls.size();
     dt.n_cls = (uint32_t)prep.size();
+    // every coefficient of the accumulated sum stays below 2^62 in absolute value
     unsigned __int128 bound = 0;
     for (const Prep& pr : prep) {
       const Cls& c = cl[pr.i];
-      DClass d{};
-      d.fac_off = (uint32_t)fidx.size();
-      d.n_fac = (uint32_t)c.f.size();
-      d.mono = pr.mono;
-      d.j0 = pr.j;
-      d.d0 = pr.raw - base;
       unsigned __int128 mag = 1;
       if (!pr.mono) {
+        mag = 0;
         for (int i = 0; i < 4; ++i) {
           if (c.coef.c[i] > ((__int128)1 << 60) || c.coef.c[i] < -((__int128)1 << 60))
             throw PackError{TSIM_ERR_OVERFLOW_BOUND, "merged term coefficient exceeds 60 bits"};
-          d.c[i] = (long long)c.coef.c[i];
+          mag += (unsigned __int128)(c.coef.c[i] < 0 ? -c.coef.c[i] : c.coef.c[i]);
         }
-        mag = 0;
-        for (int i = 0; i < 4; ++i) mag += (unsigned __int128)(d.c[i] < 0 ? -d.c[i] : d.c[i]);
         mag *= 2;  // the sqrt2 multiplication at most doubles the largest coefficient
       }
-      const int dm = d.d0 + pr.spread;
+      const int dm = pr.raw - base + pr.spread;
       if (dm / 2 + log2_ceil(mag) >= 100) throw PackError{TSIM_ERR_OVERFLOW_BOUND, "table magnitudes exceed 64-bit accumulation"};
       bound += mag << (dm / 2 + 1);
-      for (const FacKey& k : c.f) {
-        const Lut& l = lut(k.kind, k.alpha, k.beta);
-        fidx.push_back(dt.basis ? 0u : ((uint32_t)k.ia | ((uint32_t)k.ib << 8)));
-        finc.insert(finc.end(), l.inc, l.inc + 4);
-        fcoord.push_back(dt.basis ? coords[(size_t)k.ia] : 0);
-        fcoord.push_back(dt.basis ? coords[(size_t)k.ib] : 0);
-        L.class_factors++;
-      }
-      cls.push_back(d);
     }
-    // every coefficient stays below 2^62 in absolute value
     if (bound >= ((unsigned __int128)1 << 62)) throw PackError{TSIM_ERR_OVERFLOW_BOUND, "table magnitudes exceed 64-bit accumulation"};
+
+    // ---- bit-sliced layout (large tables whose factors all reduce to
+    // operations on J and Z, every term a monomial)
+    bool sliced = sliced_min >= 0 && prep.size() >= (size_t)std::max<int64_t>(sliced_min, 1) &&
+                  plist.size() + 1 <= (size_t)kSlMaxPar;
+    std::vector<SlTerm> sterms;
+    for (size_t q = 0; sliced && q < prep.size(); ++q) {
+      const Prep& pr = prep[q];
+      if (!pr.mono) { sliced = false; break; }
+      SlTerm t;
+      if (!sliced_term(cl[pr.i].f, pr.j, pr.raw - base, lut, t)) { sliced = false; break; }
+      if (!t.dead) sterms.push_back(std::move(t));
+    }
+    uint64_t real_ops = 0, padded_rows = 0;
+    if (sliced) {
+      dt.mode = TAB_SLICED;
+      dt.par_off = (uint32_t)(par.size() / (size_t)W);
+      par.insert(par.end(), plist[0].begin(), plist[0].end());  // 0: the zero parity
+      par.insert(par.end(), (size_t)W, 0ull);                   // kSlOnes: all ones (set on the device)
+      for (size_t i = 1; i < plist.size(); ++i) par.insert(par.end(), plist[i].begin(), plist[i].end());
+      dt.n_par = (uint32_t)plist.size() + 1;
+      dt.sb_off = (int32_t)sbs.size();
+      std::stable_sort(sterms.begin(), sterms.end(), [](const SlTerm& a, const SlTerm& b) {
+        if (a.d != b.d) return a.d < b.d;
+        size_t na = 0, nb = 0;
+        for (int c = 0; c < kSlCodes; ++c) { na += a.ops[c].size(); nb += b.ops[c].size(); }
+        if (na != nb) return na > nb;
+        for (int c = 0; c < kSlCodes; ++c)
+          if (a.ops[c].size() != b.ops[c].size()) return a.ops[c].size() > b.ops[c].size();
+        return false;
+      });
+      for (size_t t0 = 0; t0 < sterms.size();) {
+        size_t t1 = t0;
+        while (t1 < sterms.size() && t1 - t0 < 32 && sterms[t1].d == sterms[t0].d) ++t1;
+        DSBatch B{};
+        B.row_off = (uint32_t)rows.size();
+        B.d = sterms[t0].d;
+        for (size_t l = 0; l < t1 - t0; ++l) {
+          const SlTerm& t = sterms[t0 + l];
+          B.valid |= 1u << l;
+          for (int bit = 0; bit < 3; ++bit) B.j0m[bit] |= (uint32_t)((t.j >> bit) & 1) << l;
+        }
+        for (int c = 0; c < kSlCodes; ++c) {
+          size_t n = 0;
+          for (size_t l = t0; l < t1; ++l) n = std::max(n, sterms[l].ops[c].size());
+          if (n > 0xFFFF) throw PackError{TSIM_ERR_ARG, "too many operations of one kind in a term"};
+          B.cnt[c] = (uint16_t)n;
+          for (size_t k = 0; k < n; ++k)
+            for (size_t l = 0; l < 32; ++l) {
+              const size_t ti = t0 + l;
+              uint32_t r = c == SL_ZEROC ? kSlOnes : 0u;  // padding leaves J and Z unchanged
+              if (ti < t1 && k < sterms[ti].ops[c].size()) {
+                r = sterms[ti].ops[c][k];
+                ++real_ops;
+              }
+              rows.push_back(r);
+            }
+          padded_rows += n;
+        }
+        if (rows.size() > 0xFFFFFFFFull) throw PackError{TSIM_ERR_ARG, "sliced tables too large"};
+        sbs.push_back(B);
+        t0 = t1;
+      }
+      dt.n_sb = (int32_t)(sbs.size() - (size_t)dt.sb_off);
+      L.sl_par_max = std::max<uint32_t>(L.sl_par_max, dt.n_par);
+    } else {
+      // few distinct parities: evaluate each once per shot and index them;
+      // many: evaluate a GF(2) basis of their span and give every parity its
+      // coordinates in that basis
+      std::vector<uint64_t> coords(plist.size(), 0);
+      dt.par_off = (uint32_t)(par.size() / (size_t)W);
+      if (plist.size() <= (size_t)kMaxParities) {
+        for (const auto& m : plist) par.insert(par.end(), m.begin(), m.end());
+        dt.n_par = (uint32_t)plist.size();
+      } else {
+        dt.mode = TAB_BASIS;
+        std::vector<std::vector<uint64_t>> bvec, borig;
+        std::vector<uint64_t> bcomb;
+        std::vector<int> bpiv;
+        for (size_t i = 1; i < plist.size(); ++i) {
+          std::vector<uint64_t> v = plist[i];
+          uint64_t comb = 0;
+          for (size_t j = 0; j < bvec.size(); ++j)
+            if ((v[(size_t)bpiv[j] >> 6] >> (bpiv[j] & 63)) & 1) {
+              for (int w = 0; w < W; ++w) v[(size_t)w] ^= bvec[j][(size_t)w];
+              comb ^= bcomb[j];
+            }
+          int piv = -1;
+          for (int w = 0; w < W && piv < 0; ++w)
+            if (v[(size_t)w]) piv = w * 64 + __builtin_ctzll(v[(size_t)w]);
+          if (piv < 0) { coords[i] = comb; continue; }
+          if (borig.size() >= 64) throw PackError{TSIM_ERR_ARG, "table parities span more than 64 dimensions"};
+          const uint64_t me = 1ull << borig.size();
+          borig.push_back(plist[i]);
+          bvec.push_back(v);
+          bcomb.push_back(comb ^ me);
+          bpiv.push_back(piv);
+          coords[i] = me;
+        }
+        for (const auto& m : borig) par.insert(par.end(), m.begin(), m.end());
+        dt.n_par = (uint32_t)borig.size();
+      }
+      const bool basis = dt.mode == TAB_BASIS;
+      dt.cls_off = (uint32_t)cls.size();
+      for (const Prep& pr : prep) {
+        const Cls& c = cl[pr.i];
+        DClass d{};
+        d.fac_off = (uint32_t)fidx.size();
+        d.n_fac = (uint32_t)c.f.size();
+        d.mono = pr.mono;
+        d.j0 = pr.j;
+        d.d0 = pr.raw - base;
+        if (!pr.mono)
+          for (int i = 0; i < 4; ++i) d.c[i] = (long long)c.coef.c[i];
+        for (const FacKey& k : c.f) {
+          const Lut& l = lut(k.kind, k.alpha, k.beta);
+          fidx.push_back(basis ? 0u : ((uint32_t)k.ia | ((uint32_t)k.ib << 8)));
+          finc.insert(finc.end(), l.inc, l.inc + 4);
+          fcoord.push_back(basis ? coords[(size_t)k.ia] : 0);
+          fcoord.push_back(basis ? coords[(size_t)k.ib] : 0);
+        }
+        cls.push_back(d);
+      }
+    }
     L.classes += prep.size();
     L.parities += plist.size() - 1;
     L.table_classes.push_back(prep.size());
@@ -837,7 +1220,12 @@ void pack(const Program& p, DeviceTables& out) {
       uint64_t nf = 0;
       for (const Prep& pr : prep) nf += cl[pr.i].f.size();
       L.table_class_factors.push_back(nf);
+      L.class_factors += nf;
     }
+    L.table_mode.push_back(dt.mode);
+    L.table_batches.push_back((uint64_t)std::max(dt.n_sb, 0));
+    L.table_rows.push_back(padded_rows);
+    L.table_ops.push_back(real_ops);
     tabs.push_back(dt);
   }
   L.o_tab = s.section();
@@ -852,6 +1240,11 @@ void pack(const Program& p, DeviceTables& out) {
   if (!finc.empty()) s.put(finc.data(), finc.size() * 4);
   L.o_fco = s.section();
   if (!fcoord.empty()) s.put(fcoord.data(), fcoord.size() * 8);
+  L.o_sb = s.section();
+  if (!sbs.empty()) s.put(sbs.data(), sbs.size() * sizeof(DSBatch));
+  L.o_row = s.section();
+  if (!rows.empty()) s.put(rows.data(), rows.size() * 4);
+  L.sl_words = L.sl_par_max ? 64 * W + (int)L.sl_par_max : 0;
   // measurement-mode detector / observable maps (CSR)
   auto csr = [&](const std::vector<std::vector<int>>& m, size_t* o_off, size_t* o_idx) {
     *o_off = s.section();
@@ -893,6 +1286,9 @@ DevView make_view(const unsigned char* base, const DeviceLayout& L, const Progra
   v.fidx = (const uint32_t*)(base + L.o_fidx);
   v.finc = (const uint32_t*)(base + L.o_finc);
   v.fcoord = (const uint64_t*)(base + L.o_fco);
+  v.sb = (const DSBatch*)(base + L.o_sb);
+  v.rows = (const uint32_t*)(base + L.o_row);
+  v.sl_words = L.sl_words;
   v.dmap_off = (const int32_t*)(base + L.o_dmo);
   v.dmap_idx = (const int32_t*)(base + L.o_dmi);
   v.omap_off = (const int32_t*)(base + L.o_omo);
@@ -937,26 +1333,61 @@ const DevView& ensure_uploaded(const Program& p) {
   return slot->v;
 }
 
-cudaError_t launch(const DevView& v, unsigned blocks, cudaStream_t s, uint64_t seed, uint64_t off,
-                   uint64_t shots, uint64_t* meas, uint64_t* det, uint64_t* obs, uint8_t* acc) {
+// Threads per block and dynamic shared memory of a launch: programs with
+// sliced tables get sl_words words per warp and as many warps per block (1 to
+// 4) as fit in kSmemPerBlock; the others use kThreads threads and none.
+constexpr int kSmemPerBlock = 48 * 1024;
+
+struct LaunchShape {
+  unsigned threads;
+  size_t smem;
+};
+
+LaunchShape shape_of(int sl_words) {
+  if (sl_words <= 0) return {(unsigned)kThreads, 0};
+  const size_t per_warp = (size_t)sl_words * 4;
+  const int warps = (int)std::max<size_t>(1, std::min<size_t>(kThreads / 32, kSmemPerBlock / per_warp));
+  return {(unsigned)(32 * warps), per_warp * (size_t)warps};
+}
+
+// allow a kernel more than the default 48 KB of dynamic shared memory
+template <class K>
+cudaError_t allow_smem(K kernel, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+template <int W>
+cudaError_t launch_w(const DevView& v, cudaStream_t s, uint64_t seed, uint64_t off, uint64_t shots, uint64_t* meas,
+                     uint64_t* det, uint64_t* obs, uint8_t* acc) {
+  const LaunchShape sh = shape_of(v.sl_words);
+  const uint64_t blocks = (shots + sh.threads - 1) / sh.threads;
+  if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+  cudaError_t e = allow_smem(k_sample<W>, sh.smem);
+  if (e != cudaSuccess) return e;
+  k_sample<W><<<(unsigned)blocks, sh.threads, sh.smem, s>>>(v, seed, off, shots, meas, det, obs, acc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch(const DevView& v, cudaStream_t s, uint64_t seed, uint64_t off, uint64_t shots, uint64_t* meas,
+                   uint64_t* det, uint64_t* obs, uint8_t* acc) {
   switch (v.W) {
-    case 1: k_sample<1><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
-    case 2: k_sample<2><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
-    case 4: k_sample<4><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
-    case 8: k_sample<8><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
-    case 16: k_sample<16><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
-    case 32: k_sample<32><<<blocks, kThreads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc); break;
+    case 1: return launch_w<1>(v, s, seed, off, shots, meas, det, obs, acc);
+    case 2: return launch_w<2>(v, s, seed, off, shots, meas, det, obs, acc);
+    case 4: return launch_w<4>(v, s, seed, off, shots, meas, det, obs, acc);
+    case 8: return launch_w<8>(v, s, seed, off, shots, meas, det, obs, acc);
+    case 16: return launch_w<16>(v, s, seed, off, shots, meas, det, obs, acc);
+    case 32: return launch_w<32>(v, s, seed, off, shots, meas, det, obs, acc);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace
 
-void prepare_device_tables(Program& p) {
+void prepare_device_tables(Program& p, int64_t sliced_min) {
   auto* t = new DeviceTables();
   try {
-    pack(p, *t);
+    pack(p, *t, sliced_min);
   } catch (const PackError& e) {
     t->status = e.st;
     t->message = e.msg;
@@ -970,17 +1401,16 @@ void device_sample(const Program& p, const SampleArgs& a, void* stream) {
   if (p.mode == TSIM_MODE_DETECTORS && a.meas) fail(TSIM_ERR_ARG, "measurement records requested from a detector-mode program");
   tables_of(p);  // report a program that cannot run on the device before any CUDA call
   if (a.shots == 0) return;
-  const uint64_t blocks = (a.shots + kThreads - 1) / kThreads;
-  if (blocks > 0x7FFFFFFFull) fail(TSIM_ERR_ARG, "too many shots for one launch");
+  if (a.shots > 0x7FFFFFFFull * 32) fail(TSIM_ERR_ARG, "too many shots for one launch");
   const DevView& v = ensure_uploaded(p);
-  cudaError_t e = launch(v, (unsigned)blocks, (cudaStream_t)stream, a.seed, a.shot_offset, a.shots, a.meas, a.det,
-                         a.obs, a.accept);
+  cudaError_t e = launch(v, (cudaStream_t)stream, a.seed, a.shot_offset, a.shots, a.meas, a.det, a.obs, a.accept);
   if (e != cudaSuccess) fail(TSIM_ERR_CUDA, std::string("sampling kernel launch: ") + cudaGetErrorString(e));
 }
 
 // ----------------------------------------------------------- batch plans
 struct BatchPlan {
   int device = -1, n = 0, wmax = 1, sms = 1;
+  int sl_par_max = 0;       // largest sliced parity list over the programs (0: none)
   uint32_t sb = 512;        // shots per work item
   int blocks_per_sm = 8;
   uint64_t total_items = 0;
@@ -1004,6 +1434,19 @@ void plan_items(BatchPlan& b, cudaStream_t s) {
   TSIM_CUDA(cudaStreamSynchronize(s));
 }
 
+template <int W>
+cudaError_t launch_batch_w(const BatchPlan& b, cudaStream_t s, unsigned grid) {
+  // every warp gets room for the transposed X at the launch's W plus the
+  // largest sliced parity list of any program
+  const int stride = b.sl_par_max ? 64 * W + b.sl_par_max : 0;
+  const LaunchShape sh = shape_of(stride);
+  cudaError_t e = allow_smem(k_batch<W>, sh.smem);
+  if (e != cudaSuccess) return e;
+  k_batch<W><<<grid, sh.threads, sh.smem, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter,
+                                               stride);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch(const BatchPlan& b, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
@@ -1011,15 +1454,14 @@ cudaError_t launch_batch(const BatchPlan& b, cudaStream_t s) {
   const uint64_t want = (uint64_t)b.sms * (uint64_t)b.blocks_per_sm;
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, b.total_items));
   switch (b.wmax) {
-    case 1: k_batch<1><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
-    case 2: k_batch<2><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
-    case 4: k_batch<4><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
-    case 8: k_batch<8><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
-    case 16: k_batch<16><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
-    case 32: k_batch<32><<<grid, kThreads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter); break;
+    case 1: return launch_batch_w<1>(b, s, grid);
+    case 2: return launch_batch_w<2>(b, s, grid);
+    case 4: return launch_batch_w<4>(b, s, grid);
+    case 8: return launch_batch_w<8>(b, s, grid);
+    case 16: return launch_batch_w<16>(b, s, grid);
+    case 32: return launch_batch_w<32>(b, s, grid);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace
@@ -1044,6 +1486,7 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
     bp.obs = args[i].obs;
     bp.accept = args[i].accept;
     b->wmax = std::max(b->wmax, bp.v.W);
+    if (bp.v.sl_words) b->sl_par_max = std::max(b->sl_par_max, bp.v.sl_words - 64 * bp.v.W);
     b->h_progs.push_back(bp);
   }
   const size_t bytes = (size_t)n * sizeof(BatchProg) + ((size_t)n + 1) * 8 + 64;
@@ -1198,8 +1641,7 @@ extern "C" tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t sh
   if (T.layout.total > kNoAllocBytes)
     return noalloc_error(TSIM_ERR_ARG, "program tables exceed the 4 MiB maximum of tsim_sample_noalloc");
   if (shots == 0) return TSIM_OK;
-  const uint64_t blocks = (shots + kThreads - 1) / kThreads;
-  if (blocks > 0x7FFFFFFFull) return noalloc_error(TSIM_ERR_ARG, "too many shots for one launch");
+  if (shots > 0x7FFFFFFFull * 32) return noalloc_error(TSIM_ERR_ARG, "too many shots for one launch");
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
     return noalloc_error(TSIM_ERR_CUDA, "cudaGetDevice failed or device index out of range");
@@ -1218,7 +1660,7 @@ extern "C" tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t sh
   if (cudaMemcpyAsync(g_noalloc_dev[dev], T.blob.data(), T.layout.total, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return noalloc_error(TSIM_ERR_CUDA, "cudaMemcpyAsync into the no-alloc scratch array failed");
   const DevView v = make_view((const unsigned char*)g_noalloc_dev[dev], T.layout, p);
-  if (launch(v, (unsigned)blocks, s, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept) != cudaSuccess)
+  if (launch(v, s, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept) != cudaSuccess)
     return noalloc_error(TSIM_ERR_CUDA, "launch of the sampling kernel failed");
   return TSIM_OK;
 }

@@ -20,14 +20,24 @@ struct SampleArgs {
 // Byte offsets of the sections of the packed device tables (256-byte aligned)
 struct DeviceLayout {
   size_t o_ch = 0, o_thr = 0, o_sig = 0, o_out = 0, o_om = 0, o_cn = 0, o_tab = 0, o_par = 0,
-         o_cls = 0, o_fidx = 0, o_finc = 0, o_fco = 0, o_dmo = 0, o_dmi = 0, o_omo = 0, o_omi = 0, total = 0;
+         o_cls = 0, o_fidx = 0, o_finc = 0, o_fco = 0, o_sb = 0, o_row = 0, o_dmo = 0, o_dmi = 0, o_omo = 0,
+         o_omi = 0, total = 0;
   int W = 1;
+  uint32_t sl_par_max = 0;  // largest parity list of a bit-sliced table
+  int sl_words = 0;         // shared 32-bit words per warp the kernel needs (0: no sliced table)
   // statistics of the packed tables
   uint64_t classes = 0;     // stabilizer terms after merging terms with equal factor lists
   uint64_t class_factors = 0;
   uint64_t parities = 0;    // distinct factor parities over all tables
   std::vector<uint64_t> table_classes, table_class_factors, table_parities;  // per table
+  // per table: layout (0 scalar, 1 basis, 2 bit-sliced), and for sliced
+  // tables the batches of 32 terms, padded operation rows and real operations
+  std::vector<uint64_t> table_mode, table_batches, table_rows, table_ops;
 };
+
+// Tables with at least this many terms (after merging equal factor lists)
+// use the bit-sliced warp-cooperative layout when their factors allow it.
+constexpr int64_t kDefaultSlicedMin = 64;
 
 // Host-side packed tables of one program, built once when the program is
 // compiled or loaded.  status != TSIM_OK when the program cannot run on the
@@ -39,7 +49,8 @@ struct DeviceTables {
   std::string message;
 };
 
-void prepare_device_tables(Program& p);
+// Pack the device tables; sliced_min < 0 disables the bit-sliced layout.
+void prepare_device_tables(Program& p, int64_t sliced_min = kDefaultSlicedMin);
 void device_sample(const Program& p, const SampleArgs& a, void* stream);
 void device_sample_batch(const Program* const* progs, int n, const SampleArgs* args, void* stream);
 
