@@ -5,7 +5,13 @@ surface code, 49 qubits, 5 syndrome rounds, 16 T/T_DAG gates in the injected
 rotation, depolarising p in {5e-4, 1e-3, 2e-3}, 10^6 shots per p, detector
 sampling with bit-packed uint64 records.  One step = one pass of the whole
 hot path (noise, f, detectors, exact marginals, Algorithm 1, records) over
-10^6 shots for each of the three p (three launches).
+10^6 shots for each of the three p.
+
+Two forms are timed on the same GPU and must write identical records:
+  value  learned + batched: programs compiled with the learned cut order (the
+         committed network weights; heuristic order when they are absent), all
+         programs in one persistent launch replayed from a CUDA graph;
+  plain  heuristic cut order, one tsim_sample launch per program.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
 
@@ -32,7 +38,7 @@ SEED = 0
 METRIC = "shots/sec and Z[w] term-evals/sec, learned+batched vs plain GPU form, bit-exact"
 WORKLOADS = {
     "cfg2": "d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG, p in {5e-4,1e-3,2e-3}, 1e6 shots per p",
-    "cfg3": "d=3 triangular colour-code T-check, 19 qubits, 42 T/T_DAG, 3 check rounds, p=1e-3, postselected, 1e5 shots",
+    "cfg3": "d=3 triangular colour-code T-check, 19 qubits, 42 T/T_DAG, 3 check rounds, p=1e-3, postselected, 1e7 shots",
     "cfg4": "batched launch: 256 seeded random noisy Clifford+T mirror circuits (20-60 qubits, depth 20-100, "
             "8-40 T/T_DAG, 2-qubit density 0.3, p in U[1e-4,3e-3]), shots log-uniform in [1e3,1e6], "
             "one persistent launch replayed from a CUDA graph, autotuned shot block",
@@ -45,7 +51,7 @@ WORKLOAD = WORKLOADS["cfg2"]
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: about 0.2 s per form)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=8.0, help="bound on the oracle baseline's CPU work")
@@ -56,9 +62,11 @@ def parse():
     global WORKLOAD, SHOTS_PER_P
     WORKLOAD = WORKLOADS[args.workload]
     if args.workload == "cfg3":
-        SHOTS_PER_P = 100_000
+        SHOTS_PER_P = 10_000_000
     if args.shots:
         SHOTS_PER_P = args.shots
+    if args.steps is None:
+        args.steps = {"cfg2": 100, "cfg3": 3, "cfg4": 20}[args.workload]
     return args
 
 
@@ -73,9 +81,17 @@ WORKLOAD_NAME = "cfg2"
 SHOTS_LIST = None
 
 
-def config4_programs(n=256):
+def cut_model():
+    """The committed cut-order network weights, or None."""
+    from paper_2604_01059_gb300.train_cut_order import load_weights
+    return load_weights()
+
+
+def config4_programs(n=256, decomp=0):
     """Compile the batched workload in parallel host threads; circuits over the
-    term budgets are skipped and the next seeds drawn (deterministic order)."""
+    term budgets are skipped and the next seeds drawn (deterministic order).
+    The learned order never has more terms than the heuristic one, so the
+    same circuits pass the budgets in both forms."""
     from concurrent.futures import ThreadPoolExecutor
 
     import paper_2604_01059_gb300 as T
@@ -90,10 +106,15 @@ def config4_programs(n=256):
             if e.code == 3:
                 return None
             raise
-        return (p, shots) if p.info["total_terms"] <= CFG4_PROGRAM_BUDGET else None
+        if p.info["total_terms"] > CFG4_PROGRAM_BUDGET:
+            return None
+        if decomp:
+            p = T.Program(txt, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
+        return (p, shots)
 
     out = []
-    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+    workers = 1 if decomp else (os.cpu_count() or 1)  # the learned order scores on the GPU
+    with ThreadPoolExecutor(max_workers=workers) as ex:
         for k in range(0, len(pool), 64):
             for r in ex.map(build, pool[k:k + 64]):
                 if r is not None and len(out) < n:
@@ -103,17 +124,36 @@ def config4_programs(n=256):
     return out
 
 
-def programs():
+def programs(decomp=0):
     import paper_2604_01059_gb300 as T
     from paper_2604_01059_gb300 import workloads as Wk
     global SHOTS_LIST
     if WORKLOAD_NAME == "cfg3":
-        return [T.Program(Wk.config3_circuit(p=1e-3))]
+        return [T.Program(Wk.config3_circuit(p=1e-3), decomp=decomp)]
     if WORKLOAD_NAME == "cfg4":
-        pr = config4_programs()
+        pr = config4_programs(decomp=decomp)
         SHOTS_LIST = [s for _, s in pr]
         return [p for p, _ in pr]
-    return [T.Program(Wk.config2_circuit(p=p)) for p in P_VALUES]
+    return [T.Program(Wk.config2_circuit(p=p), decomp=decomp) for p in P_VALUES]
+
+
+def learned_programs():
+    """Programs in the learned cut order, with the order's bookkeeping."""
+    import paper_2604_01059_gb300 as T
+    w = cut_model()
+    if w is None:
+        return programs(), {"cut_order": "heuristic (no trained weights)"}
+    before = T.tsim_cut_policy_stats()
+    T.tsim_cut_model_set(w)
+    try:
+        progs = programs(decomp=T.DECOMP_LEARNED)
+    finally:
+        T.tsim_cut_model_set(None)
+    after = T.tsim_cut_policy_stats()
+    d = [a - b for a, b in zip(after, before)]
+    return progs, {"cut_order": "learned (GNN scores, heuristic as fallback and judge)",
+                   "scorer_calls": d[0], "scored": d[1], "marginals_learned_kept": d[2],
+                   "marginals_heuristic_kept": d[3]}
 
 
 def shots_of(k):
@@ -141,7 +181,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -251,6 +291,17 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _outputs(progs, shots):
+    import torch
+    outs = []
+    for p, ns in zip(progs, shots):
+        i = p.info
+        outs.append((torch.empty((ns, max(i["det_words"], 1)), dtype=torch.int64, device="cuda"),
+                     torch.empty((ns, max(i["obs_words"], 1)), dtype=torch.int64, device="cuda"),
+                     torch.empty((ns,), dtype=torch.uint8, device="cuda")))
+    return outs
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -263,22 +314,20 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    progs = programs()
+    plain_progs = programs()
+    progs, cut = learned_programs()
     n = len(progs)
+    assert n == len(plain_progs)
     shots = [shots_of(k) for k in range(n)]
     offsets = [rank * shots[k] for k in range(n)]  # weak scaling: every rank its own shot range
     seeds = [SEED] * n
     stream = torch.cuda.current_stream()
-    outs = []
-    for p, ns in zip(progs, shots):
-        i = p.info
-        outs.append((torch.empty((ns, max(i["det_words"], 1)), dtype=torch.int64, device="cuda"),
-                     torch.empty((ns, max(i["obs_words"], 1)), dtype=torch.int64, device="cuda"),
-                     torch.empty((ns,), dtype=torch.uint8, device="cuda")))
+    outs = _outputs(progs, shots)
+    plain_outs = _outputs(plain_progs, shots)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def plain_step():
-        for k, (p, (d, o, a)) in enumerate(zip(progs, outs)):
+        for k, (p, (d, o, a)) in enumerate(zip(plain_progs, plain_outs)):
             T.tsim_sample(p.h, shots[k], seeds[k], offsets[k], None, d, o, a, stream)
 
     batch = T.tsim_batch_create([p.h for p in progs], shots, seeds, offsets, None,
@@ -325,10 +374,15 @@ def run_gpu(args):
     plain_ms = timed(plain_step, args.steps)
     clk = clocks.stop()
     T.tsim_batch_free(batch)
+    # both forms wrote every record of the step: they must agree bit for bit
+    identical = all(torch.equal(a[:, :p.info["det_words"]], b[:, :p.info["det_words"]]) and
+                    torch.equal(x[:, :p.info["obs_words"]], y[:, :p.info["obs_words"]]) and torch.equal(u, v)
+                    for p, (a, x, u), (b, y, v) in zip(progs, outs, plain_outs))
     shots_step = sum(shots) * world
     value = shots_step * args.steps / (batch_ms / 1e3)
     plain = shots_step * args.steps / (plain_ms / 1e3)
     terms_step = sum(term_evals_per_shot(p) * ns for p, ns in zip(progs, shots)) * world
+    plain_terms_step = sum(term_evals_per_shot(p) * ns for p, ns in zip(plain_progs, shots)) * world
     tev = terms_step * args.steps / (batch_ms / 1e3)
 
     # end to end through the host-buffer entry point: copies inside the timed region
@@ -377,12 +431,19 @@ def run_gpu(args):
                 "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (256 MiB write)",
                            "programs": n, "shots_per_step": shots_step,
                            "terms_per_shot": [term_evals_per_shot(p) for p in progs][:8],
+                           "plain_terms_per_shot": [term_evals_per_shot(p) for p in plain_progs][:8],
                            "channels": [p.info["num_channels"] for p in progs][:8],
-                           "cut_order": "heuristic", "batch": binfo},
+                           "form": "learned cut order + batched persistent launch (CUDA graph)",
+                           "cut": cut, "batch": binfo},
                 "term_evals_per_s": tev,
+                "identical_records": bool(identical),
                 "plain": {"value": plain, "unit": "shots/s", "ms_per_step": plain_ms / args.steps,
-                          "form": "one tsim_sample launch per program"},
-                "e2e": {"value": e2e, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+                          "term_evals_per_s": plain_terms_step * args.steps / (plain_ms / 1e3),
+                          "form": "heuristic cut order, one tsim_sample launch per program",
+                          "gpu_launches": args.steps * n},
+                "speedup_vs_plain": value / plain,
+                "e2e": {"value": e2e, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
+                        "api": "tsim_sample_host (device staging, records copied to host inside the timed region)"},
                 "gpu_launches": args.steps, "roofline": roof, "clocks": clk,
                 "cpu_baseline": base}
         print(json.dumps(line))
@@ -397,13 +458,19 @@ def kernel_int_ops(prog):
                + 2 three-input XORs) = 40 per call, plus one compare per channel;
       outputs: 3 per single-bit deterministic output, 60 per Bernoulli decision;
       tables:  per distinct parity 2W+2 (AND, XOR, popcount, insert), per merged
-               term 12 (+5 per factor: two bit extracts, index, lookup, add)."""
+               term 12 (+5 per factor: two bit extracts, index, lookup, add);
+               bit-sliced tables: the lane-operations of one warp for its 32
+               shots, as the library counts them, divided by 32."""
     i = prog.info
     C = i["num_channels"]
     W = next(p for p in (1, 2, 4, 8, 16, 32) if i["x_words"] <= p)
     ops = 40 * ((C + 3) // 4) + C
     ops += 3 * (i["num_outputs"] - i["num_random"]) + 60 * i["num_random"]
     for t in range(i["num_tables"]):
+        layout = prog.device_table_layout(t)
+        if layout[0] == 2:  # bit-sliced: the library counts one warp's lane-operations for 32 shots
+            ops += layout[4] / 32
+            continue
         classes, factors, parities = prog.device_table_stats(t)
         ops += parities * (2 * W + 2) + 12 * classes + 5 * factors
     return ops

@@ -178,8 +178,10 @@ tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t shots, uint64
 /* Reusable batched launch (Appendix "Additional benchmarks": batched sampling;
  * here heterogeneous programs share one persistent kernel).  tsim_batch_create
  * uploads every program, lays out the (program, shot-block) work items,
- * optionally autotunes the shot-block size (128, 512, 2048 shots) and the
- * resident blocks per SM (4, 8, 16) by timing each candidate on the real
+ * optionally autotunes the shot-block size (1, 4 or 16 times the threads of
+ * a block: 128 threads, or 32 to 128 when a program has bit-sliced tables;
+ * 4 times without autotuning) and the resident blocks per SM (4, 8, 16) by
+ * timing each candidate on the real
  * batch, and captures "reset the work counter + persistent launch" in a CUDA
  * graph.  tsim_batch_launch replays that graph on cuda_stream (asynchronous);
  * the output pointers given at creation are written on every launch.  The
@@ -250,16 +252,27 @@ tsim_status tsim_program_device_table_stats(const tsim_program* prog, int t, uin
  *
  * tsim_program_set_table_layout re-packs the program: tables with at least
  * sliced_min_terms terms (after merging terms with equal factor lists) use
- * SLICED when they qualify; sliced_min_terms < 0 disables SLICED.  The
- * default at compile / load time is 64.  It frees the program's uploaded
+ * SLICED when they qualify; sliced_min_terms < 0 disables SLICED.  A SLICED
+ * table whose batches have at most stage_rows operation rows each is read
+ * through shared memory (each warp bulk-copies the next batch's rows while
+ * it evaluates the current one); 0 reads rows from global memory through
+ * L1, < 0 takes the default (0).  A SLICED table is split into segments of
+ * consecutive terms whose distinct parities fit segment_parities 32-bit words
+ * of shared memory per warp (each segment forms its own parity words; fewer
+ * words let more warps reside per SM); <= 0 takes the default (2048).  The
+ * defaults at compile / load time are 64, 0 and 2048.
+ * It frees the program's uploaded
  * device copy, so it must not be called while a launch of the program is in
  * flight or while a batch created from it (tsim_batch_create) exists.
  *
  * tsim_program_device_table_layout: out[0] = layout of table t, out[1] =
- * batches of 32 terms, out[2] = padded operation rows over those batches,
- * out[3] = operations before padding (out[1..3] are 0 unless SLICED). */
-tsim_status tsim_program_set_table_layout(tsim_program* prog, int64_t sliced_min_terms);
-tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[4]);
+ * batches of 32 terms (over all segments), out[2] = padded operation rows,
+ * out[3] = operations before padding, out[4] = integer lane-operations one
+ * warp executes on the table for its 32 shots (out[1..4] are 0 unless
+ * SLICED). */
+tsim_status tsim_program_set_table_layout(tsim_program* prog, int64_t sliced_min_terms, int32_t stage_rows,
+                                          int32_t segment_parities);
+tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[5]);
 
 /* Self-check of the compiler's rewrite rules against brute-force summation on
  * random small parameterised graphs (no GPU).  Returns TSIM_OK when all pass. */

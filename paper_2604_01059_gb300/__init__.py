@@ -98,7 +98,7 @@ def load_library(path: str | None = None):
     L.tsim_selftest_rules.argtypes = [u64, i32]
     L.tsim_measure_int_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
     L.tsim_program_device_table_stats.argtypes = [vp, i32, ctypes.POINTER(u64)]
-    L.tsim_program_set_table_layout.argtypes = [vp, i64]
+    L.tsim_program_set_table_layout.argtypes = [vp, i64, i32, i32]
     L.tsim_program_device_table_layout.argtypes = [vp, i32, ctypes.POINTER(u64)]
     L.tsim_cut_num_params.argtypes = []
     L.tsim_cut_init_params.argtypes = [u64, vp]
@@ -285,15 +285,20 @@ def tsim_program_device_table_stats(h, t):
 TABLE_SCALAR, TABLE_BASIS, TABLE_SLICED = 0, 1, 2
 
 
-def tsim_program_set_table_layout(h, sliced_min_terms):
+def tsim_program_set_table_layout(h, sliced_min_terms, stage_rows=-1, segment_parities=0):
     """Re-pack the device tables: tables with at least sliced_min_terms terms
-    use the bit-sliced warp layout where they qualify (< 0: never)."""
-    _check(load_library().tsim_program_set_table_layout(h, int(sliced_min_terms)))
+    use the bit-sliced warp layout where they qualify (< 0: never); sliced
+    batches of at most stage_rows rows are staged in shared memory (0: none,
+    < 0: default); sliced tables are split into segments of at most
+    segment_parities parity words (<= 0: default)."""
+    _check(load_library().tsim_program_set_table_layout(h, int(sliced_min_terms), int(stage_rows),
+                                                        int(segment_parities)))
 
 
 def tsim_program_device_table_layout(h, t):
-    """(layout, batches of 32 terms, padded operation rows, operations) of table t."""
-    out = (ctypes.c_uint64 * 4)()
+    """(layout, batches of 32 terms, padded operation rows, operations,
+    integer lane-operations per 32 shots) of table t."""
+    out = (ctypes.c_uint64 * 5)()
     _check(load_library().tsim_program_device_table_layout(h, t, out))
     return tuple(out)
 
@@ -448,8 +453,8 @@ class Program:
     def device_table_stats(self, t):
         return tsim_program_device_table_stats(self.h, t)
 
-    def set_table_layout(self, sliced_min_terms):
-        tsim_program_set_table_layout(self.h, sliced_min_terms)
+    def set_table_layout(self, sliced_min_terms, stage_rows=-1, segment_parities=0):
+        tsim_program_set_table_layout(self.h, sliced_min_terms, stage_rows, segment_parities)
         self.info = tsim_program_info(self.h)
 
     def device_table_layout(self, t):

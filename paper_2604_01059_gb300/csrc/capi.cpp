@@ -133,17 +133,18 @@ tsim_status tsim_program_device_table_stats(const tsim_program* prog, int t, uin
   });
 }
 
-tsim_status tsim_program_set_table_layout(tsim_program* prog, int64_t sliced_min_terms) {
+tsim_status tsim_program_set_table_layout(tsim_program* prog, int64_t sliced_min_terms, int32_t stage_rows,
+                                          int32_t segment_parities) {
   return guard([&] {
     tsim::Program& p = const_cast<tsim::Program&>(prog_of(prog));
     tsim::device_release(p.dev);  // the uploaded copy of the old layout
     p.dev = nullptr;
-    tsim::prepare_device_tables(p, sliced_min_terms);
+    tsim::prepare_device_tables(p, sliced_min_terms, stage_rows, segment_parities);
     if (p.devtab->status != TSIM_OK) tsim::fail(p.devtab->status, p.devtab->message);
   });
 }
 
-tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[4]) {
+tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[5]) {
   return guard([&] {
     const tsim::Program& p = prog_of(prog);
     if (!out || t < 0 || t >= (int)p.tables.size()) tsim::fail(TSIM_ERR_ARG, "bad table index");
@@ -153,6 +154,7 @@ tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, ui
     out[1] = L.table_batches[(size_t)t];
     out[2] = L.table_rows[(size_t)t];
     out[3] = L.table_ops[(size_t)t];
+    out[4] = L.table_work32[(size_t)t];
   });
 }
 

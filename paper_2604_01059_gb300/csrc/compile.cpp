@@ -367,19 +367,23 @@ void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget,
     decompose(M, TSIM_DECOMP_HEURISTIC, out, st);
     return;
   }
+  // the heuristic order first; the learned order then runs with the
+  // heuristic's term count as its budget, so a worse order stops as soon as
+  // it has more terms (and costs no more than the heuristic did)
   std::vector<Term> learned, heuristic;
   DecompStats s1 = st, s2 = st;
   uint64_t t1 = total ? *total : 0, t2 = t1;
   s1.total = &t1;
   s2.total = &t2;
   bool ok1 = true, ok2 = true;
-  try { decompose(M, TSIM_DECOMP_LEARNED, learned, s1, &scores); } catch (const Error& e) {
-    if (e.code != TSIM_ERR_CHI_BUDGET) throw;
-    ok1 = false;
-  }
   try { decompose(M, TSIM_DECOMP_HEURISTIC, heuristic, s2); } catch (const Error& e) {
-    if (e.code != TSIM_ERR_CHI_BUDGET || !ok1) throw;
+    if (e.code != TSIM_ERR_CHI_BUDGET) throw;
     ok2 = false;
+  }
+  if (ok2) s1.budget = std::min<uint64_t>(s1.budget, std::max<uint64_t>(heuristic.size(), 1));
+  try { decompose(M, TSIM_DECOMP_LEARNED, learned, s1, &scores); } catch (const Error& e) {
+    if (e.code != TSIM_ERR_CHI_BUDGET || !ok2) throw;
+    ok1 = false;
   }
   g_cut_stats[1]++;
   const bool use_learned = ok1 && (!ok2 || learned.size() <= heuristic.size());

@@ -40,7 +40,7 @@ namespace tsim {
     if (e_ != cudaSuccess) fail(TSIM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-enum : int { ST_NOT_REAL = 1, ST_OVERFLOW = 2, ST_ZERO_PROB = 4 };
+enum : int { ST_NOT_REAL = 1, ST_OVERFLOW = 2, ST_ZERO_PROB = 4, ST_TIMEOUT = 8 };
 
 // device-wide status word: bits of the conditions above, read by tsim_sync
 __device__ int g_status;
@@ -58,7 +58,7 @@ struct DOut { int32_t kind, cst, a, chain, table, pad; };
 // per shot), BASIS = parities as coordinates in a GF(2) basis of their span,
 // SLICED = warp-cooperative bit-sliced evaluation (below).
 enum : int { TAB_SCALAR = 0, TAB_BASIS = 1, TAB_SLICED = 2 };
-struct DTable { uint32_t par_off, n_par, cls_off, n_cls; int32_t base, mode, sb_off, n_sb; };
+struct DTable { uint32_t par_off, n_par, cls_off, n_cls; int32_t base, mode, sb_off, n_sb, stage, pad[3]; };
 struct DClass { uint32_t fac_off, n_fac; int32_t mono, j0, d0, pad; long long c[4]; };
 
 // Bit-sliced tables.  A warp evaluates 32 shots at once: bit s of every
@@ -79,12 +79,15 @@ enum : int {
   kSlCodes = 7
 };
 constexpr uint32_t kSlOnes = 1;        // parity index whose word is all ones
-constexpr int kSlMaxPar = 16384;       // distinct parities of one sliced table
+constexpr int kSlMaxPar = 16384;       // parity words of one segment (4q fits 16 bits)
 // One batch of 32 terms: rows of operation code c are cnt[c] x 32 parity
 // indices (lane-interleaved, padded with no-op indices), starting at row_off.
 // All terms of a batch share the magnitude sqrt2^d; j0m[b] holds bit b of
 // each lane's constant phase; valid marks lanes that carry a term.
 struct DSBatch { uint32_t row_off; uint16_t cnt[8]; int32_t d; uint32_t j0m[3]; uint32_t valid; };
+// A sliced table is a list of segments: consecutive terms whose distinct
+// parities (par_off, n_par masks) fit one shared buffer, and their batches.
+struct DSeg { uint32_t par_off, n_par, sb_off, n_sb; };
 
 struct DevView {
   int W;
@@ -102,9 +105,11 @@ struct DevView {
   const uint32_t* fidx;   // per factor: parity index of a | parity index of b << 8
   const uint32_t* finc;   // per factor: 4 packed increments
   const uint64_t* fcoord; // basis tables: per factor the coordinates of a and b (2 words)
+  const DSeg* seg;        // sliced tables: segments
   const DSBatch* sb;      // sliced tables: batches
   const uint32_t* rows;   // sliced tables: operation rows
-  int sl_words;           // 32-bit shared-memory words one warp needs (0: no sliced table)
+  int sl_par;             // shared words for parity words per warp (0: no sliced table)
+  int sl_rb;              // shared words of one row staging buffer (0: no staging)
   const int32_t* dmap_off;
   const int32_t* dmap_idx;
   const int32_t* omap_off;
@@ -285,127 +290,260 @@ __device__ __forceinline__ void accumulate(const DClass& C, uint32_t acc, long l
   }
 }
 
-// 32 x 32 bit-matrix transpose across the warp: on entry lane r holds row r
-// (bit c = column c), on exit lane c holds column c (bit r = row r).  Five
-// stages exchange the off-diagonal blocks of size 16, 8, 4, 2, 1.
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
-  const uint32_t keep[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-  for (int st = 0; st < 5; ++st) {
-    const int j = 16 >> st;
-    const uint32_t m = keep[st];  // bit positions c with (c & j) == 0
-    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, j);
-    x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+// ---- shared-memory staging of operation rows (bulk copies through the
+// tensor memory accelerator, completion tracked by an mbarrier per buffer)
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t lds(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// one elected lane: expect `bytes` on the barrier and start the bulk copy
+// (global source and shared destination 16-byte aligned, bytes a multiple of 16)
+// (no copy for 0 bytes: the arrival alone completes the phase)
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  if (bytes)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Warp-uniform bounded wait for the phase of the given parity; false when it
+// did not complete within the limit (the caller reports ST_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (__all_sync(0xFFFFFFFFu, mbar_test(bar, parity))) return true;
+  return false;
+}
+
+// A warp's shared words for sliced tables: transposed X (64 W), parity words
+// (par), two row staging buffers (rb each), two mbarriers and a state word
+// (bit 0 / 1: next phase parity of buffer 0 / 1; bit 2: staging failed).
+struct SlSmem {
+  uint32_t xs, par, rb0, rb1, bar0, bar1, state;
+  int rb;
+};
+
+__host__ __device__ __forceinline__ int sl_round32(int x) { return (x + 31) & ~31; }
+
+__host__ __device__ __forceinline__ int sl_warp_words(int W, int par, int rb) {
+  if (par <= 0) return 0;
+  return sl_round32(64 * W + par) + (rb > 0 ? 2 * rb + 32 : 0);
+}
+
+__device__ __forceinline__ SlSmem sl_smem(uint32_t* warp_base, int W, int par, int rb) {
+  SlSmem m;
+  const uint32_t b = smem_u32(warp_base);
+  m.xs = b;
+  m.par = b + 4u * (uint32_t)(64 * W);
+  const uint32_t st = b + 4u * (uint32_t)sl_round32(64 * W + par);
+  m.rb0 = st;
+  m.rb1 = st + 4u * (uint32_t)rb;
+  m.bar0 = st + 8u * (uint32_t)rb;
+  m.bar1 = m.bar0 + 8;
+  m.state = m.bar0 + 16;
+  m.rb = rb;
+  return m;
+}
+
+// once per warp at kernel start, when rows are staged
+__device__ __forceinline__ void sl_init(const SlSmem& m) {
+  if (m.rb > 0) {
+    if ((threadIdx.x & 31) == 0) {
+      mbar_init(m.bar0, 1);
+      mbar_init(m.bar1, 1);
+      asm volatile("st.shared.u32 [%0], %1;" ::"r"(m.state), "r"(0u) : "memory");
+      fence_mbar_init();
+    }
+    __syncwarp();
   }
-  return x;
+}
+
+// 32 x 32 bit-matrix transpose across the warp: on entry lane r holds row r
+// (bit c = column c), on exit lane c holds column c (bit r = row r).  Stage j
+// (16, 8, 4, 2, 1) swaps the off-diagonal j x j blocks between lanes r and
+// r ^ j: each lane sends the half its partner keeps, and rotates what it
+// receives into place (left by j in the lower lane, right by j in the upper
+// one; the received bits never wrap).
+struct Transposer {
+  uint32_t mk[5];   // the bits a lane keeps at each stage
+  uint32_t rot[5];  // left-rotation of the received bits
+  __device__ __forceinline__ explicit Transposer(int lane) {
+    const uint32_t keep[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+      const int j = 16 >> st;
+      const bool upper = (lane & j) != 0;
+      mk[st] = upper ? ~keep[st] : keep[st];
+      rot[st] = upper ? 32u - (uint32_t)j : (uint32_t)j;
+    }
+  }
+  __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+      const uint32_t recv = __shfl_xor_sync(0xFFFFFFFFu, x & ~mk[st], 16 >> st);
+      x = (x & mk[st]) | __funnelshift_l(recv, recv, rot[st]);
+    }
+    return x;
+  }
+};
+
+// Operation rows read from global memory (lane-interleaved, through L1) or
+// from a shared staging buffer.  A row holds the byte offset of a parity word
+// (4q), or two of them (4qa | 4qb << 16) for pi-pairs.
+struct RowsG {
+  const uint32_t* p;
+  __device__ __forceinline__ uint32_t get(int i) const { return __ldg(p + 32 * i); }
+  __device__ __forceinline__ void adv(int k) { p += 32 * k; }
+};
+struct RowsS {
+  uint32_t a;
+  __device__ __forceinline__ uint32_t get(int i) const { return lds(a + 128u * (uint32_t)i); }
+  __device__ __forceinline__ void adv(int k) { a += 128u * (uint32_t)k; }
+};
+
+// The n rows of one operation code, in chunks whose row loads and parity
+// loads are all issued before the updates; f(way, a, b) spreads consecutive
+// rows over 4 independent accumulators (way = row & 3) so that the update
+// chains overlap.
+template <bool PAIR, class Rows, class F>
+__device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
+  int k = 0;
+  for (; k + 16 <= n; k += 16, R.adv(16)) {
+    uint32_t r[16], a[16], b[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) r[i] = R.get(i);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      a[i] = lds(par + (PAIR ? (r[i] & 0xFFFFu) : r[i]));
+      b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) f(i & 3, a[i], b[i]);
+  }
+  for (; k + 4 <= n; k += 4, R.adv(4)) {
+    uint32_t r[4], a[4], b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r[i] = R.get(i);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      a[i] = lds(par + (PAIR ? (r[i] & 0xFFFFu) : r[i]));
+      b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f(i, a[i], b[i]);
+  }
+  for (; k < n; ++k, R.adv(1)) {
+    const uint32_t r = R.get(0);
+    f(0, lds(par + (PAIR ? (r & 0xFFFFu) : r)), PAIR ? lds(par + (r >> 16)) : 0u);
+  }
+}
+
+// (x1, x2) += (y1, y2) for 2-bit bit-sliced counters mod 4
+__device__ __forceinline__ void add2bit(uint32_t& x1, uint32_t& x2, uint32_t y1, uint32_t y2) {
+  x2 ^= y2 ^ (x1 & y1);
+  x1 ^= y1;
+}
+
+// All operation rows of one batch; returns the planes (J0, J1, J2, Z).
+template <class Rows>
+__device__ __forceinline__ void sl_batch(const DSBatch& B, Rows R, uint32_t par, int lane, uint32_t& J0, uint32_t& J1,
+                                         uint32_t& J2, uint32_t& Z) {
+  J0 = 0u - ((B.j0m[0] >> lane) & 1u);
+  J1 = 0u - ((B.j0m[1] >> lane) & 1u);
+  J2 = 0u - ((B.j0m[2] >> lane) & 1u);
+  Z = 0u - ((~B.valid >> lane) & 1u);
+  // per way: J2 flips k, vanishing flags z, and a 2-bit counter (c1, c2) of
+  // the rows that add 2 to J (J2 flips and vanishing flags commute with it)
+  uint32_t k[4] = {0, 0, 0, 0}, z[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0}, c2[4] = {0, 0, 0, 0};
+  sl_loop<false>(B.cnt[SL_XOR4], R, par, [&](int w, uint32_t a, uint32_t) { k[w] ^= a; });
+  sl_loop<false>(B.cnt[SL_ADD2], R, par, [&](int w, uint32_t a, uint32_t) {
+    c2[w] ^= c1[w] & a;
+    c1[w] ^= a;
+  });
+  // J += 6a = 2a + 4a
+  sl_loop<false>(B.cnt[SL_ADD6], R, par, [&](int w, uint32_t a, uint32_t) {
+    c2[w] ^= c1[w] & a;
+    c1[w] ^= a;
+    k[w] ^= a;
+  });
+  sl_loop<true>(B.cnt[SL_XOR4AB], R, par, [&](int w, uint32_t a, uint32_t b) { k[w] ^= a & b; });
+  sl_loop<false>(B.cnt[SL_ZERO], R, par, [&](int w, uint32_t a, uint32_t) { z[w] |= a; });
+  sl_loop<false>(B.cnt[SL_ZEROC], R, par, [&](int w, uint32_t a, uint32_t) { z[w] |= ~a; });
+  add2bit(c1[0], c2[0], c1[1], c2[1]);
+  add2bit(c1[2], c2[2], c1[3], c2[3]);
+  add2bit(c1[0], c2[0], c1[2], c2[2]);
+  add2bit(J1, J2, c1[0], c2[0]);
+  J2 ^= (k[0] ^ k[1]) ^ (k[2] ^ k[3]);
+  Z |= (z[0] | z[1]) | (z[2] | z[3]);
+  // J += a (odd phases; rare): a three-plane increment
+  sl_loop<false>(B.cnt[SL_ADD1], R, par, [&](int, uint32_t a, uint32_t) {
+    const uint32_t cy = J0 & a;
+    J0 ^= a;
+    J2 ^= J1 & cy;
+    J1 ^= cy;
+  });
+}
+
+__device__ __forceinline__ uint32_t sl_batch_rows(const DSBatch& B) {
+  uint32_t n = 0;
+#pragma unroll
+  for (int c = 0; c < kSlCodes; ++c) n += B.cnt[c];
+  return n;
 }
 
 // Warp-cooperative exact value of a sliced table for the 32 shots of the
 // warp (every lane must call it; lane s receives shot s's value).
-// sm: this warp's shared words, 64 W for the transposed X, then Par.
 template <int W>
-__device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64_t (&X)[W], uint32_t* sm) {
+__device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64_t (&X)[W], const SlSmem& S) {
   const int lane = threadIdx.x & 31;
-  uint32_t* Xs = sm;           // Xs[i]: bit s = bit i of shot s's X
-  uint32_t* Par = sm + 64 * W; // Par[q]: bit s = parity q of shot s
+  const Transposer transpose32(lane);
   __syncwarp();
+  uint32_t state = S.rb > 0 ? lds(S.state) : 4u;
+  const bool staged = tb.stage && !(state & 4u);
 #pragma unroll
   for (int w = 0; w < W; ++w) {
-    Xs[64 * w + lane] = transpose32((uint32_t)X[w], lane);
-    Xs[64 * w + 32 + lane] = transpose32((uint32_t)(X[w] >> 32), lane);
+    const uint32_t lo = transpose32((uint32_t)X[w]), hi = transpose32((uint32_t)(X[w] >> 32));
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)(64 * w + lane)), "r"(lo) : "memory");
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)(64 * w + 32 + lane)), "r"(hi) : "memory");
   }
-  __syncwarp();
-  // every distinct parity as the XOR of the X bits in its mask, 32 shots at once
-  // (masks have V.W <= W words; a batched launch may run with a larger W)
-  const int ws = V.W;
-  const uint64_t* pm = V.par + (size_t)tb.par_off * ws;
-  for (uint32_t q = lane; q < tb.n_par; q += 32) {
-    uint32_t acc = 0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) {
-      uint64_t m = w < ws ? __ldg(pm + (size_t)q * ws + w) : 0ull;
-      while (m) {
-        acc ^= Xs[64 * w + (__ffsll((long long)m) - 1)];
-        m &= m - 1;
-      }
-    }
-    Par[q] = q == kSlOnes ? 0xFFFFFFFFu : acc;
-  }
-  __syncwarp();
   ZC z{{0, 0, 0, 0}, tb.base};
   long long (&c)[4] = z.c;
-  const DSBatch* bt = V.sb + tb.sb_off;
-  for (int b = 0; b < tb.n_sb; ++b) {
-    const DSBatch B = bt[b];
-    const uint32_t* R = V.rows + B.row_off + lane;
-    uint32_t J0 = 0u - ((B.j0m[0] >> lane) & 1u);
-    uint32_t J1 = 0u - ((B.j0m[1] >> lane) & 1u);
-    uint32_t J2 = 0u - ((B.j0m[2] >> lane) & 1u);
-    uint32_t Z = 0u - ((~B.valid >> lane) & 1u);
-    uint32_t K2 = 0, K2b = 0, Zb = 0;  // J2 flips and vanishing flags commute with the additions
-    {
-      const int n = B.cnt[SL_XOR4];
-      int k = 0;
-      for (; k + 1 < n; k += 2, R += 64) {
-        K2 ^= Par[__ldg(R)];
-        K2b ^= Par[__ldg(R + 32)];
-      }
-      if (k < n) { K2 ^= Par[__ldg(R)]; R += 32; }
-    }
-    for (int k = 0; k < B.cnt[SL_ADD2]; ++k, R += 32) {
-      const uint32_t A = Par[__ldg(R)];
-      J2 ^= J1 & A;
-      J1 ^= A;
-    }
-    for (int k = 0; k < B.cnt[SL_ADD6]; ++k, R += 32) {
-      const uint32_t A = Par[__ldg(R)];
-      J2 ^= ~J1 & A;
-      J1 ^= A;
-    }
-    {
-      const int n = B.cnt[SL_XOR4AB];
-      int k = 0;
-      for (; k + 1 < n; k += 2, R += 64) {
-        const uint32_t r0 = __ldg(R), r1 = __ldg(R + 32);
-        K2 ^= Par[r0 & 0xFFFFu] & Par[r0 >> 16];
-        K2b ^= Par[r1 & 0xFFFFu] & Par[r1 >> 16];
-      }
-      if (k < n) {
-        const uint32_t r0 = __ldg(R);
-        K2 ^= Par[r0 & 0xFFFFu] & Par[r0 >> 16];
-        R += 32;
-      }
-    }
-    {
-      const int n = B.cnt[SL_ZERO];
-      int k = 0;
-      for (; k + 1 < n; k += 2, R += 64) {
-        Z |= Par[__ldg(R)];
-        Zb |= Par[__ldg(R + 32)];
-      }
-      if (k < n) { Z |= Par[__ldg(R)]; R += 32; }
-    }
-    for (int k = 0; k < B.cnt[SL_ZEROC]; ++k, R += 32) Z |= ~Par[__ldg(R)];
-    for (int k = 0; k < B.cnt[SL_ADD1]; ++k, R += 32) {
-      const uint32_t A = Par[__ldg(R)];
-      const uint32_t cy = J0 & A;
-      J0 ^= A;
-      J2 ^= J1 & cy;
-      J1 ^= cy;
-    }
-    J2 ^= K2 ^ K2b;
-    Z |= Zb;
-    // lane s now needs, for each of the 32 terms, its phase and flag at shot s
-    const uint32_t T0 = transpose32(J0, lane), T1 = transpose32(J1, lane);
-    const uint32_t T2 = transpose32(J2, lane), TZ = transpose32(Z, lane);
-    const uint32_t nz = ~TZ;
-    const uint32_t M[4] = {~T0 & ~T1 & nz, T0 & ~T1 & nz, ~T0 & T1 & nz, T0 & T1 & nz};
+  bool ok = true;
+  // signed counts of the batches since the magnitude sqrt2^d last changed
+  // (batches are sorted by d within a segment; |n| <= 32 per batch)
+  int n[4] = {0, 0, 0, 0};
+  int d_cur = 0;
+  auto flush = [&]() {
+    const int sh = d_cur >> 1;
     long long r[4];
-    const int sh = B.d >> 1;
 #pragma unroll
-    for (int q = 0; q < 4; ++q)  // terms with J = q count +1, with J = q + 4 count -1
-      r[q] = (long long)(__popc(M[q]) - 2 * __popc(M[q] & T2)) << sh;
-    if (B.d & 1) {  // times sqrt2 = w - w^3
+    for (int q = 0; q < 4; ++q) {
+      r[q] = (long long)n[q] << sh;
+      n[q] = 0;
+    }
+    if (d_cur & 1) {  // times sqrt2 = w - w^3
       c[0] += r[1] - r[3];
       c[1] += r[0] + r[2];
       c[2] += r[1] + r[3];
@@ -414,14 +552,107 @@ __device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64
 #pragma unroll
       for (int q = 0; q < 4; ++q) c[q] += r[q];
     }
+  };
+  const int ws = V.W;  // masks have V.W <= W words (a batched launch may run with a larger W)
+  uint32_t bi = 0;     // batches so far: the staging buffer alternates with it
+  for (int g = 0; g < tb.n_sb; ++g) {
+    const DSeg sg = V.seg[tb.sb_off + g];
+    const DSBatch* bt = V.sb + sg.sb_off;
+    DSBatch next = sg.n_sb > 0 ? bt[0] : DSBatch{};
+    __syncwarp();  // every lane is done with the previous segment's parity words
+    // rows of batches that fit the buffers go through shared memory; the
+    // segment's first copy overlaps its parity computation below
+    if (staged && ok && lane == 0 && sg.n_sb > 0) {
+      fence_proxy_async();
+      bulk_load((bi & 1) ? S.rb1 : S.rb0, V.rows + next.row_off, 128u * sl_batch_rows(next), (bi & 1) ? S.bar1 : S.bar0);
+    }
+    // the segment's parities as XORs of the X bits in their masks, 32 shots
+    // at once; four per lane at a time so that their mask loads overlap
+    const uint64_t* pm = V.par + (size_t)sg.par_off * ws;
+    for (uint32_t q0 = lane; q0 < sg.n_par; q0 += 128) {
+      uint64_t m[4][W];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t q = q0 + 32u * (uint32_t)u;
+#pragma unroll
+        for (int w = 0; w < W; ++w) m[u][w] = (w < ws && q < sg.n_par) ? __ldg(pm + (size_t)q * ws + w) : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const uint32_t q = q0 + 32u * (uint32_t)u;
+        uint32_t acc = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          uint64_t x = m[u][w];
+          while (x) {
+            acc ^= lds(S.xs + 4u * (uint32_t)(64 * w + __ffsll((long long)x) - 1));
+            x &= x - 1;
+          }
+        }
+        if (q < sg.n_par)
+          asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.par + 4u * q), "r"(q == kSlOnes ? 0xFFFFFFFFu : acc)
+                       : "memory");
+      }
+    }
+    __syncwarp();
+    for (uint32_t b = 0; b < sg.n_sb; ++b, ++bi) {
+      const DSBatch B = next;
+      if (b + 1 < sg.n_sb) next = bt[b + 1];  // the next header's load overlaps this batch
+      uint32_t J0, J1, J2, Z;
+      if (staged && ok) {
+        const uint32_t buf = bi & 1;
+        // the other buffer held the previous batch, which every lane has finished
+        if (lane == 0 && b + 1 < sg.n_sb) {
+          fence_proxy_async();
+          bulk_load(buf ? S.rb0 : S.rb1, V.rows + next.row_off, 128u * sl_batch_rows(next), buf ? S.bar0 : S.bar1);
+        }
+        const uint32_t bar = buf ? S.bar1 : S.bar0;
+        if (!mbar_wait_bounded(bar, (state >> buf) & 1u)) {
+          // a copy that does not land in time: report it, let the copies in
+          // flight finish (bounded), and read rows from global memory
+          if (lane == 0) atomicOr(&g_status, ST_TIMEOUT);
+          mbar_wait_bounded(S.bar0, state & 1u);
+          mbar_wait_bounded(S.bar1, (state >> 1) & 1u);
+          ok = false;
+          state |= 4u;
+        } else {
+          state ^= 1u << buf;
+          sl_batch(B, RowsS{(buf ? S.rb1 : S.rb0) + 4u * (uint32_t)lane}, S.par, lane, J0, J1, J2, Z);
+        }
+      }
+      if (!staged || !ok) sl_batch(B, RowsG{V.rows + B.row_off + lane}, S.par, lane, J0, J1, J2, Z);
+      __syncwarp();
+      // lane s now needs, for each of the 32 terms, its phase and flag at shot s
+      const uint32_t T0 = transpose32(J0), T1 = transpose32(J1);
+      const uint32_t T2 = transpose32(J2), TZ = transpose32(Z);
+      const uint32_t nz = ~TZ;
+      const uint32_t M[4] = {~T0 & ~T1 & nz, T0 & ~T1 & nz, ~T0 & T1 & nz, T0 & T1 & nz};
+      if (B.d != d_cur) {
+        flush();
+        d_cur = B.d;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)  // terms with J = q count +1, with J = q + 4 count -1
+        n[q] += __popc(M[q]) - 2 * __popc(M[q] & T2);
+    }
+  }
+  flush();
+  if (S.rb > 0) {
+    __syncwarp();
+    if (lane == 0) asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.state), "r"(state) : "memory");
+    __syncwarp();
   }
   return z;
 }
 
-template <int W>
-__device__ ZC eval_table(const DevView& V, int t, const uint64_t (&X)[W], uint32_t* sm) {
+// SL: the program has sliced tables (kernels without them never contain the
+// warp-cooperative code and keep their register budget)
+template <int W, bool SL>
+__device__ ZC eval_table(const DevView& V, int t, const uint64_t (&X)[W], const SlSmem& sm) {
   const DTable tb = V.tab[t];
-  if (tb.mode == TAB_SLICED) return eval_table_sliced<W>(V, tb, X, sm);
+  if constexpr (SL) {
+    if (tb.mode == TAB_SLICED) return eval_table_sliced<W>(V, tb, X, sm);
+  }
   ZC z{{0, 0, 0, 0}, tb.base};
   long long (&c)[4] = z.c;
   if (tb.mode == TAB_BASIS) {
@@ -509,10 +740,10 @@ __device__ __forceinline__ int get_xbit(const uint64_t (&X)[W], int b) {
 // Every lane of a warp calls it together (sliced tables are evaluated by the
 // whole warp); lanes past the end of the launch have valid = false and
 // compute a shot whose records are not written.  sm: the warp's shared words.
-template <int W>
+template <int W, bool SL>
 __device__ void sample_one(const DevView& V, uint64_t s, bool valid, uint64_t seed, uint64_t shot0,
                            uint64_t* __restrict__ meas, uint64_t* __restrict__ det,
-                           uint64_t* __restrict__ obs, uint8_t* __restrict__ accept, uint32_t* sm) {
+                           uint64_t* __restrict__ obs, uint8_t* __restrict__ accept, const SlSmem& sm) {
   const uint64_t shot = shot0 + s;
   RoundKeys rk;
   {
@@ -557,7 +788,7 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, uint64_t se
   RV pp[kMaxChains];
   int rot[kMaxChains];
   for (int c = 0; c < V.n_chains; ++c) {
-    const ZC z = eval_table<W>(V, V.chain_norm[c], X, sm);
+    const ZC z = eval_table<W, SL>(V, V.chain_norm[c], X, sm);
     rot[c] = chain_rotation(z, &st);
     pp[c] = to_real_rot(z, rot[c], &st);
   }
@@ -574,7 +805,7 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, uint64_t se
       bit = parity_w<W>(V.omask + o.a, X, V.W) ^ o.cst;
     } else {
       set_xbit<W>(X, o.a, true);
-      const RV p1 = to_real_rot(eval_table<W>(V, o.table, X, sm), rot[o.chain], &st);
+      const RV p1 = to_real_rot(eval_table<W, SL>(V, o.table, X, sm), rot[o.chain], &st);
       const RV pv = pp[o.chain];
       if (sign_xy(pv.A, pv.B, &st) <= 0) st |= ST_ZERO_PROB;
       uint32_t u[4];
@@ -658,18 +889,22 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, uint64_t se
   if (st) atomicOr(&g_status, st);
 }
 
-// dynamic shared memory: sl_words per warp for programs with sliced tables
-extern __shared__ uint32_t g_warp_smem[];
+// dynamic shared memory: sl_warp_words(...) per warp for programs with sliced tables
+extern __shared__ __align__(128) uint32_t g_warp_smem[];
 
-template <int W>
+template <int W, bool SL>
 __global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, uint64_t shot0,
                                                      uint64_t nshots, uint64_t* __restrict__ meas,
                                                      uint64_t* __restrict__ det,
                                                      uint64_t* __restrict__ obs,
                                                      uint8_t* __restrict__ accept) {
   const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t* sm = g_warp_smem + (threadIdx.x >> 5) * V.sl_words;
-  sample_one<W>(V, s, s < nshots, seed, shot0, meas, det, obs, accept, sm);
+  SlSmem sm{};
+  if constexpr (SL) {
+    sm = sl_smem(g_warp_smem + (threadIdx.x >> 5) * sl_warp_words(W, V.sl_par, V.sl_rb), W, V.sl_par, V.sl_rb);
+    sl_init(sm);
+  }
+  sample_one<W, SL>(V, s, s < nshots, seed, shot0, meas, det, obs, accept, sm);
 }
 
 // ------------------------------------------------------- batched launch
@@ -686,13 +921,17 @@ struct BatchProg {
   uint8_t* accept;
 };
 
-template <int W>
+template <int W, bool SL>
 __global__ void __launch_bounds__(kThreads) k_batch(const BatchProg* __restrict__ progs, int n,
                                                     const uint64_t* __restrict__ item_start,
                                                     uint64_t total_items, uint32_t sb,
-                                                    unsigned long long* counter, int sl_stride) {
+                                                    unsigned long long* counter, int sl_par, int sl_rb) {
   __shared__ unsigned long long item;
-  uint32_t* sm = g_warp_smem + (threadIdx.x >> 5) * sl_stride;
+  SlSmem sm{};
+  if constexpr (SL) {
+    sm = sl_smem(g_warp_smem + (threadIdx.x >> 5) * sl_warp_words(W, sl_par, sl_rb), W, sl_par, sl_rb);
+    sl_init(sm);
+  }
   for (;;) {
     if (threadIdx.x == 0) item = atomicAdd(counter, 1ull);
     __syncthreads();
@@ -710,7 +949,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const BatchProg* __restrict_
     const uint64_t last = min(first + sb, P.shots);
     for (uint64_t s0 = first; s0 < last; s0 += blockDim.x) {
       const uint64_t s = s0 + threadIdx.x;
-      sample_one<W>(P.v, s, s < last, P.seed, P.shot_offset, P.meas, P.det, P.obs, P.accept, sm);
+      sample_one<W, SL>(P.v, s, s < last, P.seed, P.shot_offset, P.meas, P.det, P.obs, P.accept, sm);
     }
   }
 }
@@ -797,7 +1036,7 @@ struct FacKey {
 struct SlTerm {
   int d = 0, j = 0;
   bool dead = false;
-  std::vector<uint32_t> ops[kSlCodes];
+  std::vector<uint64_t> ops[kSlCodes];  // parity indices (qa | qb << 32 for pi-pairs)
 };
 
 // How one factor acts on (J, Z): J += j00 + da a + db b + dab ab (mod 8) on
@@ -878,7 +1117,8 @@ bool sliced_term(const std::vector<FacKey>& f, int j, int d, LutFn& lut, SlTerm&
   t.d = d;
   int jc = j;
   std::map<uint32_t, int> delta;
-  std::set<uint32_t> pairs, zp, zn;
+  std::set<uint64_t> pairs;
+  std::set<uint32_t> zp, zn;
   for (const FacKey& k : f) {
     const uint32_t qa = k.ia ? (uint32_t)k.ia + 1 : 0u, qb = k.ib ? (uint32_t)k.ib + 1 : 0u;
     const bool za = qa == 0, zb = qb == 0, same = qa != 0 && qa == qb;
@@ -897,7 +1137,7 @@ bool sliced_term(const std::vector<FacKey>& f, int j, int d, LutFn& lut, SlTerm&
     if (dec.da) delta[qa] = (delta[qa] + dec.da) & 7;
     if (dec.db) delta[qb] = (delta[qb] + dec.db) & 7;
     if (dec.dab) {
-      const uint32_t key = std::min(qa, qb) | (std::max(qa, qb) << 16);
+      const uint64_t key = (uint64_t)std::min(qa, qb) | ((uint64_t)std::max(qa, qb) << 32);
       if (!pairs.erase(key)) pairs.insert(key);  // (-1)^(ab) twice is 1
     }
     if (dec.zop == 1) zp.insert(qa);
@@ -908,6 +1148,7 @@ bool sliced_term(const std::vector<FacKey>& f, int j, int d, LutFn& lut, SlTerm&
   for (uint32_t q : zp)
     if (zn.count(q)) { t.dead = true; return true; }
   t.j = jc & 7;
+  // table-wide parity indices q (qa | qb << 32 for pi-pairs)
   for (const auto& [q, dl] : delta) {
     if (dl & 1) t.ops[SL_ADD1].push_back(q);
     const int rem = dl & 6;
@@ -915,13 +1156,13 @@ bool sliced_term(const std::vector<FacKey>& f, int j, int d, LutFn& lut, SlTerm&
     if (rem == 4) t.ops[SL_XOR4].push_back(q);
     if (rem == 6) t.ops[SL_ADD6].push_back(q);
   }
-  t.ops[SL_XOR4AB].assign(pairs.begin(), pairs.end());
-  t.ops[SL_ZERO].assign(zp.begin(), zp.end());
-  t.ops[SL_ZEROC].assign(zn.begin(), zn.end());
+  for (uint64_t pq : pairs) t.ops[SL_XOR4AB].push_back(pq);
+  for (uint32_t q : zp) t.ops[SL_ZERO].push_back(q);
+  for (uint32_t q : zn) t.ops[SL_ZEROC].push_back(q);
   return true;
 }
 
-void pack(const Program& p, DeviceTables& out, int64_t sliced_min) {
+void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_rows, int seg_par) {
   std::map<std::tuple<int, int, int>, Lut> lut_cache;
   auto lut = [&](int kind, int alpha, int beta) -> const Lut& {
     auto key = std::make_tuple(kind, alpha & 7, beta & 7);
@@ -1006,6 +1247,7 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min) {
   std::vector<uint32_t> fidx, finc;
   std::vector<uint64_t> fcoord;
   std::vector<DSBatch> sbs;
+  std::vector<DSeg> segs;
   std::vector<uint32_t> rows;
   for (const ProgTable& tb : p.tables) {
     DTable dt{};
@@ -1091,8 +1333,7 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min) {
 
     // ---- bit-sliced layout (large tables whose factors all reduce to
     // operations on J and Z, every term a monomial)
-    bool sliced = sliced_min >= 0 && prep.size() >= (size_t)std::max<int64_t>(sliced_min, 1) &&
-                  plist.size() + 1 <= (size_t)kSlMaxPar;
+    bool sliced = sliced_min >= 0 && prep.size() >= (size_t)std::max<int64_t>(sliced_min, 1);
     std::vector<SlTerm> sterms;
     for (size_t q = 0; sliced && q < prep.size(); ++q) {
       const Prep& pr = prep[q];
@@ -1101,58 +1342,131 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min) {
       if (!sliced_term(cl[pr.i].f, pr.j, pr.raw - base, lut, t)) { sliced = false; break; }
       if (!t.dead) sterms.push_back(std::move(t));
     }
-    uint64_t real_ops = 0, padded_rows = 0;
+    uint64_t real_ops = 0, padded_rows = 0, sliced_work = 0, nbatches = 0;
     if (sliced) {
       dt.mode = TAB_SLICED;
-      dt.par_off = (uint32_t)(par.size() / (size_t)W);
-      par.insert(par.end(), plist[0].begin(), plist[0].end());  // 0: the zero parity
-      par.insert(par.end(), (size_t)W, 0ull);                   // kSlOnes: all ones (set on the device)
-      for (size_t i = 1; i < plist.size(); ++i) par.insert(par.end(), plist[i].begin(), plist[i].end());
-      dt.n_par = (uint32_t)plist.size() + 1;
-      dt.sb_off = (int32_t)sbs.size();
-      std::stable_sort(sterms.begin(), sterms.end(), [](const SlTerm& a, const SlTerm& b) {
-        if (a.d != b.d) return a.d < b.d;
-        size_t na = 0, nb = 0;
-        for (int c = 0; c < kSlCodes; ++c) { na += a.ops[c].size(); nb += b.ops[c].size(); }
-        if (na != nb) return na > nb;
+      dt.sb_off = (int32_t)segs.size();  // sliced: the table's segments
+      // integer lane-operations of one warp (32 shots) on this table: the
+      // bit transpose of X (2W transposes of 5 stages of 4 ops, 32 lanes), per
+      // segment each parity (load, store, and per mask bit: find, load, XOR),
+      // each padded row on 32 lanes (index load, parity load and the word
+      // operations of its code), and per batch 4 transposes, the signed
+      // counts and their accumulation (about 110 per lane)
+      static const int kRowOps[kSlCodes] = {3, 4, 5, 6, 3, 3, 6};
+      uint64_t w32 = 2ull * (uint64_t)W * 5 * 4 * 32;
+      uint32_t most = 0;
+      auto parities_of = [](const SlTerm& t, std::vector<uint32_t>& out) {
+        out.clear();
         for (int c = 0; c < kSlCodes; ++c)
-          if (a.ops[c].size() != b.ops[c].size()) return a.ops[c].size() > b.ops[c].size();
-        return false;
-      });
+          for (uint64_t r : t.ops[c]) {
+            out.push_back((uint32_t)r);
+            if (c == SL_XOR4AB) out.push_back((uint32_t)(r >> 32));
+          }
+      };
+      // segments: consecutive terms (the decomposition's order keeps their
+      // parities local) while the parity list stays within seg_par words
+      std::vector<uint32_t> tp;
       for (size_t t0 = 0; t0 < sterms.size();) {
+        std::set<uint32_t> ps;
         size_t t1 = t0;
-        while (t1 < sterms.size() && t1 - t0 < 32 && sterms[t1].d == sterms[t0].d) ++t1;
-        DSBatch B{};
-        B.row_off = (uint32_t)rows.size();
-        B.d = sterms[t0].d;
-        for (size_t l = 0; l < t1 - t0; ++l) {
-          const SlTerm& t = sterms[t0 + l];
-          B.valid |= 1u << l;
-          for (int bit = 0; bit < 3; ++bit) B.j0m[bit] |= (uint32_t)((t.j >> bit) & 1) << l;
+        while (t1 < sterms.size()) {
+          parities_of(sterms[t1], tp);
+          size_t add = 0;
+          for (uint32_t q : tp) add += q > kSlOnes && !ps.count(q);
+          if (t1 > t0 && ps.size() + add + 2 > (size_t)seg_par) break;
+          for (uint32_t q : tp)
+            if (q > kSlOnes) ps.insert(q);
+          ++t1;
         }
-        for (int c = 0; c < kSlCodes; ++c) {
-          size_t n = 0;
-          for (size_t l = t0; l < t1; ++l) n = std::max(n, sterms[l].ops[c].size());
-          if (n > 0xFFFF) throw PackError{TSIM_ERR_ARG, "too many operations of one kind in a term"};
-          B.cnt[c] = (uint16_t)n;
-          for (size_t k = 0; k < n; ++k)
-            for (size_t l = 0; l < 32; ++l) {
-              const size_t ti = t0 + l;
-              uint32_t r = c == SL_ZEROC ? kSlOnes : 0u;  // padding leaves J and Z unchanged
-              if (ti < t1 && k < sterms[ti].ops[c].size()) {
-                r = sterms[ti].ops[c][k];
-                ++real_ops;
+        if (ps.size() + 2 > (size_t)kSlMaxPar) throw PackError{TSIM_ERR_ARG, "a sliced term has too many parities"};
+        DSeg g{};
+        g.par_off = (uint32_t)(par.size() / (size_t)W);
+        par.insert(par.end(), plist[0].begin(), plist[0].end());  // 0: the zero parity
+        par.insert(par.end(), (size_t)W, 0ull);                   // kSlOnes: all ones (set on the device)
+        std::map<uint32_t, uint32_t> local;
+        local[0] = 0;
+        local[kSlOnes] = kSlOnes;
+        for (uint32_t q : ps) {  // table index q is plist[q - 1]
+          local[q] = (uint32_t)local.size();
+          par.insert(par.end(), plist[q - 1].begin(), plist[q - 1].end());
+        }
+        g.n_par = (uint32_t)local.size();
+        for (uint32_t q : ps) {
+          uint64_t pop = 0;
+          for (uint64_t m : plist[q - 1]) pop += (uint64_t)__builtin_popcountll(m);
+          w32 += 3 + 3 * pop;
+        }
+        w32 += 2 * 3;
+        // rows hold byte offsets of the segment's parity words: 4q, or
+        // 4qa | 4qb << 16 for pi-pairs
+        std::vector<SlTerm> lt(sterms.begin() + (long)t0, sterms.begin() + (long)t1);
+        for (SlTerm& t : lt)
+          for (int c = 0; c < kSlCodes; ++c) {
+            for (uint64_t& r : t.ops[c])
+              r = c == SL_XOR4AB ? ((uint64_t)(4 * local.at((uint32_t)r)) | ((uint64_t)(4 * local.at((uint32_t)(r >> 32))) << 16))
+                                 : (uint64_t)(4 * local.at((uint32_t)r));
+            std::sort(t.ops[c].begin(), t.ops[c].end());
+          }
+        std::stable_sort(lt.begin(), lt.end(), [](const SlTerm& a, const SlTerm& b) {
+          if (a.d != b.d) return a.d < b.d;
+          size_t na = 0, nb = 0;
+          for (int c = 0; c < kSlCodes; ++c) { na += a.ops[c].size(); nb += b.ops[c].size(); }
+          if (na != nb) return na > nb;
+          for (int c = 0; c < kSlCodes; ++c)
+            if (a.ops[c].size() != b.ops[c].size()) return a.ops[c].size() > b.ops[c].size();
+          return false;
+        });
+        g.sb_off = (uint32_t)sbs.size();
+        for (size_t b0 = 0; b0 < lt.size();) {
+          size_t b1 = b0;
+          while (b1 < lt.size() && b1 - b0 < 32 && lt[b1].d == lt[b0].d) ++b1;
+          DSBatch B{};
+          B.row_off = (uint32_t)rows.size();
+          B.d = lt[b0].d;
+          for (size_t l = 0; l < b1 - b0; ++l) {
+            const SlTerm& t = lt[b0 + l];
+            B.valid |= 1u << l;
+            for (int bit = 0; bit < 3; ++bit) B.j0m[bit] |= (uint32_t)((t.j >> bit) & 1) << l;
+          }
+          uint32_t nrows = 0;
+          for (int c = 0; c < kSlCodes; ++c) {
+            size_t n = 0;
+            for (size_t l = b0; l < b1; ++l) n = std::max(n, lt[l].ops[c].size());
+            n = (n + 3) & ~(size_t)3;  // whole groups of 4 rows: no single-row tail loop on the device
+            if (n > 0xFFFF) throw PackError{TSIM_ERR_ARG, "too many operations of one kind in a term"};
+            B.cnt[c] = (uint16_t)n;
+            for (size_t k = 0; k < n; ++k)
+              for (size_t l = 0; l < 32; ++l) {
+                const size_t ti = b0 + l;
+                uint32_t r = c == SL_ZEROC ? 4 * kSlOnes : 0u;  // padding leaves J and Z unchanged
+                if (ti < b1 && k < lt[ti].ops[c].size()) {
+                  r = (uint32_t)lt[ti].ops[c][k];
+                  ++real_ops;
+                }
+                rows.push_back(r);
               }
-              rows.push_back(r);
-            }
-          padded_rows += n;
+            padded_rows += n;
+            nrows += (uint32_t)n;
+            w32 += (uint64_t)n * 32 * (uint64_t)kRowOps[c];
+          }
+          w32 += 32 * 110;
+          most = std::max(most, nrows);
+          if (rows.size() > 0xFFFFFFFFull) throw PackError{TSIM_ERR_ARG, "sliced tables too large"};
+          sbs.push_back(B);
+          b0 = b1;
         }
-        if (rows.size() > 0xFFFFFFFFull) throw PackError{TSIM_ERR_ARG, "sliced tables too large"};
-        sbs.push_back(B);
+        g.n_sb = (uint32_t)(sbs.size() - g.sb_off);
+        nbatches += g.n_sb;
+        L.sl_par_max = std::max<uint32_t>(L.sl_par_max, g.n_par);
+        segs.push_back(g);
         t0 = t1;
       }
-      dt.n_sb = (int32_t)(sbs.size() - (size_t)dt.sb_off);
-      L.sl_par_max = std::max<uint32_t>(L.sl_par_max, dt.n_par);
+      dt.n_sb = (int32_t)(segs.size() - (size_t)dt.sb_off);
+      dt.n_par = 0;
+      // stage the rows through shared memory when every batch fits a buffer
+      dt.stage = stage_rows > 0 && most <= (uint32_t)stage_rows ? 1 : 0;
+      if (dt.stage) L.sl_rows_max = std::max(L.sl_rows_max, most);
+      sliced_work = w32;
     } else {
       // few distinct parities: evaluate each once per shot and index them;
       // many: evaluate a GF(2) basis of their span and give every parity its
@@ -1223,9 +1537,10 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min) {
       L.class_factors += nf;
     }
     L.table_mode.push_back(dt.mode);
-    L.table_batches.push_back((uint64_t)std::max(dt.n_sb, 0));
+    L.table_batches.push_back(nbatches);
     L.table_rows.push_back(padded_rows);
     L.table_ops.push_back(real_ops);
+    L.table_work32.push_back(sliced_work);
     tabs.push_back(dt);
   }
   L.o_tab = s.section();
@@ -1240,11 +1555,14 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min) {
   if (!finc.empty()) s.put(finc.data(), finc.size() * 4);
   L.o_fco = s.section();
   if (!fcoord.empty()) s.put(fcoord.data(), fcoord.size() * 8);
+  L.o_seg = s.section();
+  if (!segs.empty()) s.put(segs.data(), segs.size() * sizeof(DSeg));
   L.o_sb = s.section();
   if (!sbs.empty()) s.put(sbs.data(), sbs.size() * sizeof(DSBatch));
   L.o_row = s.section();
   if (!rows.empty()) s.put(rows.data(), rows.size() * 4);
-  L.sl_words = L.sl_par_max ? 64 * W + (int)L.sl_par_max : 0;
+  L.sl_par = L.sl_par_max ? (int)((L.sl_par_max + 3) & ~3u) : 0;
+  L.sl_rb = (int)L.sl_rows_max * 32;
   // measurement-mode detector / observable maps (CSR)
   auto csr = [&](const std::vector<std::vector<int>>& m, size_t* o_off, size_t* o_idx) {
     *o_off = s.section();
@@ -1286,9 +1604,11 @@ DevView make_view(const unsigned char* base, const DeviceLayout& L, const Progra
   v.fidx = (const uint32_t*)(base + L.o_fidx);
   v.finc = (const uint32_t*)(base + L.o_finc);
   v.fcoord = (const uint64_t*)(base + L.o_fco);
+  v.seg = (const DSeg*)(base + L.o_seg);
   v.sb = (const DSBatch*)(base + L.o_sb);
   v.rows = (const uint32_t*)(base + L.o_row);
-  v.sl_words = L.sl_words;
+  v.sl_par = L.sl_par;
+  v.sl_rb = L.sl_rb;
   v.dmap_off = (const int32_t*)(base + L.o_dmo);
   v.dmap_idx = (const int32_t*)(base + L.o_dmi);
   v.omap_off = (const int32_t*)(base + L.o_omo);
@@ -1334,8 +1654,9 @@ const DevView& ensure_uploaded(const Program& p) {
 }
 
 // Threads per block and dynamic shared memory of a launch: programs with
-// sliced tables get sl_words words per warp and as many warps per block (1 to
-// 4) as fit in kSmemPerBlock; the others use kThreads threads and none.
+// sliced tables get sl_words words per warp (sl_warp_words) and as many warps
+// per block (1 to 4) as fit in kSmemPerBlock; the others use kThreads
+// threads and none.
 constexpr int kSmemPerBlock = 48 * 1024;
 
 struct LaunchShape {
@@ -1360,12 +1681,16 @@ cudaError_t allow_smem(K kernel, size_t smem) {
 template <int W>
 cudaError_t launch_w(const DevView& v, cudaStream_t s, uint64_t seed, uint64_t off, uint64_t shots, uint64_t* meas,
                      uint64_t* det, uint64_t* obs, uint8_t* acc) {
-  const LaunchShape sh = shape_of(v.sl_words);
+  const LaunchShape sh = shape_of(sl_warp_words(W, v.sl_par, v.sl_rb));
   const uint64_t blocks = (shots + sh.threads - 1) / sh.threads;
   if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-  cudaError_t e = allow_smem(k_sample<W>, sh.smem);
-  if (e != cudaSuccess) return e;
-  k_sample<W><<<(unsigned)blocks, sh.threads, sh.smem, s>>>(v, seed, off, shots, meas, det, obs, acc);
+  if (v.sl_par > 0) {
+    cudaError_t e = allow_smem(k_sample<W, true>, sh.smem);
+    if (e != cudaSuccess) return e;
+    k_sample<W, true><<<(unsigned)blocks, sh.threads, sh.smem, s>>>(v, seed, off, shots, meas, det, obs, acc);
+  } else {
+    k_sample<W, false><<<(unsigned)blocks, sh.threads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc);
+  }
   return cudaGetLastError();
 }
 
@@ -1384,10 +1709,11 @@ cudaError_t launch(const DevView& v, cudaStream_t s, uint64_t seed, uint64_t off
 
 }  // namespace
 
-void prepare_device_tables(Program& p, int64_t sliced_min) {
+void prepare_device_tables(Program& p, int64_t sliced_min, int stage_rows, int seg_par) {
   auto* t = new DeviceTables();
   try {
-    pack(p, *t, sliced_min);
+    pack(p, *t, sliced_min, stage_rows < 0 ? kDefaultStageRows : stage_rows,
+         seg_par <= 0 ? kDefaultSegmentParities : std::max(seg_par, 16));
   } catch (const PackError& e) {
     t->status = e.st;
     t->message = e.msg;
@@ -1410,7 +1736,8 @@ void device_sample(const Program& p, const SampleArgs& a, void* stream) {
 // ----------------------------------------------------------- batch plans
 struct BatchPlan {
   int device = -1, n = 0, wmax = 1, sms = 1;
-  int sl_par_max = 0;       // largest sliced parity list over the programs (0: none)
+  int sl_par_max = 0;       // largest sliced parity buffer over the programs (0: none)
+  int sl_rb = 0;            // largest row staging buffer over the programs
   uint32_t sb = 512;        // shots per work item
   int blocks_per_sm = 8;
   uint64_t total_items = 0;
@@ -1436,14 +1763,18 @@ void plan_items(BatchPlan& b, cudaStream_t s) {
 
 template <int W>
 cudaError_t launch_batch_w(const BatchPlan& b, cudaStream_t s, unsigned grid) {
-  // every warp gets room for the transposed X at the launch's W plus the
-  // largest sliced parity list of any program
-  const int stride = b.sl_par_max ? 64 * W + b.sl_par_max : 0;
-  const LaunchShape sh = shape_of(stride);
-  cudaError_t e = allow_smem(k_batch<W>, sh.smem);
-  if (e != cudaSuccess) return e;
-  k_batch<W><<<grid, sh.threads, sh.smem, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter,
-                                               stride);
+  // every warp gets room for the transposed X at the launch's W, the
+  // largest sliced parity buffer and the largest row buffers of any program
+  const LaunchShape sh = shape_of(sl_warp_words(W, b.sl_par_max, b.sl_rb));
+  if (b.sl_par_max > 0) {
+    cudaError_t e = allow_smem(k_batch<W, true>, sh.smem);
+    if (e != cudaSuccess) return e;
+    k_batch<W, true><<<grid, sh.threads, sh.smem, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb,
+                                                       b.d_counter, b.sl_par_max, b.sl_rb);
+  } else {
+    k_batch<W, false><<<grid, sh.threads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter,
+                                                  0, 0);
+  }
   return cudaGetLastError();
 }
 
@@ -1486,7 +1817,8 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
     bp.obs = args[i].obs;
     bp.accept = args[i].accept;
     b->wmax = std::max(b->wmax, bp.v.W);
-    if (bp.v.sl_words) b->sl_par_max = std::max(b->sl_par_max, bp.v.sl_words - 64 * bp.v.W);
+    b->sl_par_max = std::max(b->sl_par_max, bp.v.sl_par);
+    b->sl_rb = std::max(b->sl_rb, bp.v.sl_rb);
     b->h_progs.push_back(bp);
   }
   const size_t bytes = (size_t)n * sizeof(BatchProg) + ((size_t)n + 1) * 8 + 64;
@@ -1499,6 +1831,7 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
   TSIM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   struct SD { cudaStream_t s; ~SD() { cudaStreamDestroy(s); } } sd{s};
   if (n) TSIM_CUDA(cudaMemcpyAsync(b->d_progs, b->h_progs.data(), (size_t)n * sizeof(BatchProg), cudaMemcpyHostToDevice, s));
+  b->sb = 4 * shape_of(sl_warp_words(b->wmax, b->sl_par_max, b->sl_rb)).threads;
   plan_items(*b, s);
   if (autotune && b->total_items) {
     // shot-block size x resident blocks per SM: time every candidate twice on
@@ -1509,7 +1842,10 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
     float best = 1e30f;
     uint32_t best_sb = b->sb;
     int best_bps = b->blocks_per_sm;
-    for (uint32_t sb : {128u, 512u, 2048u}) {
+    // shot blocks of 1, 4 and 16 times the block's threads (128 threads, or
+    // 32 to 128 for programs with sliced tables)
+    const unsigned thr = shape_of(sl_warp_words(b->wmax, b->sl_par_max, b->sl_rb)).threads;
+    for (uint32_t sb : {thr, 4 * thr, 16 * thr}) {
       b->sb = sb;
       plan_items(*b, s);
       for (int bps : {4, 8, 16}) {
@@ -1587,6 +1923,7 @@ void device_sync(void* stream) {
   if (st) {
     int z = 0;
     TSIM_CUDA(cudaMemcpyToSymbol(g_status, &z, sizeof z));
+    if (st & ST_TIMEOUT) fail(TSIM_ERR_TIMEOUT, "device: a shared-memory staging copy did not complete in time");
     if (st & ST_ZERO_PROB) fail(TSIM_ERR_ZERO_PROB, "device: a sampled prefix had P_prev <= 0");
     if (st & ST_NOT_REAL) fail(TSIM_ERR_INTERNAL, "device: a marginal was not real");
     fail(TSIM_ERR_OVERFLOW_BOUND, "device: exact arithmetic overflow");

@@ -20,11 +20,13 @@ struct SampleArgs {
 // Byte offsets of the sections of the packed device tables (256-byte aligned)
 struct DeviceLayout {
   size_t o_ch = 0, o_thr = 0, o_sig = 0, o_out = 0, o_om = 0, o_cn = 0, o_tab = 0, o_par = 0,
-         o_cls = 0, o_fidx = 0, o_finc = 0, o_fco = 0, o_sb = 0, o_row = 0, o_dmo = 0, o_dmi = 0, o_omo = 0,
+         o_cls = 0, o_fidx = 0, o_finc = 0, o_fco = 0, o_seg = 0, o_sb = 0, o_row = 0, o_dmo = 0, o_dmi = 0, o_omo = 0,
          o_omi = 0, total = 0;
   int W = 1;
   uint32_t sl_par_max = 0;  // largest parity list of a bit-sliced table
-  int sl_words = 0;         // shared 32-bit words per warp the kernel needs (0: no sliced table)
+  uint32_t sl_rows_max = 0; // most operation rows of a staged batch
+  int sl_par = 0;           // shared 32-bit words per warp for parity words (0: no sliced table)
+  int sl_rb = 0;            // shared 32-bit words of one row staging buffer (0: none)
   // statistics of the packed tables
   uint64_t classes = 0;     // stabilizer terms after merging terms with equal factor lists
   uint64_t class_factors = 0;
@@ -33,6 +35,7 @@ struct DeviceLayout {
   // per table: layout (0 scalar, 1 basis, 2 bit-sliced), and for sliced
   // tables the batches of 32 terms, padded operation rows and real operations
   std::vector<uint64_t> table_mode, table_batches, table_rows, table_ops;
+  std::vector<uint64_t> table_work32;  // sliced: integer lane-operations of one warp (32 shots)
 };
 
 // Tables with at least this many terms (after merging equal factor lists)
@@ -49,8 +52,21 @@ struct DeviceTables {
   std::string message;
 };
 
-// Pack the device tables; sliced_min < 0 disables the bit-sliced layout.
-void prepare_device_tables(Program& p, int64_t sliced_min = kDefaultSlicedMin);
+// Sliced batches with at most this many operation rows are staged through
+// shared memory by bulk copies.  Off by default: the staging buffers cost
+// resident warps, and on the colour-code T-check the rows read through L1
+// were faster (1.08e7 against 8.8e6 shots/s).
+constexpr int kDefaultStageRows = 0;
+
+// Sliced tables are split into segments of consecutive terms whose parity
+// words (two reserved) fit this many 32-bit words of shared memory per warp.
+constexpr int kDefaultSegmentParities = 2048;
+
+// Pack the device tables; sliced_min < 0 disables the bit-sliced layout;
+// stage_rows: largest staged batch (0: read rows from global memory, < 0:
+// the default); seg_par: parity words per segment (<= 0: the default).
+void prepare_device_tables(Program& p, int64_t sliced_min = kDefaultSlicedMin, int stage_rows = -1,
+                           int seg_par = 0);
 void device_sample(const Program& p, const SampleArgs& a, void* stream);
 void device_sample_batch(const Program* const* progs, int n, const SampleArgs* args, void* stream);
 

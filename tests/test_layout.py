@@ -1,0 +1,60 @@
+"""Device table layouts, checked on the host (packing needs no GPU): which
+tables take the bit-sliced layout, how they split into segments and batches,
+and that the layout can be changed and queried through the C ABI."""
+import pytest
+
+import paper_2604_01059_gb300 as T
+from paper_2604_01059_gb300 import workloads as Wk
+from tests.test_compile_semantics import WORKED_EXAMPLE
+
+
+@pytest.fixture(scope="module")
+def color_code():
+    return T.Program(Wk.config3_circuit())
+
+
+def _layouts(prog):
+    return [prog.device_table_layout(t) for t in range(prog.info["num_tables"])]
+
+
+def test_color_code_default_layout(color_code):
+    # marginals of 64 terms or more are sliced; each segment's batches hold
+    # 32 terms but its last one, so a table has at least ceil(n / 32) batches
+    for (mode, nb, rows, ops, work), n in zip(_layouts(color_code), color_code.table_terms()):
+        assert mode == (T.TABLE_SLICED if n >= 64 else T.TABLE_SCALAR)
+        if mode == T.TABLE_SLICED:
+            assert (n + 31) // 32 <= nb <= (n + 31) // 32 + n // 32
+            assert rows % 4 == 0 or rows >= ops / 32
+            assert rows * 32 >= ops and work > rows * 32 * 3
+        else:
+            assert nb == rows == ops == work == 0
+
+
+@pytest.mark.parametrize("seg", [256, 1024, 2048, 16384])
+def test_segment_sizes(color_code, seg):
+    # smaller segments only add batches (a partial batch per segment) and
+    # never change which tables are sliced or how many operations they hold
+    color_code.set_table_layout(64, 0, seg)
+    lay = _layouts(color_code)
+    color_code.set_table_layout(64, 0, 16384)
+    whole = _layouts(color_code)
+    for a, b in zip(lay, whole):
+        assert a[0] == b[0] and a[3] == b[3]
+        assert a[1] >= b[1]
+
+
+def test_layout_switches(color_code):
+    color_code.set_table_layout(-1)
+    assert T.TABLE_SLICED not in [m for m, *_ in _layouts(color_code)]
+    color_code.set_table_layout(1)
+    assert all(m == T.TABLE_SLICED for m, *_ in _layouts(color_code))
+    color_code.set_table_layout(64)
+    with pytest.raises(T.TsimError):
+        color_code.device_table_layout(color_code.info["num_tables"])
+
+
+def test_worked_example_forced_sliced():
+    prog = T.Program(WORKED_EXAMPLE)
+    prog.set_table_layout(1, 128, 16)
+    for mode, nb, rows, ops, work in _layouts(prog):
+        assert mode == T.TABLE_SLICED and nb >= 1
