@@ -432,6 +432,8 @@ def run_gpu(args):
                            "programs": n, "shots_per_step": shots_step,
                            "terms_per_shot": [term_evals_per_shot(p) for p in progs][:8],
                            "plain_terms_per_shot": [term_evals_per_shot(p) for p in plain_progs][:8],
+                           "terms_all_programs": {"learned": sum(term_evals_per_shot(p) for p in progs),
+                                                  "heuristic": sum(term_evals_per_shot(p) for p in plain_progs)},
                            "channels": [p.info["num_channels"] for p in progs][:8],
                            "form": "learned cut order + batched persistent launch (CUDA graph)",
                            "cut": cut, "batch": binfo},

@@ -892,8 +892,17 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, uint64_t se
 // dynamic shared memory: sl_warp_words(...) per warp for programs with sliced tables
 extern __shared__ __align__(128) uint32_t g_warp_smem[];
 
+// Register bounds (resident blocks of up to 128 threads per SM) for X of up
+// to 4 words: kernels for programs with sliced tables at 80 registers (6
+// blocks: occupancy hides the latency of the operation rows read through
+// L1), the others at 48 (10 blocks for the Philox-bound noise loop).  Wider X
+// needs 2W registers of its own, so the bounds relax with W.
+constexpr int min_blocks(int W, bool sl) {
+  return sl ? (W <= 4 ? 6 : W <= 8 ? 4 : 2) : (W <= 4 ? 10 : W <= 8 ? 6 : 2);
+}
+
 template <int W, bool SL>
-__global__ void __launch_bounds__(kThreads) k_sample(DevView V, uint64_t seed, uint64_t shot0,
+__global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_sample(DevView V, uint64_t seed, uint64_t shot0,
                                                      uint64_t nshots, uint64_t* __restrict__ meas,
                                                      uint64_t* __restrict__ det,
                                                      uint64_t* __restrict__ obs,
@@ -922,7 +931,7 @@ struct BatchProg {
 };
 
 template <int W, bool SL>
-__global__ void __launch_bounds__(kThreads) k_batch(const BatchProg* __restrict__ progs, int n,
+__global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_batch(const BatchProg* __restrict__ progs, int n,
                                                     const uint64_t* __restrict__ item_start,
                                                     uint64_t total_items, uint32_t sb,
                                                     unsigned long long* counter, int sl_par, int sl_rb) {
