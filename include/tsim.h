@@ -178,18 +178,23 @@ tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t shots, uint64
 /* Reusable batched launch (Appendix "Additional benchmarks": batched sampling;
  * here heterogeneous programs share one persistent kernel).  tsim_batch_create
  * uploads every program, lays out the (program, shot-block) work items,
- * optionally autotunes the shot-block size (1, 4 or 16 times the threads of
- * a block: 128 threads, or 32 to 128 when a program has bit-sliced tables;
- * 4 times without autotuning) and the resident blocks per SM (4, 8, 16) by
- * timing each candidate on the real
- * batch, and captures "reset the work counter + persistent launch" in a CUDA
- * graph.  tsim_batch_launch replays that graph on cuda_stream (asynchronous);
- * the output pointers given at creation are written on every launch.  The
- * batch owns a small device allocation (descriptors, work counter) freed by
- * tsim_batch_free, which must not be called while a launch is in flight.
+ * (autotune = 1) autotunes the shots per work item (32, 128 or 512; 128
+ * without autotuning; each item is taken by one warp) and the resident
+ * blocks per SM (4, 8, 16) by timing each candidate on the real batch,
+ * then times the other launch form (each program's own sampling kernel, one
+ * after another) and keeps the faster form, and captures the launch
+ * ("reset the work counter + persistent launch", or the programs' launches)
+ * in a CUDA graph.  Both forms write the same records.  tsim_batch_launch
+ * replays that graph on cuda_stream (asynchronous); the output pointers
+ * given at creation are written on every launch.  The batch owns a small
+ * device allocation (descriptors, work counter) freed by tsim_batch_free,
+ * which must not be called while a launch is in flight.
  * tsim_batch_info: out[0] shots per work item, out[1] blocks per SM,
  * out[2] work items, out[3] 1 if a graph is captured, out[4] words of X,
- * out[5] autotuned launch time in microseconds (0 without autotuning). */
+ * out[5] autotuned launch time in microseconds (0 without autotuning),
+ * out[6] launch form (0 persistent, 1 one launch per program).
+ * autotune = 0 keeps the persistent form with its defaults; autotune = 2
+ * takes the one-launch-per-program form without timing anything. */
 typedef struct tsim_batch tsim_batch;
 tsim_status tsim_batch_create(const tsim_program* const* progs, int n, const uint64_t* shots,
                               const uint64_t* seeds, const uint64_t* shot_offsets,
@@ -197,7 +202,7 @@ tsim_status tsim_batch_create(const tsim_program* const* progs, int n, const uin
                               uint64_t* const* d_obs, uint8_t* const* d_accept, int autotune,
                               tsim_batch** out);
 tsim_status tsim_batch_launch(tsim_batch* batch, void* cuda_stream);
-tsim_status tsim_batch_info(const tsim_batch* batch, int64_t out[6]);
+tsim_status tsim_batch_info(const tsim_batch* batch, int64_t out[7]);
 void tsim_batch_free(tsim_batch* batch);
 
 /* Wait for cuda_stream and report any device-side error status. */
@@ -259,8 +264,8 @@ tsim_status tsim_program_device_table_stats(const tsim_program* prog, int t, uin
  * L1, < 0 takes the default (0).  A SLICED table is split into segments of
  * consecutive terms whose distinct parities fit segment_parities 32-bit words
  * of shared memory per warp (each segment forms its own parity words; fewer
- * words let more warps reside per SM); <= 0 takes the default (2048).  The
- * defaults at compile / load time are 64, 0 and 2048.
+ * words let more warps reside per SM); <= 0 takes the default (1536).  The
+ * defaults at compile / load time are 64, 0 and 1536.
  * It frees the program's uploaded
  * device copy, so it must not be called while a launch of the program is in
  * flight or while a batch created from it (tsim_batch_create) exists.

@@ -209,10 +209,12 @@ def _batch_arrays(hs, shots, seeds, shot_offsets, meas, det, obs, accept):
 
 def tsim_batch_create(hs, shots, seeds, shot_offsets=None, meas=None, det=None, obs=None, accept=None,
                       autotune=True):
-    """Reusable batched launch (persistent kernel captured in a CUDA graph)."""
+    """Reusable batched launch captured in a CUDA graph; autotune: 0 persistent
+    kernel with defaults, 1 (True) autotuned shot blocks, residency and launch
+    form, 2 one launch per program."""
     out = ctypes.c_void_p()
     _check(load_library().tsim_batch_create(*_batch_arrays(hs, shots, seeds, shot_offsets, meas, det, obs,
-                                                           accept), 1 if autotune else 0, ctypes.byref(out)))
+                                                           accept), int(autotune), ctypes.byref(out)))
     return out.value
 
 
@@ -222,9 +224,9 @@ def tsim_batch_launch(b, stream=None):
 
 
 def tsim_batch_info(b):
-    out = (ctypes.c_int64 * 6)()
+    out = (ctypes.c_int64 * 7)()
     _check(load_library().tsim_batch_info(b, out))
-    keys = ["shots_per_item", "blocks_per_sm", "work_items", "graph", "x_words", "tuned_us"]
+    keys = ["shots_per_item", "blocks_per_sm", "work_items", "graph", "x_words", "tuned_us", "form"]
     return dict(zip(keys, list(out)))
 
 

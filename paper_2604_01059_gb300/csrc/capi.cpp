@@ -274,7 +274,7 @@ tsim_status tsim_batch_launch(tsim_batch* batch, void* cuda_stream) {
   });
 }
 
-tsim_status tsim_batch_info(const tsim_batch* batch, int64_t out[6]) {
+tsim_status tsim_batch_info(const tsim_batch* batch, int64_t out[7]) {
   return guard([&] {
     if (!batch || !batch->b || !out) tsim::fail(TSIM_ERR_ARG, "NULL argument");
     tsim::batch_info(batch->b, out);

@@ -80,8 +80,9 @@ enum : int {
 };
 constexpr uint32_t kSlOnes = 1;        // parity index whose word is all ones
 constexpr int kSlMaxPar = 16384;       // parity words of one segment (4q fits 16 bits)
-// One batch of 32 terms: rows of operation code c are cnt[c] x 32 parity
-// indices (lane-interleaved, padded with no-op indices), starting at row_off.
+// One batch of 32 terms: rows of operation code c are cnt[c] (a multiple of
+// 4) x 32 parity offsets, padded with no-op offsets and stored in groups of 4
+// rows as [group][lane][4], starting at row_off.
 // All terms of a batch share the magnitude sqrt2^d; j0m[b] holds bit b of
 // each lane's constant phase; valid marks lanes that carry a term.
 struct DSBatch { uint32_t row_off; uint16_t cnt[8]; int32_t d; uint32_t j0m[3]; uint32_t valid; };
@@ -409,31 +410,45 @@ struct Transposer {
   }
 };
 
-// Operation rows read from global memory (lane-interleaved, through L1) or
-// from a shared staging buffer.  A row holds the byte offset of a parity word
-// (4q), or two of them (4qa | 4qb << 16) for pi-pairs.
+// Operation rows read from global memory (through L1) or from a shared
+// staging buffer.  A row holds the byte offset of a parity word (4q), or two
+// of them (4qa | 4qb << 16) for pi-pairs.  Rows come in groups of 4: group g
+// of a code is 32 lanes x 4 consecutive rows, so one 16-byte load per lane
+// fetches 4 rows and a warp's load is 512 contiguous bytes.
 struct RowsG {
-  const uint32_t* p;
-  __device__ __forceinline__ uint32_t get(int i) const { return __ldg(p + 32 * i); }
-  __device__ __forceinline__ void adv(int k) { p += 32 * k; }
+  const uint4* p;  // this lane's current group
+  __device__ __forceinline__ uint4 get4(int g) const { return __ldg(p + 32 * g); }
+  __device__ __forceinline__ void adv4(int k) { p += 32 * k; }
 };
 struct RowsS {
-  uint32_t a;
-  __device__ __forceinline__ uint32_t get(int i) const { return lds(a + 128u * (uint32_t)i); }
-  __device__ __forceinline__ void adv(int k) { a += 128u * (uint32_t)k; }
+  uint32_t a;  // shared address of this lane's current group
+  __device__ __forceinline__ uint4 get4(int g) const {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(a + 512u * (uint32_t)g));
+    return v;
+  }
+  __device__ __forceinline__ void adv4(int k) { a += 512u * (uint32_t)k; }
 };
 
-// The n rows of one operation code, in chunks whose row loads and parity
-// loads are all issued before the updates; f(way, a, b) spreads consecutive
-// rows over 4 independent accumulators (way = row & 3) so that the update
-// chains overlap.
+// The n rows (a multiple of 4) of one operation code, in chunks whose row
+// loads and parity loads are all issued before the updates; f(way, a, b)
+// spreads consecutive rows over 4 independent accumulators (way = row & 3)
+// so that the update chains overlap.
 template <bool PAIR, class Rows, class F>
 __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
   int k = 0;
-  for (; k + 16 <= n; k += 16, R.adv(16)) {
+  for (; k + 16 <= n; k += 16, R.adv4(4)) {
     uint32_t r[16], a[16], b[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) r[i] = R.get(i);
+    for (int g = 0; g < 4; ++g) {
+      const uint4 v = R.get4(g);
+      r[4 * g] = v.x;
+      r[4 * g + 1] = v.y;
+      r[4 * g + 2] = v.z;
+      r[4 * g + 3] = v.w;
+    }
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       a[i] = lds(par + (PAIR ? (r[i] & 0xFFFFu) : r[i]));
@@ -442,10 +457,10 @@ __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) f(i & 3, a[i], b[i]);
   }
-  for (; k + 4 <= n; k += 4, R.adv(4)) {
-    uint32_t r[4], a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) r[i] = R.get(i);
+  for (; k < n; k += 4, R.adv4(1)) {
+    const uint4 v = R.get4(0);
+    const uint32_t r[4] = {v.x, v.y, v.z, v.w};
+    uint32_t a[4], b[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       a[i] = lds(par + (PAIR ? (r[i] & 0xFFFFu) : r[i]));
@@ -453,10 +468,6 @@ __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) f(i, a[i], b[i]);
-  }
-  for (; k < n; ++k, R.adv(1)) {
-    const uint32_t r = R.get(0);
-    f(0, lds(par + (PAIR ? (r & 0xFFFFu) : r)), PAIR ? lds(par + (r >> 16)) : 0u);
   }
 }
 
@@ -617,11 +628,12 @@ __device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64
           state |= 4u;
         } else {
           state ^= 1u << buf;
-          sl_batch(B, RowsS{(buf ? S.rb1 : S.rb0) + 4u * (uint32_t)lane}, S.par, lane, J0, J1, J2, Z);
+          sl_batch(B, RowsS{(buf ? S.rb1 : S.rb0) + 16u * (uint32_t)lane}, S.par, lane, J0, J1, J2, Z);
         }
       }
-      if (!staged || !ok) sl_batch(B, RowsG{V.rows + B.row_off + lane}, S.par, lane, J0, J1, J2, Z);
-      __syncwarp();
+      if (!staged || !ok)
+        sl_batch(B, RowsG{reinterpret_cast<const uint4*>(V.rows + B.row_off) + lane}, S.par, lane, J0, J1, J2, Z);
+      if (staged) __syncwarp();  // the buffer just read is refilled next batch
       // lane s now needs, for each of the 32 terms, its phase and flag at shot s
       const uint32_t T0 = transpose32(J0), T1 = transpose32(J1);
       const uint32_t T2 = transpose32(J2), TZ = transpose32(Z);
@@ -900,6 +912,9 @@ extern __shared__ __align__(128) uint32_t g_warp_smem[];
 constexpr int min_blocks(int W, bool sl) {
   return sl ? (W <= 4 ? 6 : W <= 8 ? 4 : 2) : (W <= 4 ? 10 : W <= 8 ? 6 : 2);
 }
+// the batched kernel keeps its work-item state live across the whole shot
+// loop: one block less for programs with sliced tables (96 registers)
+constexpr int min_blocks_batch(int W, bool sl) { return sl && W <= 4 ? 5 : min_blocks(W, sl); }
 
 template <int W, bool SL>
 __global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_sample(DevView V, uint64_t seed, uint64_t shot0,
@@ -918,8 +933,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_sample(DevView 
 
 // ------------------------------------------------------- batched launch
 // One persistent launch over many programs: work item i is a block of `sb`
-// shots of one program; blocks take items from an atomic counter until all
-// are done (no waiting on other blocks).  Program p owns items
+// shots (a multiple of 32) of one program; warps take items from an atomic
+// counter until all are done (no waiting on other warps or blocks).  Program p owns items
 // [item_start[p], item_start[p+1]).
 struct BatchProg {
   DevView v;
@@ -931,21 +946,21 @@ struct BatchProg {
 };
 
 template <int W, bool SL>
-__global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_batch(const BatchProg* __restrict__ progs, int n,
+__global__ void __launch_bounds__(kThreads, min_blocks_batch(W, SL)) k_batch(const BatchProg* __restrict__ progs, int n,
                                                     const uint64_t* __restrict__ item_start,
                                                     uint64_t total_items, uint32_t sb,
                                                     unsigned long long* counter, int sl_par, int sl_rb) {
-  __shared__ unsigned long long item;
   SlSmem sm{};
   if constexpr (SL) {
     sm = sl_smem(g_warp_smem + (threadIdx.x >> 5) * sl_warp_words(W, sl_par, sl_rb), W, sl_par, sl_rb);
     sl_init(sm);
   }
+  // every warp takes its own work items (no block-wide synchronisation)
+  const int lane = threadIdx.x & 31;
   for (;;) {
-    if (threadIdx.x == 0) item = atomicAdd(counter, 1ull);
-    __syncthreads();
-    const uint64_t it = item;
-    __syncthreads();
+    unsigned long long it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1ull);
+    it = __shfl_sync(0xFFFFFFFFu, it, 0);
     if (it >= total_items) return;
     int lo = 0, hi = n - 1;  // last program with item_start <= it
     while (lo < hi) {
@@ -956,8 +971,8 @@ __global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_batch(const Bat
     const BatchProg& P = progs[lo];
     const uint64_t first = (it - item_start[lo]) * sb;
     const uint64_t last = min(first + sb, P.shots);
-    for (uint64_t s0 = first; s0 < last; s0 += blockDim.x) {
-      const uint64_t s = s0 + threadIdx.x;
+    for (uint64_t s0 = first; s0 < last; s0 += 32) {
+      const uint64_t s = s0 + lane;
       sample_one<W, SL>(P.v, s, s < last, P.seed, P.shot_offset, P.meas, P.det, P.obs, P.accept, sm);
     }
   }
@@ -1444,16 +1459,19 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
             n = (n + 3) & ~(size_t)3;  // whole groups of 4 rows: no single-row tail loop on the device
             if (n > 0xFFFF) throw PackError{TSIM_ERR_ARG, "too many operations of one kind in a term"};
             B.cnt[c] = (uint16_t)n;
-            for (size_t k = 0; k < n; ++k)
-              for (size_t l = 0; l < 32; ++l) {
-                const size_t ti = b0 + l;
-                uint32_t r = c == SL_ZEROC ? 4 * kSlOnes : 0u;  // padding leaves J and Z unchanged
-                if (ti < b1 && k < lt[ti].ops[c].size()) {
-                  r = (uint32_t)lt[ti].ops[c][k];
-                  ++real_ops;
+            // groups of 4 rows: [group][lane][4], so a lane's 4 rows are 16
+            // contiguous bytes and a group is 512 contiguous bytes
+            for (size_t g = 0; g < n / 4; ++g)
+              for (size_t l = 0; l < 32; ++l)
+                for (size_t k = 4 * g; k < 4 * g + 4; ++k) {
+                  const size_t ti = b0 + l;
+                  uint32_t r = c == SL_ZEROC ? 4 * kSlOnes : 0u;  // padding leaves J and Z unchanged
+                  if (ti < b1 && k < lt[ti].ops[c].size()) {
+                    r = (uint32_t)lt[ti].ops[c][k];
+                    ++real_ops;
+                  }
+                  rows.push_back(r);
                 }
-                rows.push_back(r);
-              }
             padded_rows += n;
             nrows += (uint32_t)n;
             w32 += (uint64_t)n * 32 * (uint64_t)kRowOps[c];
@@ -1758,6 +1776,7 @@ struct BatchPlan {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   float tuned_ms = 0;
+  int form = 0;  // 0: one persistent launch over all work items; 1: each program's own launch
 };
 
 namespace {
@@ -1788,6 +1807,14 @@ cudaError_t launch_batch_w(const BatchPlan& b, cudaStream_t s, unsigned grid) {
 }
 
 cudaError_t launch_batch(const BatchPlan& b, cudaStream_t s) {
+  if (b.form == 1) {  // the programs' own sampling launches, one after another
+    for (const BatchProg& p : b.h_progs) {
+      if (!p.shots) continue;
+      cudaError_t e = launch(p.v, s, p.seed, p.shot_offset, p.shots, p.meas, p.det, p.obs, p.accept);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   cudaError_t e = cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   if (!b.total_items) return cudaSuccess;
@@ -1840,9 +1867,10 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
   TSIM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   struct SD { cudaStream_t s; ~SD() { cudaStreamDestroy(s); } } sd{s};
   if (n) TSIM_CUDA(cudaMemcpyAsync(b->d_progs, b->h_progs.data(), (size_t)n * sizeof(BatchProg), cudaMemcpyHostToDevice, s));
-  b->sb = 4 * shape_of(sl_warp_words(b->wmax, b->sl_par_max, b->sl_rb)).threads;
+  b->sb = 128;
   plan_items(*b, s);
-  if (autotune && b->total_items) {
+  if (autotune == 2) b->form = 1;
+  if (autotune == 1 && b->total_items) {
     // shot-block size x resident blocks per SM: time every candidate twice on
     // the real batch (records are overwritten with identical values)
     cudaEvent_t e0, e1;
@@ -1851,10 +1879,8 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
     float best = 1e30f;
     uint32_t best_sb = b->sb;
     int best_bps = b->blocks_per_sm;
-    // shot blocks of 1, 4 and 16 times the block's threads (128 threads, or
-    // 32 to 128 for programs with sliced tables)
-    const unsigned thr = shape_of(sl_warp_words(b->wmax, b->sl_par_max, b->sl_rb)).threads;
-    for (uint32_t sb : {thr, 4 * thr, 16 * thr}) {
+    // work items of 32, 128 or 512 shots (one warp each)
+    for (uint32_t sb : {32u, 128u, 512u}) {
       b->sb = sb;
       plan_items(*b, s);
       for (int bps : {4, 8, 16}) {
@@ -1871,6 +1897,23 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
         }
         if (t < best) { best = t; best_sb = sb; best_bps = bps; }
       }
+    }
+    // the other launch form: every program's own kernel (few large programs
+    // can run faster that way than through the persistent loop)
+    {
+      b->form = 1;
+      float t = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        TSIM_CUDA(cudaEventRecord(e0, s));
+        TSIM_CUDA(launch_batch(*b, s));
+        TSIM_CUDA(cudaEventRecord(e1, s));
+        TSIM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        TSIM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        t = std::min(t, ms);
+      }
+      b->form = t < best ? 1 : 0;
+      best = std::min(best, t);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1909,13 +1952,14 @@ void batch_free(BatchPlan* b) {
   delete b;
 }
 
-void batch_info(const BatchPlan* b, int64_t out[6]) {
+void batch_info(const BatchPlan* b, int64_t out[7]) {
   out[0] = b->sb;
   out[1] = b->blocks_per_sm;
   out[2] = (int64_t)b->total_items;
   out[3] = b->exec ? 1 : 0;
   out[4] = b->wmax;
   out[5] = (int64_t)(b->tuned_ms * 1000.0f);
+  out[6] = b->form;
 }
 
 void device_sample_batch(const Program* const* progs, int n, const SampleArgs* args, void* stream) {

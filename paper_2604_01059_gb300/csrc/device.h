@@ -60,7 +60,7 @@ constexpr int kDefaultStageRows = 0;
 
 // Sliced tables are split into segments of consecutive terms whose parity
 // words (two reserved) fit this many 32-bit words of shared memory per warp.
-constexpr int kDefaultSegmentParities = 2048;
+constexpr int kDefaultSegmentParities = 1536;
 
 // Pack the device tables; sliced_min < 0 disables the bit-sliced layout;
 // stage_rows: largest staged batch (0: read rows from global memory, < 0:
@@ -74,7 +74,7 @@ struct BatchPlan;
 BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* args, int autotune);
 void batch_launch(BatchPlan* b, void* stream);
 void batch_free(BatchPlan* b);
-void batch_info(const BatchPlan* b, int64_t out[6]);
+void batch_info(const BatchPlan* b, int64_t out[7]);
 void device_sync(void* stream);
 void device_release(DeviceProgram* d);
 

@@ -45,7 +45,7 @@ def _np(bufs):
     return [None if t is None else t.cpu().numpy() for t in bufs]
 
 
-@pytest.mark.parametrize("autotune", [False, True])
+@pytest.mark.parametrize("autotune", [0, 1, 2])  # persistent, autotuned, one launch per program
 def test_batch_matches_single_launches(tmp_path, autotune):
     progs = _programs()
     rng = np.random.default_rng(5)
@@ -66,6 +66,7 @@ def test_batch_matches_single_launches(tmp_path, autotune):
     try:
         info = T.tsim_batch_info(batch)
         assert info["graph"] == 1 and info["work_items"] >= len(progs)
+        assert info["form"] == {0: 0, 2: 1}.get(autotune, info["form"]) and info["form"] in (0, 1)
         for rep in range(2):  # graph replay: the same records every time
             for b in got:
                 for t in b:
@@ -109,3 +110,34 @@ def test_simple_batch_entry_point():
         for a, c in zip(w, _np(g)):
             if a is not None:
                 np.testing.assert_array_equal(a, c)
+
+
+def test_batch_of_large_sliced_programs():
+    # few large programs (colour-code T-check twice, different seeds): the
+    # autotuner may keep either launch form; records must equal plain launches
+    progs = [T.Program(Wk.config3_circuit()) for _ in range(2)]
+    shots, seeds, offs = [20000, 12345], [3, 4], [0, 1 << 32]
+    want, got = [], []
+    for p, n, sd, of in zip(progs, shots, seeds, offs):
+        b = _bufs(p, n)
+        T.tsim_sample(p.h, n, sd, of, *b)
+        want.append(b)
+        got.append(_bufs(p, n))
+    T.tsim_sync()
+    cols = list(zip(*got))
+    for autotune in (1, 2, 0):
+        batch = T.tsim_batch_create([p.h for p in progs], shots, seeds, offs, *[list(c) for c in cols],
+                                    autotune=autotune)
+        try:
+            for b in got:
+                for t in b:
+                    if t is not None:
+                        t.zero_()
+            T.tsim_batch_launch(batch)
+            T.tsim_sync()
+            for w, g in zip(want, got):
+                for a, c in zip(_np(w), _np(g)):
+                    if a is not None:
+                        np.testing.assert_array_equal(a, c)
+        finally:
+            T.tsim_batch_free(batch)
