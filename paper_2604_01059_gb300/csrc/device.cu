@@ -95,6 +95,7 @@ struct DevView {
   int n_ch, n_out, n_chains, n_tab;
   int nmeas, ndet, nobs, mode;
   const DChan* ch;
+  const uint4* thr0;      // outcome-0 threshold per channel, 4 per block, padded with 2^32-1
   const uint32_t* thr;
   const uint64_t* sig;
   const DOut* out;
@@ -775,16 +776,21 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, uint64_t se
   uint64_t X[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) X[w] = 0;
+  // four channels per Philox block: their outcome-0 thresholds in one
+  // 16-byte load and one test; the rare block where some channel fires walks
+  // its channels
   for (int c = 0; c < V.n_ch; c += 4) {
     uint32_t u[4];
     philox4x32_10(c0, c1, 0u, (uint32_t)(c >> 2), rk, u);
+    const uint4 t0 = __ldg(V.thr0 + (c >> 2));
+    if (!((u[0] >= t0.x) | (u[1] >= t0.y) | (u[2] >= t0.z) | (u[3] >= t0.w))) continue;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
       const int ci = c + l;
       if (ci >= V.n_ch) break;
       const DChan ch = V.ch[ci];
       const uint32_t U = u[l];
-      if (U < ch.thr0) continue;  // outcome 0: nothing fires (the common case)
+      if (U < ch.thr0) continue;  // outcome 0: nothing fires
       const uint32_t* thr = V.thr + ch.thr_off;
       uint32_t o = 1;
       while (o + 1 < ch.n_out && U >= __ldg(thr + o)) ++o;
@@ -1223,6 +1229,11 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
         if (c.sig[0][w]) throw PackError{TSIM_ERR_INTERNAL, "channel outcome 0 must not flip anything"};
     }
   }
+  L.o_t0 = s.section();
+  for (size_t i = 0; i < (p.channels.size() + 3) / 4 * 4; ++i) {
+    const uint32_t t = i < p.channels.size() && !p.channels[i].thr.empty() ? p.channels[i].thr[0] : 0xFFFFFFFFu;
+    s.put(&t, 4);
+  }
   L.o_thr = s.section();
   for (const ProgChannel& c : p.channels)
     for (uint32_t t : c.thr) s.put(&t, 4);
@@ -1620,6 +1631,7 @@ DevView make_view(const unsigned char* base, const DeviceLayout& L, const Progra
   v.nobs = p.nobs;
   v.mode = p.mode;
   v.ch = (const DChan*)(base + L.o_ch);
+  v.thr0 = (const uint4*)(base + L.o_t0);
   v.thr = (const uint32_t*)(base + L.o_thr);
   v.sig = (const uint64_t*)(base + L.o_sig);
   v.out = (const DOut*)(base + L.o_out);
