@@ -468,7 +468,9 @@ def kernel_int_ops(prog):
     on the packed device tables it actually evaluates:
       noise:   ceil(C/4) Philox4x32-10 calls x 10 rounds x (2 wide multiplies
                + 2 three-input XORs) = 40 per call, plus one compare per channel;
-      outputs: 3 per single-bit deterministic output, 60 per Bernoulli decision;
+      outputs: 3 per deterministic output outside runs, 6 per run of
+               single-bit outputs (+4 per further 64 of its bits), 60 per
+               Bernoulli decision;
       tables:  per distinct parity 2W+2 (AND, XOR, popcount, insert), per merged
                term 12 (+5 per factor: two bit extracts, index, lookup, add);
                bit-sliced tables: the lane-operations of one warp for its 32
@@ -477,7 +479,9 @@ def kernel_int_ops(prog):
     C = i["num_channels"]
     W = next(p for p in (1, 2, 4, 8, 16, 32) if i["x_words"] <= p)
     ops = 40 * ((C + 3) // 4) + C
-    ops += 3 * (i["num_outputs"] - i["num_random"]) + 60 * i["num_random"]
+    entries, runs, run_outputs = prog.device_output_stats()
+    ops += 3 * (i["num_outputs"] - i["num_random"] - run_outputs) + 60 * i["num_random"]
+    ops += 6 * runs + 4 * (run_outputs // 64)  # a run: word extracts, shift, merge
     for t in range(i["num_tables"]):
         layout = prog.device_table_layout(t)
         if layout[0] == 2:  # bit-sliced: the library counts one warp's lane-operations for 32 shots

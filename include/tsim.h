@@ -279,6 +279,13 @@ tsim_status tsim_program_set_table_layout(tsim_program* prog, int64_t sliced_min
                                           int32_t segment_parities);
 tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[5]);
 
+/* Output entries of the packed program: out[0] = entries the kernel walks
+ * per shot, out[1] = runs (in detector mode, consecutive single-bit
+ * deterministic outputs without a constant that read consecutive bits of X,
+ * Eq. detector_sampling, copied into the record by word shifts), out[2] =
+ * outputs covered by runs. */
+tsim_status tsim_program_device_output_stats(const tsim_program* prog, uint64_t out[3]);
+
 /* Self-check of the compiler's rewrite rules against brute-force summation on
  * random small parameterised graphs (no GPU).  Returns TSIM_OK when all pass. */
 tsim_status tsim_selftest_rules(uint64_t seed, int iterations);

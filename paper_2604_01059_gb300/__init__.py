@@ -19,7 +19,8 @@ __all__ = [
     "tsim_batch_launch", "tsim_batch_info", "tsim_batch_free", "tsim_sync", "tsim_eval_table",
     "tsim_raw_to_x", "tsim_program_save", "tsim_program_load", "tsim_program_free",
     "tsim_last_error", "tsim_selftest_rules", "tsim_measure_int_peak", "tsim_program_device_table_stats",
-    "tsim_program_set_table_layout", "tsim_program_device_table_layout", "load_library",
+    "tsim_program_set_table_layout", "tsim_program_device_table_layout", "tsim_program_device_output_stats",
+    "load_library",
     "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T",
 ]
 
@@ -100,6 +101,7 @@ def load_library(path: str | None = None):
     L.tsim_program_device_table_stats.argtypes = [vp, i32, ctypes.POINTER(u64)]
     L.tsim_program_set_table_layout.argtypes = [vp, i64, i32, i32]
     L.tsim_program_device_table_layout.argtypes = [vp, i32, ctypes.POINTER(u64)]
+    L.tsim_program_device_output_stats.argtypes = [vp, ctypes.POINTER(u64)]
     L.tsim_cut_num_params.argtypes = []
     L.tsim_cut_init_params.argtypes = [u64, vp]
     L.tsim_cut_dataset.argtypes = [u64, i32, i32, i32, u64, i32, ctypes.c_char_p]
@@ -114,7 +116,8 @@ def load_library(path: str | None = None):
               "tsim_batch_launch", "tsim_batch_info", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
               "tsim_program_save", "tsim_program_load", "tsim_selftest_rules", "tsim_measure_int_peak",
               "tsim_program_device_table_stats", "tsim_program_set_table_layout",
-              "tsim_program_device_table_layout", "tsim_cut_num_params", "tsim_cut_init_params",
+              "tsim_program_device_table_layout", "tsim_program_device_output_stats", "tsim_cut_num_params",
+              "tsim_cut_init_params",
               "tsim_cut_dataset", "tsim_cut_forward", "tsim_cut_loss_grad", "tsim_cut_adam_step", "tsim_cut_train",
               "tsim_cut_model_set", "tsim_cut_policy_stats"):
         getattr(L, n).restype = ctypes.c_int
@@ -305,6 +308,13 @@ def tsim_program_device_table_layout(h, t):
     return tuple(out)
 
 
+def tsim_program_device_output_stats(h):
+    """(output entries, runs, outputs covered by runs) of the packed program."""
+    out = (ctypes.c_uint64 * 3)()
+    _check(load_library().tsim_program_device_output_stats(h, out))
+    return tuple(out)
+
+
 def tsim_selftest_rules(seed=0, iterations=200):
     _check(load_library().tsim_selftest_rules(seed, iterations))
 
@@ -461,6 +471,9 @@ class Program:
 
     def device_table_layout(self, t):
         return tsim_program_device_table_layout(self.h, t)
+
+    def device_output_stats(self):
+        return tsim_program_device_output_stats(self.h)
 
     def table_terms(self):
         return [tsim_program_table_terms(self.h, t) for t in range(self.info["num_tables"])]

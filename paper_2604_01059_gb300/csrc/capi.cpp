@@ -158,6 +158,18 @@ tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, ui
   });
 }
 
+tsim_status tsim_program_device_output_stats(const tsim_program* prog, uint64_t out[3]) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!out) tsim::fail(TSIM_ERR_ARG, "NULL output array");
+    if (!p.devtab || p.devtab->status != TSIM_OK) tsim::fail(TSIM_ERR_ARG, "program has no device tables");
+    const auto& L = p.devtab->layout;
+    out[0] = (uint64_t)L.n_ent;
+    out[1] = L.runs;
+    out[2] = L.run_outputs;
+  });
+}
+
 tsim_status tsim_sample(const tsim_program* prog, uint64_t shots, uint64_t seed, uint64_t shot_offset,
                         uint64_t* d_meas, uint64_t* d_det, uint64_t* d_obs, uint8_t* d_accept,
                         void* cuda_stream) {

@@ -50,10 +50,13 @@ constexpr int kMaxOutWords = 64;  // measurement mode: 4096 outputs
 constexpr int kMaxParities = 256;
 constexpr int kThreads = 128;
 
-enum : int { OUT_MASK = 0, OUT_BIT = 1, OUT_RANDOM = 2 };
+// Output entries, in autoregressive order.  rec is the output index (its
+// record bit); a run (detector mode) covers outputs rec .. rec + chain - 1,
+// which are X bits a .. a + chain - 1 with no constant, in one record.
+enum : int { OUT_MASK = 0, OUT_BIT = 1, OUT_RANDOM = 2, OUT_RUN = 3 };
 
 struct DChan { uint32_t n_out, thr_off, sig_off, thr0; };
-struct DOut { int32_t kind, cst, a, chain, table, pad; };
+struct DOut { int32_t kind, cst, a, chain, table, rec; };
 // Table layouts: SCALAR = distinct parities indexed per factor (one thread
 // per shot), BASIS = parities as coordinates in a GF(2) basis of their span,
 // SLICED = warp-cooperative bit-sliced evaluation (below).
@@ -92,7 +95,7 @@ struct DSeg { uint32_t par_off, n_par, sb_off, n_sb; };
 
 struct DevView {
   int W;
-  int n_ch, n_out, n_chains, n_tab;
+  int n_ch, n_out, n_ent, n_chains, n_tab;
   int nmeas, ndet, nobs, mode;
   const DChan* ch;
   const uint4* thr0;      // outcome-0 threshold per channel, 4 per block, padded with 2^32-1
@@ -749,6 +752,20 @@ __device__ __forceinline__ int get_xbit(const uint64_t (&X)[W], int b) {
   return (int)((v >> (b & 63)) & 1);
 }
 
+// `take` (1..64) bits of X starting at bit x
+template <int W>
+__device__ __forceinline__ uint64_t get_xbits(const uint64_t (&X)[W], int x, int take) {
+  const int wi = x >> 6, sh = x & 63;
+  uint64_t lo = 0, hi = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    if (w == wi) lo = X[w];
+    if (w == wi + 1) hi = X[w];
+  }
+  const uint64_t v = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
+  return take >= 64 ? v : v & ((1ull << take) - 1);
+}
+
 // One shot s of a launch (global shot index shot0 + s), records at row s.
 // Every lane of a warp calls it together (sliced tables are evaluated by the
 // whole warp); lanes past the end of the launch have valid = false and
@@ -812,10 +829,45 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, uint64_t se
   }
   const int dw = (V.ndet + 63) >> 6, mw = (V.nmeas + 63) >> 6, ow = (V.nobs + 63) >> 6;
   uint64_t ob[kMaxOutWords];  // measurement mode only
-  uint64_t cur = 0;           // detector mode: current record word
+  uint64_t cur = 0;  // detector mode: record word cw (detector words, then observable words)
+  int cw = -1;
   bool any_det = false;
-  for (int i = 0; i < V.n_out; ++i) {
-    const DOut o = V.out[i];
+  auto flush = [&]() {
+    if (cw < 0) return;
+    if (cw < dw) {
+      any_det |= cur != 0;
+      if (det && valid) det[s * dw + cw] = cur;
+    } else if (obs && valid) {
+      obs[s * ow + (cw - dw)] = cur;
+    }
+    cur = 0;
+  };
+  // bits of outputs i, i + 1, ... (within one record word) into the record
+  auto put = [&](int i, uint64_t bits) {
+    const bool is_det = i < V.ndet;
+    const int j = is_det ? i : i - V.ndet;
+    const int gw = is_det ? (j >> 6) : dw + (j >> 6);
+    if (gw != cw) {
+      flush();
+      cw = gw;
+    }
+    cur |= bits << (j & 63);
+  };
+  for (int e = 0; e < V.n_ent; ++e) {
+    const DOut o = V.out[e];
+    const int i = o.rec;
+    if (o.kind == OUT_RUN) {  // consecutive X bits straight into the record
+      int ii = i, x = o.a, n = o.chain;
+      while (n > 0) {
+        const int j = ii < V.ndet ? ii : ii - V.ndet;
+        const int take = min(n, 64 - (j & 63));
+        put(ii, get_xbits<W>(X, x, take));
+        ii += take;
+        x += take;
+        n -= take;
+      }
+      continue;
+    }
     int bit;
     if (o.kind == OUT_BIT) {
       bit = get_xbit<W>(X, o.a) ^ o.cst;
@@ -849,25 +901,13 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, uint64_t se
       }
     }
     if (V.mode == 0) {
-      // detectors are outputs [0, ndet), observables [ndet, ndet + nobs)
-      const bool is_det = i < V.ndet;
-      const int j = is_det ? i : i - V.ndet;
-      cur |= (uint64_t)bit << (j & 63);
-      const bool last = is_det ? (i + 1 == V.ndet) : (i + 1 == V.n_out);
-      if ((j & 63) == 63 || last) {
-        if (is_det) {
-          any_det |= cur != 0;
-          if (det && valid) det[s * dw + (j >> 6)] = cur;
-        } else if (obs && valid) {
-          obs[s * ow + (j >> 6)] = cur;
-        }
-        cur = 0;
-      }
+      put(i, (uint64_t)bit);  // detectors are outputs [0, ndet), observables [ndet, ndet + nobs)
     } else {
       if ((i & 63) == 0) ob[i >> 6] = 0;
       ob[i >> 6] |= (uint64_t)bit << (i & 63);
     }
   }
+  if (V.mode == 0) flush();
 
   // 4. measurement-mode records
   if (V.mode != 0) {
@@ -1241,13 +1281,17 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
   L.o_sig = s.section();
   for (const ProgChannel& c : p.channels)
     for (const auto& sg : c.sig) s.put_padded(sg, W);
-  // outputs
+  // outputs; in detector mode consecutive single-bit outputs without a
+  // constant on consecutive X bits, in the same record, become one run
   L.o_out = s.section();
   {
     int32_t mo = 0;
-    for (const ProgOutput& o : p.outputs) {
+    std::vector<DOut> ents;
+    for (size_t i = 0; i < p.outputs.size(); ++i) {
+      const ProgOutput& o = p.outputs[i];
       DOut d{};
       d.cst = o.cst;
+      d.rec = (int32_t)i;
       if (o.random) {
         d.kind = OUT_RANDOM;
         d.a = o.xbit;
@@ -1262,8 +1306,28 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
         else { d.kind = OUT_MASK; d.a = mo; }
       }
       mo += W;
-      s.put(&d, sizeof d);
+      if (p.mode == TSIM_MODE_DETECTORS && d.kind == OUT_BIT && d.cst == 0 && !ents.empty()) {
+        DOut& prev = ents.back();
+        const bool same_rec = ((int)i < p.ndet) == (prev.rec < p.ndet);
+        if (same_rec && prev.kind == OUT_BIT && prev.cst == 0 && prev.a + 1 == d.a && prev.rec + 1 == d.rec) {
+          prev.kind = OUT_RUN;
+          prev.chain = 2;
+          continue;
+        }
+        if (same_rec && prev.kind == OUT_RUN && prev.a + prev.chain == d.a && prev.rec + prev.chain == d.rec) {
+          prev.chain++;
+          continue;
+        }
+      }
+      ents.push_back(d);
     }
+    if (!ents.empty()) s.put(ents.data(), ents.size() * sizeof(DOut));
+    L.n_ent = (int)ents.size();
+    for (const DOut& d : ents)
+      if (d.kind == OUT_RUN) {
+        L.runs++;
+        L.run_outputs += (uint64_t)d.chain;
+      }
   }
   L.o_om = s.section();
   for (const ProgOutput& o : p.outputs) s.put_padded(o.mask, W);
@@ -1624,6 +1688,7 @@ DevView make_view(const unsigned char* base, const DeviceLayout& L, const Progra
   v.W = L.W;
   v.n_ch = (int)p.channels.size();
   v.n_out = (int)p.outputs.size();
+  v.n_ent = L.n_ent;
   v.n_chains = (int)p.chain_norm.size();
   v.n_tab = (int)p.tables.size();
   v.nmeas = p.nmeas;

@@ -23,6 +23,8 @@ struct DeviceLayout {
          o_cls = 0, o_fidx = 0, o_finc = 0, o_fco = 0, o_seg = 0, o_sb = 0, o_row = 0, o_dmo = 0, o_dmi = 0, o_omo = 0,
          o_omi = 0, total = 0;
   int W = 1;
+  int n_ent = 0;            // output entries (runs of single-bit outputs merged)
+  uint64_t runs = 0, run_outputs = 0;  // runs and the outputs they cover
   uint32_t sl_par_max = 0;  // largest parity list of a bit-sliced table
   uint32_t sl_rows_max = 0; // most operation rows of a staged batch
   int sl_par = 0;           // shared 32-bit words per warp for parity words (0: no sliced table)
