@@ -429,7 +429,9 @@ def run_gpu(args):
     peak = int_peak_ops()
     achieved = ops / (batch_ms / args.steps / 1e3)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": None, "kernel": "k_batch (persistent, graph replay)",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": ("k_batch (persistent kernel over all programs, graph replay)" if binfo.get("form", 0) == 0
+                       else "k_sample (each program's launch, graph replay)"),
             "ops_per_shot": ops / sum(shots),
             "peak_source": "derived: 152 SMs x 4 sub-partitions x 16 INT32 lanes x 2070 MHz",
             "measured_issue_tops": int_peaks_measured()}
