@@ -1838,47 +1838,59 @@ void device_sample(const Program& p, const SampleArgs& a, void* stream) {
 }
 
 // ----------------------------------------------------------- batch plans
-struct BatchPlan {
-  int device = -1, n = 0, wmax = 1, sms = 1;
-  int sl_par_max = 0;       // largest sliced parity buffer over the programs (0: none)
-  int sl_rb = 0;            // largest row staging buffer over the programs
-  uint32_t sb = 512;        // shots per work item
-  int blocks_per_sm = 8;
+// Programs of a batch fall in two groups, without and with sliced tables:
+// each group is one persistent launch with its own register budget (the
+// kernels with sliced tables keep fewer warps resident).
+struct BatchGroup {
+  int off = 0, n = 0;       // programs [off, off + n) of the plan's (reordered) list
+  int wmax = 1, sl_par = 0, sl_rb = 0;
   uint64_t total_items = 0;
-  std::vector<BatchProg> h_progs;
+  uint64_t* d_item_start = nullptr;   // n + 1 entries
+  unsigned long long* d_counter = nullptr;
+};
+
+struct BatchPlan {
+  int device = -1, n = 0, sms = 1;
+  uint32_t sb = 128;        // shots per work item
+  int blocks_per_sm = 8;
+  BatchGroup grp[2];
+  std::vector<BatchProg> h_progs;  // group 0 first, then group 1
   unsigned char* dmem = nullptr;
   BatchProg* d_progs = nullptr;
-  uint64_t* d_item_start = nullptr;
-  unsigned long long* d_counter = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   float tuned_ms = 0;
-  int form = 0;  // 0: one persistent launch over all work items; 1: each program's own launch
+  int form = 0;  // 0: persistent launches over the work items; 1: each program's own launch
+  uint64_t total_items() const { return grp[0].total_items + grp[1].total_items; }
+  int wmax() const { return std::max(grp[0].wmax, grp[1].wmax); }
 };
 
 namespace {
 
 void plan_items(BatchPlan& b, cudaStream_t s) {
-  std::vector<uint64_t> start((size_t)b.n + 1, 0);
-  for (int i = 0; i < b.n; ++i) start[(size_t)i + 1] = start[(size_t)i] + (b.h_progs[(size_t)i].shots + b.sb - 1) / b.sb;
-  b.total_items = start[(size_t)b.n];
-  TSIM_CUDA(cudaMemcpyAsync(b.d_item_start, start.data(), start.size() * 8, cudaMemcpyHostToDevice, s));
+  for (BatchGroup& g : b.grp) {
+    std::vector<uint64_t> start((size_t)g.n + 1, 0);
+    for (int i = 0; i < g.n; ++i)
+      start[(size_t)i + 1] = start[(size_t)i] + (b.h_progs[(size_t)(g.off + i)].shots + b.sb - 1) / b.sb;
+    g.total_items = start[(size_t)g.n];
+    TSIM_CUDA(cudaMemcpyAsync(g.d_item_start, start.data(), start.size() * 8, cudaMemcpyHostToDevice, s));
+  }
   TSIM_CUDA(cudaStreamSynchronize(s));
 }
 
 template <int W>
-cudaError_t launch_batch_w(const BatchPlan& b, cudaStream_t s, unsigned grid) {
+cudaError_t launch_group_w(const BatchPlan& b, const BatchGroup& g, cudaStream_t s, unsigned grid) {
   // every warp gets room for the transposed X at the launch's W, the
-  // largest sliced parity buffer and the largest row buffers of any program
-  const LaunchShape sh = shape_of(sl_warp_words(W, b.sl_par_max, b.sl_rb));
-  if (b.sl_par_max > 0) {
+  // largest sliced parity buffer and the largest row buffers of the group
+  const LaunchShape sh = shape_of(sl_warp_words(W, g.sl_par, g.sl_rb));
+  if (g.sl_par > 0) {
     cudaError_t e = allow_smem(k_batch<W, true>, sh.smem);
     if (e != cudaSuccess) return e;
-    k_batch<W, true><<<grid, sh.threads, sh.smem, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb,
-                                                       b.d_counter, b.sl_par_max, b.sl_rb);
+    k_batch<W, true><<<grid, sh.threads, sh.smem, s>>>(b.d_progs + g.off, g.n, g.d_item_start, g.total_items, b.sb,
+                                                       g.d_counter, g.sl_par, g.sl_rb);
   } else {
-    k_batch<W, false><<<grid, sh.threads, 0, s>>>(b.d_progs, b.n, b.d_item_start, b.total_items, b.sb, b.d_counter,
-                                                  0, 0);
+    k_batch<W, false><<<grid, sh.threads, 0, s>>>(b.d_progs + g.off, g.n, g.d_item_start, g.total_items, b.sb,
+                                                  g.d_counter, 0, 0);
   }
   return cudaGetLastError();
 }
@@ -1892,20 +1904,24 @@ cudaError_t launch_batch(const BatchPlan& b, cudaStream_t s) {
     }
     return cudaSuccess;
   }
-  cudaError_t e = cudaMemsetAsync(b.d_counter, 0, sizeof(unsigned long long), s);
-  if (e != cudaSuccess) return e;
-  if (!b.total_items) return cudaSuccess;
-  const uint64_t want = (uint64_t)b.sms * (uint64_t)b.blocks_per_sm;
-  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, b.total_items));
-  switch (b.wmax) {
-    case 1: return launch_batch_w<1>(b, s, grid);
-    case 2: return launch_batch_w<2>(b, s, grid);
-    case 4: return launch_batch_w<4>(b, s, grid);
-    case 8: return launch_batch_w<8>(b, s, grid);
-    case 16: return launch_batch_w<16>(b, s, grid);
-    case 32: return launch_batch_w<32>(b, s, grid);
-    default: return cudaErrorInvalidValue;
+  for (const BatchGroup& g : b.grp) {
+    if (!g.total_items) continue;
+    cudaError_t e = cudaMemsetAsync(g.d_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const uint64_t want = (uint64_t)b.sms * (uint64_t)b.blocks_per_sm;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, g.total_items));
+    switch (g.wmax) {
+      case 1: e = launch_group_w<1>(b, g, s, grid); break;
+      case 2: e = launch_group_w<2>(b, g, s, grid); break;
+      case 4: e = launch_group_w<4>(b, g, s, grid); break;
+      case 8: e = launch_group_w<8>(b, g, s, grid); break;
+      case 16: e = launch_group_w<16>(b, g, s, grid); break;
+      case 32: e = launch_group_w<32>(b, g, s, grid); break;
+      default: e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
   }
+  return cudaSuccess;
 }
 
 }  // namespace
@@ -1915,6 +1931,7 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
   b->n = n;
   TSIM_CUDA(cudaGetDevice(&b->device));
   TSIM_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device));
+  std::vector<BatchProg> per_group[2];
   for (int i = 0; i < n; ++i) {
     const Program& p = *progs[i];
     if (p.mode == TSIM_MODE_DETECTORS && args[i].meas)
@@ -1929,17 +1946,30 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
     bp.det = args[i].det;
     bp.obs = args[i].obs;
     bp.accept = args[i].accept;
-    b->wmax = std::max(b->wmax, bp.v.W);
-    b->sl_par_max = std::max(b->sl_par_max, bp.v.sl_par);
-    b->sl_rb = std::max(b->sl_rb, bp.v.sl_rb);
-    b->h_progs.push_back(bp);
+    const int gi = bp.v.sl_par > 0 ? 1 : 0;
+    BatchGroup& g = b->grp[gi];
+    g.wmax = std::max(g.wmax, bp.v.W);
+    g.sl_par = std::max(g.sl_par, bp.v.sl_par);
+    g.sl_rb = std::max(g.sl_rb, bp.v.sl_rb);
+    per_group[gi].push_back(bp);
   }
-  const size_t bytes = (size_t)n * sizeof(BatchProg) + ((size_t)n + 1) * 8 + 64;
+  b->grp[0].off = 0;
+  b->grp[0].n = (int)per_group[0].size();
+  b->grp[1].off = b->grp[0].n;
+  b->grp[1].n = (int)per_group[1].size();
+  for (const auto& v : per_group) b->h_progs.insert(b->h_progs.end(), v.begin(), v.end());
+  const size_t bytes = (size_t)n * sizeof(BatchProg) + ((size_t)n + 2) * 8 + 2 * 64;
   cudaError_t e = cudaMalloc(&b->dmem, bytes);
   if (e != cudaSuccess) fail(TSIM_ERR_OOM, std::string("cudaMalloc of the batch plan: ") + cudaGetErrorString(e));
   b->d_progs = (BatchProg*)b->dmem;
-  b->d_item_start = (uint64_t*)(b->dmem + (size_t)n * sizeof(BatchProg));
-  b->d_counter = (unsigned long long*)(b->dmem + (size_t)n * sizeof(BatchProg) + ((size_t)n + 1) * 8);
+  {
+    uint64_t* starts = (uint64_t*)(b->dmem + (size_t)n * sizeof(BatchProg));
+    b->grp[0].d_item_start = starts;
+    b->grp[1].d_item_start = starts + b->grp[0].n + 1;
+    unsigned char* ctr = b->dmem + (size_t)n * sizeof(BatchProg) + ((size_t)n + 2) * 8;
+    b->grp[0].d_counter = (unsigned long long*)ctr;
+    b->grp[1].d_counter = (unsigned long long*)(ctr + 64);
+  }
   cudaStream_t s = nullptr;
   TSIM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
   struct SD { cudaStream_t s; ~SD() { cudaStreamDestroy(s); } } sd{s};
@@ -1947,7 +1977,7 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
   b->sb = 128;
   plan_items(*b, s);
   if (autotune == 2) b->form = 1;
-  if (autotune == 1 && b->total_items) {
+  if (autotune == 1 && b->total_items()) {
     // shot-block size x resident blocks per SM: time every candidate twice on
     // the real batch (records are overwritten with identical values)
     cudaEvent_t e0, e1;
@@ -2032,9 +2062,9 @@ void batch_free(BatchPlan* b) {
 void batch_info(const BatchPlan* b, int64_t out[7]) {
   out[0] = b->sb;
   out[1] = b->blocks_per_sm;
-  out[2] = (int64_t)b->total_items;
+  out[2] = (int64_t)b->total_items();
   out[3] = b->exec ? 1 : 0;
-  out[4] = b->wmax;
+  out[4] = b->wmax();
   out[5] = (int64_t)(b->tuned_ms * 1000.0f);
   out[6] = b->form;
 }
