@@ -135,8 +135,11 @@ tsim_status tsim_sample(const tsim_program* prog, uint64_t shots, uint64_t seed,
                         uint64_t shot_offset, uint64_t* d_meas, uint64_t* d_det,
                         uint64_t* d_obs, uint8_t* d_accept, void* cuda_stream);
 
-/* End-to-end variant with HOST buffers (same layout as tsim_sample): allocates
- * device staging buffers, samples, copies records back, synchronises. */
+/* End-to-end variant with HOST buffers (same layout as tsim_sample): samples
+ * into a device staging buffer, copies the records back and synchronises.
+ * The staging buffer is kept per host thread and device and grown as needed
+ * (it stays allocated until the process exits); page-locked host buffers
+ * make the copies fastest. */
 tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t seed,
                              uint64_t shot_offset, uint64_t* h_meas, uint64_t* h_det,
                              uint64_t* h_obs, uint8_t* h_accept, void* cuda_stream);

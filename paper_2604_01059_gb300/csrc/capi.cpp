@@ -195,11 +195,35 @@ tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t 
     size_t mw = (size_t)(p.nmeas + 63) / 64, dw = (size_t)(p.ndet + 63) / 64, ow = (size_t)(p.nobs + 63) / 64;
     size_t bm = h_meas ? shots * mw * 8 : 0, bd = h_det ? shots * dw * 8 : 0;
     size_t bo = h_obs ? shots * ow * 8 : 0, ba = h_accept ? shots : 0;
-    unsigned char* d = nullptr;
-    size_t tot = bm + bd + bo + ba + 64;
-    cudaError_t e = cudaMalloc(&d, tot);
-    if (e != cudaSuccess) tsim::fail(TSIM_ERR_OOM, std::string("cudaMalloc staging: ") + cudaGetErrorString(e));
-    struct Free { unsigned char* d; ~Free() { cudaFree(d); } } fr{d};
+    // device staging, kept per host thread and device and grown as needed
+    // (the call synchronises before returning, so the next call may reuse it)
+    struct Staging {
+      int device = -1;
+      unsigned char* d = nullptr;
+      size_t size = 0;
+    };
+    static thread_local Staging st;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) tsim::fail(TSIM_ERR_CUDA, "cudaGetDevice failed");
+    const size_t tot = bm + bd + bo + ba + 64;
+    if (st.d && (st.device != dev || st.size < tot)) {
+      int cur = dev;
+      if (st.device != dev) cudaSetDevice(st.device);
+      cudaFree(st.d);
+      if (st.device != dev) cudaSetDevice(cur);
+      st.d = nullptr;
+      st.size = 0;
+    }
+    if (!st.d) {
+      cudaError_t e = cudaMalloc(&st.d, tot);
+      if (e != cudaSuccess) {
+        st.d = nullptr;
+        tsim::fail(TSIM_ERR_OOM, std::string("cudaMalloc staging: ") + cudaGetErrorString(e));
+      }
+      st.device = dev;
+      st.size = tot;
+    }
+    unsigned char* d = st.d;
     tsim::SampleArgs a;
     a.shots = shots;
     a.seed = seed;
