@@ -136,10 +136,12 @@ tsim_status tsim_sample(const tsim_program* prog, uint64_t shots, uint64_t seed,
                         uint64_t* d_obs, uint8_t* d_accept, void* cuda_stream);
 
 /* End-to-end variant with HOST buffers (same layout as tsim_sample): samples
- * into a device staging buffer, copies the records back and synchronises.
- * The staging buffer is kept per host thread and device and grown as needed
- * (it stays allocated until the process exits); page-locked host buffers
- * make the copies fastest. */
+ * into device staging buffers, copies the records back and synchronises.
+ * Launches of more than 2^19 shots run in up to 8 chunks, the copies of one
+ * chunk (on a stream of the library's own) overlapping the sampling of the
+ * next; the records are the same.  The staging buffers, copy stream and
+ * events are kept per host thread and device (until the process exits);
+ * page-locked host buffers make the copies fastest. */
 tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t seed,
                              uint64_t shot_offset, uint64_t* h_meas, uint64_t* h_det,
                              uint64_t* h_obs, uint8_t* h_accept, void* cuda_stream);

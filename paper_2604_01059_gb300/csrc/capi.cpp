@@ -192,57 +192,78 @@ tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t 
   return guard([&] {
     const tsim::Program& p = prog_of(prog);
     if (p.mode == TSIM_MODE_DETECTORS && h_meas) tsim::fail(TSIM_ERR_ARG, "measurement records requested from a detector-mode program");
-    size_t mw = (size_t)(p.nmeas + 63) / 64, dw = (size_t)(p.ndet + 63) / 64, ow = (size_t)(p.nobs + 63) / 64;
-    size_t bm = h_meas ? shots * mw * 8 : 0, bd = h_det ? shots * dw * 8 : 0;
-    size_t bo = h_obs ? shots * ow * 8 : 0, ba = h_accept ? shots : 0;
-    // device staging, kept per host thread and device and grown as needed
-    // (the call synchronises before returning, so the next call may reuse it)
+    if (shots == 0) return;
+    const size_t mw = (size_t)(p.nmeas + 63) / 64, dw = (size_t)(p.ndet + 63) / 64, ow = (size_t)(p.nobs + 63) / 64;
+    // bytes of one shot's records
+    const size_t row = (h_meas ? mw * 8 : 0) + (h_det ? dw * 8 : 0) + (h_obs ? ow * 8 : 0) + (h_accept ? 1 : 0);
+    // chunks of at least 2^18 shots (at most 8): the copies of one chunk
+    // overlap the sampling of the next
+    const uint64_t nchunk = std::max<uint64_t>(1, std::min<uint64_t>(8, shots >> 18));
+    const uint64_t chunk = (shots + nchunk - 1) / nchunk;
+    // per host thread and device: two staging buffers, a copy stream and
+    // events, grown as needed and kept until the process exits
     struct Staging {
       int device = -1;
       unsigned char* d = nullptr;
       size_t size = 0;
+      cudaStream_t copy = nullptr;
+      cudaEvent_t done[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
     };
     static thread_local Staging st;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) tsim::fail(TSIM_ERR_CUDA, "cudaGetDevice failed");
-    const size_t tot = bm + bd + bo + ba + 64;
-    if (st.d && (st.device != dev || st.size < tot)) {
-      int cur = dev;
-      if (st.device != dev) cudaSetDevice(st.device);
-      cudaFree(st.d);
-      if (st.device != dev) cudaSetDevice(cur);
+    const size_t half = ((chunk * row + 255) & ~(size_t)255) + 256;
+    if (st.device != dev) {  // resources of another device are left as they are
+      st = Staging();
+      st.device = dev;
+      if (cudaStreamCreateWithFlags(&st.copy, cudaStreamNonBlocking) != cudaSuccess)
+        tsim::fail(TSIM_ERR_CUDA, "cudaStreamCreate of the copy stream failed");
+      for (int b = 0; b < 2; ++b)
+        if (cudaEventCreateWithFlags(&st.done[b], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&st.freed[b], cudaEventDisableTiming) != cudaSuccess)
+          tsim::fail(TSIM_ERR_CUDA, "cudaEventCreate failed");
+    }
+    if (st.size < 2 * half) {
+      if (st.d) cudaFree(st.d);
       st.d = nullptr;
       st.size = 0;
+      cudaError_t e = cudaMalloc(&st.d, 2 * half);
+      if (e != cudaSuccess) tsim::fail(TSIM_ERR_OOM, std::string("cudaMalloc staging: ") + cudaGetErrorString(e));
+      st.size = 2 * half;
     }
-    if (!st.d) {
-      cudaError_t e = cudaMalloc(&st.d, tot);
-      if (e != cudaSuccess) {
-        st.d = nullptr;
-        tsim::fail(TSIM_ERR_OOM, std::string("cudaMalloc staging: ") + cudaGetErrorString(e));
-      }
-      st.device = dev;
-      st.size = tot;
-    }
-    unsigned char* d = st.d;
-    tsim::SampleArgs a;
-    a.shots = shots;
-    a.seed = seed;
-    a.shot_offset = shot_offset;
-    a.meas = h_meas ? (uint64_t*)d : nullptr;
-    a.det = h_det ? (uint64_t*)(d + bm) : nullptr;
-    a.obs = h_obs ? (uint64_t*)(d + bm + bd) : nullptr;
-    a.accept = h_accept ? (uint8_t*)(d + bm + bd + bo) : nullptr;
-    tsim::device_sample(p, a, cuda_stream);
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    auto cp = [&](void* dst, const void* src, size_t n) {
-      if (!n) return;
-      cudaError_t ce = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
-      if (ce != cudaSuccess) tsim::fail(TSIM_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(ce));
+    auto ck = [](cudaError_t ce, const char* what) {
+      if (ce != cudaSuccess) tsim::fail(TSIM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(ce));
     };
-    cp(h_meas, a.meas, bm);
-    cp(h_det, a.det, bd);
-    cp(h_obs, a.obs, bo);
-    cp(h_accept, a.accept, ba);
+    for (uint64_t k = 0; k < nchunk; ++k) {
+      const uint64_t first = k * chunk;
+      if (first >= shots) break;
+      const uint64_t n = std::min<uint64_t>(chunk, shots - first);
+      const int b = (int)(k & 1);
+      unsigned char* d = st.d + (size_t)b * half;
+      if (k >= 2) ck(cudaStreamWaitEvent(s, st.freed[b], 0), "cudaStreamWaitEvent");  // buffer b copied out
+      const size_t bm = h_meas ? n * mw * 8 : 0, bd = h_det ? n * dw * 8 : 0, bo = h_obs ? n * ow * 8 : 0;
+      tsim::SampleArgs a;
+      a.shots = n;
+      a.seed = seed;
+      a.shot_offset = shot_offset + first;
+      a.meas = h_meas ? (uint64_t*)d : nullptr;
+      a.det = h_det ? (uint64_t*)(d + bm) : nullptr;
+      a.obs = h_obs ? (uint64_t*)(d + bm + bd) : nullptr;
+      a.accept = h_accept ? (uint8_t*)(d + bm + bd + bo) : nullptr;
+      tsim::device_sample(p, a, cuda_stream);
+      ck(cudaEventRecord(st.done[b], s), "cudaEventRecord");
+      ck(cudaStreamWaitEvent(st.copy, st.done[b], 0), "cudaStreamWaitEvent");
+      auto cp = [&](void* dst, const void* src, size_t bytes) {
+        if (bytes) ck(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st.copy), "cudaMemcpyAsync");
+      };
+      cp(h_meas ? h_meas + first * mw : nullptr, a.meas, bm);
+      cp(h_det ? h_det + first * dw : nullptr, a.det, bd);
+      cp(h_obs ? h_obs + first * ow : nullptr, a.obs, bo);
+      cp(h_accept ? h_accept + first : nullptr, a.accept, h_accept ? n : 0);
+      ck(cudaEventRecord(st.freed[b], st.copy), "cudaEventRecord");
+    }
+    ck(cudaStreamSynchronize(st.copy), "cudaStreamSynchronize");
     tsim::device_sync(cuda_stream);
   });
 }

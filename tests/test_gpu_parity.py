@@ -125,6 +125,31 @@ def test_host_entry_point_matches_device(tmp_path):
     np.testing.assert_array_equal(acc, g["accept"])
 
 
+@pytest.mark.parametrize("name,text,mode,shots", [
+    ("cfg2", Wk.config2_circuit(p=2e-3), T.MODE_DETECTORS, 1_300_001),
+    ("cfg1_meas", Wk.config1_circuit(p=2e-3), T.MODE_MEASUREMENTS, (1 << 20) + 3),
+])
+def test_host_entry_point_in_chunks(name, text, mode, shots):
+    # more than 2^19 shots run in chunks whose copies overlap the sampling of
+    # the next one (ragged last chunk): the records equal the device path's
+    prog = T.Program(text, mode=mode)
+    g = _gpu(prog, shots, 9, 12345)
+    i = prog.info
+    meas = np.zeros((shots, i["meas_words"]), dtype=np.uint64) if mode == T.MODE_MEASUREMENTS else None
+    det = np.zeros((shots, i["det_words"]), dtype=np.uint64) if i["det_words"] else None
+    obs = np.zeros((shots, i["obs_words"]), dtype=np.uint64) if i["obs_words"] else None
+    acc = np.zeros(shots, dtype=np.uint8)
+    for rep in range(2):  # the second call reuses the staging buffers
+        T.tsim_sample_host(prog.h, shots, 9, 12345, meas, det, obs, acc)
+        if meas is not None:
+            np.testing.assert_array_equal(meas, g["meas"])
+        if det is not None:
+            np.testing.assert_array_equal(det, g["det"])
+        if obs is not None:
+            np.testing.assert_array_equal(obs, g["obs"])
+        np.testing.assert_array_equal(acc, g["accept"])
+
+
 def test_empty_and_invalid_requests():
     prog = T.Program(WORKED_EXAMPLE)
     T.tsim_sample(prog.h, 0, 1, 0)           # zero shots: no launch, no error
