@@ -270,7 +270,7 @@ tsim_status tsim_program_device_table_stats(const tsim_program* prog, int t, uin
  * consecutive terms whose distinct parities fit segment_parities 32-bit words
  * of shared memory per warp (each segment forms its own parity words; fewer
  * words let more warps reside per SM); <= 0 takes the default (1536).  The
- * defaults at compile / load time are 64, 0 and 1536.
+ * defaults at compile / load time are 4, 0 and 1536.
  * It frees the program's uploaded
  * device copy, so it must not be called while a launch of the program is in
  * flight or while a batch created from it (tsim_batch_create) exists.

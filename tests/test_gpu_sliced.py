@@ -101,8 +101,8 @@ def test_random_clifford_t_many_terms(tmp_path, k):
 
 
 def test_color_code_default_layout_is_sliced(tmp_path):
-    # the 16383-term colour-code program: its large marginals take the sliced
-    # layout by default; 97 shots (a ragged warp) checked against the oracle,
+    # the 16383-term colour-code program: its marginals of 4 terms or more
+    # take the sliced layout by default; 97 shots (a ragged warp) checked against the oracle,
     # records identical with the layout disabled
     prog = T.Program(Wk.config3_circuit())
     path = str(tmp_path / "c3.prog")
@@ -114,7 +114,7 @@ def test_color_code_default_layout_is_sliced(tmp_path):
     np.testing.assert_array_equal(g["obs"].view(np.uint64), o["obs"])
     np.testing.assert_array_equal(g["accept"], o["accept"])
     big = _records(prog, 20000, 3, 0)
-    for layout in ((64, 128, 2048), (64, 0, 512), (64, 0, 16384), (-1,)):
+    for layout in ((4, 128, 2048), (64, 0, 512), (4, 0, 16384), (-1,)):
         prog.set_table_layout(*layout)
         _same(_records(prog, 20000, 3, 0), big)
 
@@ -129,7 +129,7 @@ def test_batch_with_sliced_programs():
             if e.code == 3:
                 continue
             raise
-        p.set_table_layout(1 if k % 2 else 64)
+        p.set_table_layout(1 if k % 2 else 4)
         progs.append(p)
     progs.append(T.Program(Wk.config1_circuit()))
     w = T.Program(WORKED_EXAMPLE, mode=T.MODE_MEASUREMENTS)

@@ -18,10 +18,11 @@ def _layouts(prog):
 
 
 def test_color_code_default_layout(color_code):
-    # marginals of 64 terms or more are sliced; each segment's batches hold
-    # 32 terms but its last one, so a table has at least ceil(n / 32) batches
+    # marginals of 4 terms or more (no two with equal factor lists here) are
+    # sliced; each segment's batches hold 32 terms but its last one, so a
+    # table has at least ceil(n / 32) batches
     for (mode, nb, rows, ops, work), n in zip(_layouts(color_code), color_code.table_terms()):
-        assert mode == (T.TABLE_SLICED if n >= 64 else T.TABLE_SCALAR)
+        assert mode == (T.TABLE_SLICED if n >= 4 else T.TABLE_SCALAR)
         if mode == T.TABLE_SLICED:
             assert (n + 31) // 32 <= nb <= (n + 31) // 32 + n // 32
             assert rows % 4 == 0 or rows >= ops / 32
@@ -34,9 +35,9 @@ def test_color_code_default_layout(color_code):
 def test_segment_sizes(color_code, seg):
     # smaller segments only add batches (a partial batch per segment) and
     # never change which tables are sliced or how many operations they hold
-    color_code.set_table_layout(64, 0, seg)
+    color_code.set_table_layout(4, 0, seg)
     lay = _layouts(color_code)
-    color_code.set_table_layout(64, 0, 16384)
+    color_code.set_table_layout(4, 0, 16384)
     whole = _layouts(color_code)
     for a, b in zip(lay, whole):
         assert a[0] == b[0] and a[3] == b[3]
@@ -48,7 +49,7 @@ def test_layout_switches(color_code):
     assert T.TABLE_SLICED not in [m for m, *_ in _layouts(color_code)]
     color_code.set_table_layout(1)
     assert all(m == T.TABLE_SLICED for m, *_ in _layouts(color_code))
-    color_code.set_table_layout(64)
+    color_code.set_table_layout(4)
     with pytest.raises(T.TsimError):
         color_code.device_table_layout(color_code.info["num_tables"])
 
