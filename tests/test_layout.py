@@ -59,3 +59,28 @@ def test_worked_example_forced_sliced():
     prog.set_table_layout(1, 128, 16)
     for mode, nb, rows, ops, work in _layouts(prog):
         assert mode == T.TABLE_SLICED and nb >= 1
+
+
+def test_detector_runs_of_the_surface_code():
+    # d=5 memory: the 114 detectors are X bits in output order with no
+    # constant, so they pack as one run; the observable stays an entry
+    prog = T.Program(Wk.config2_circuit(p=1e-3))
+    entries, runs, covered = prog.device_output_stats()
+    assert (entries, runs, covered) == (2, 1, 114)
+    assert prog.info["num_detectors"] == 114 and prog.info["num_outputs"] == 115
+
+
+def test_measurement_mode_has_no_runs():
+    # runs exist only for detector / observable records
+    prog = T.Program(Wk.config1_circuit(p=2e-3), mode=T.MODE_MEASUREMENTS)
+    entries, runs, covered = prog.device_output_stats()
+    assert runs == 0 and covered == 0 and entries == prog.info["num_outputs"]
+
+
+def test_output_entries_account_for_every_output():
+    # every output is one entry or part of exactly one run
+    for text in (WORKED_EXAMPLE, Wk.config1_circuit(), Wk.config3_circuit()):
+        prog = T.Program(text)
+        entries, runs, covered = prog.device_output_stats()
+        i = prog.info
+        assert covered <= i["num_outputs"] and entries + covered - runs == i["num_outputs"]
