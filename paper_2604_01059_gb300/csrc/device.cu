@@ -22,12 +22,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <set>
 #include <string>
 #include <tuple>
+#include <unordered_map>
 
 #include "device.h"
 #include "zx.h"
@@ -1478,34 +1480,9 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
           ++t1;
         }
         if (ps.size() + 2 > (size_t)kSlMaxPar) throw PackError{TSIM_ERR_ARG, "a sliced term has too many parities"};
-        DSeg g{};
-        g.par_off = (uint32_t)(par.size() / (size_t)W);
-        par.insert(par.end(), plist[0].begin(), plist[0].end());  // 0: the zero parity
-        par.insert(par.end(), (size_t)W, 0ull);                   // kSlOnes: all ones (set on the device)
-        std::map<uint32_t, uint32_t> local;
-        local[0] = 0;
-        local[kSlOnes] = kSlOnes;
-        for (uint32_t q : ps) {  // table index q is plist[q - 1]
-          local[q] = (uint32_t)local.size();
-          par.insert(par.end(), plist[q - 1].begin(), plist[q - 1].end());
-        }
-        g.n_par = (uint32_t)local.size();
-        for (uint32_t q : ps) {
-          uint64_t pop = 0;
-          for (uint64_t m : plist[q - 1]) pop += (uint64_t)__builtin_popcountll(m);
-          w32 += 3 + 3 * pop;
-        }
-        w32 += 2 * 3;
-        // rows hold byte offsets of the segment's parity words: 4q, or
-        // 4qa | 4qb << 16 for pi-pairs
+        // the segment's terms, sorted by magnitude then by operation counts
+        // (so that a batch's terms need similar numbers of rows per code)
         std::vector<SlTerm> lt(sterms.begin() + (long)t0, sterms.begin() + (long)t1);
-        for (SlTerm& t : lt)
-          for (int c = 0; c < kSlCodes; ++c) {
-            for (uint64_t& r : t.ops[c])
-              r = c == SL_XOR4AB ? ((uint64_t)(4 * local.at((uint32_t)r)) | ((uint64_t)(4 * local.at((uint32_t)(r >> 32))) << 16))
-                                 : (uint64_t)(4 * local.at((uint32_t)r));
-            std::sort(t.ops[c].begin(), t.ops[c].end());
-          }
         std::stable_sort(lt.begin(), lt.end(), [](const SlTerm& a, const SlTerm& b) {
           if (a.d != b.d) return a.d < b.d;
           size_t na = 0, nb = 0;
@@ -1515,38 +1492,127 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
             if (a.ops[c].size() != b.ops[c].size()) return a.ops[c].size() > b.ops[c].size();
           return false;
         });
-        g.sb_off = (uint32_t)sbs.size();
+        // batches of 32 terms and their rows, as table-wide parity indices
+        // (0 and kSlOnes for padding, qa | qb << 32 for pi-pairs)
+        struct PBatch {
+          size_t b0, b1;
+          uint16_t cnt[kSlCodes];
+        };
+        std::vector<PBatch> pb;
+        std::vector<std::array<uint64_t, 32>> prow;
+        std::vector<int> prow_code;
         for (size_t b0 = 0; b0 < lt.size();) {
           size_t b1 = b0;
           while (b1 < lt.size() && b1 - b0 < 32 && lt[b1].d == lt[b0].d) ++b1;
-          DSBatch B{};
-          B.row_off = (uint32_t)rows.size();
-          B.d = lt[b0].d;
-          for (size_t l = 0; l < b1 - b0; ++l) {
-            const SlTerm& t = lt[b0 + l];
-            B.valid |= 1u << l;
-            for (int bit = 0; bit < 3; ++bit) B.j0m[bit] |= (uint32_t)((t.j >> bit) & 1) << l;
-          }
-          uint32_t nrows = 0;
+          PBatch B{b0, b1, {}};
           for (int c = 0; c < kSlCodes; ++c) {
             size_t n = 0;
             for (size_t l = b0; l < b1; ++l) n = std::max(n, lt[l].ops[c].size());
             n = (n + 3) & ~(size_t)3;  // whole groups of 4 rows: no single-row tail loop on the device
             if (n > 0xFFFF) throw PackError{TSIM_ERR_ARG, "too many operations of one kind in a term"};
             B.cnt[c] = (uint16_t)n;
-            // groups of 4 rows: [group][lane][4], so a lane's 4 rows are 16
-            // contiguous bytes and a group is 512 contiguous bytes
-            for (size_t g = 0; g < n / 4; ++g)
+            for (size_t k = 0; k < n; ++k) {
+              std::array<uint64_t, 32> r;
+              for (size_t l = 0; l < 32; ++l) {
+                const size_t ti = b0 + l;
+                r[l] = (ti < b1 && k < lt[ti].ops[c].size()) ? lt[ti].ops[c][k] : (c == SL_ZEROC ? kSlOnes : 0u);
+              }
+              prow.push_back(r);
+              prow_code.push_back(c);
+            }
+          }
+          pb.push_back(B);
+          b0 = b1;
+        }
+        // shared-memory slot of every parity: word q of the buffer lies in
+        // bank q mod 32, and the 32 lanes of a row read their words at once,
+        // so distinct parities of one row go to distinct banks where possible
+        // (greedy, in row order; slot = bank + 32 x fill)
+        std::unordered_map<uint32_t, uint32_t> slot;
+        slot.reserve(ps.size() * 2 + 4);
+        slot[0] = 0;
+        slot[kSlOnes] = kSlOnes;
+        uint32_t fill[32] = {0};
+        fill[0] = fill[1] = 1;
+        const uint32_t cap = (uint32_t)((ps.size() + 2 + 31) / 32) + 1;
+        for (size_t ri = 0; ri < prow.size(); ++ri) {
+          uint32_t qs[64];
+          int nq = 0;
+          for (uint64_t v : prow[ri]) {
+            qs[nq++] = (uint32_t)v;
+            if (prow_code[ri] == SL_XOR4AB && (v >> 32)) qs[nq++] = (uint32_t)(v >> 32);
+          }
+          std::sort(qs, qs + nq);
+          nq = (int)(std::unique(qs, qs + nq) - qs);
+          int used[32] = {0};
+          for (int k = 0; k < nq; ++k) {
+            auto it = slot.find(qs[k]);
+            if (it != slot.end()) used[it->second & 31]++;
+          }
+          for (int k = 0; k < nq; ++k) {
+            if (slot.count(qs[k])) continue;
+            int best = -1;
+            for (int b = 0; b < 32; ++b)
+              if (fill[b] < cap && (best < 0 || used[b] < used[best] || (used[b] == used[best] && fill[b] < fill[best])))
+                best = b;
+            slot[qs[k]] = (uint32_t)best + 32u * fill[best];
+            fill[best]++;
+            used[best]++;
+          }
+        }
+        uint32_t nslot = 2;
+        for (const auto& kv : slot) nslot = std::max(nslot, kv.second + 1);
+        if (nslot > (uint32_t)kSlMaxPar) throw PackError{TSIM_ERR_ARG, "a sliced term has too many parities"};
+        DSeg g{};
+        g.par_off = (uint32_t)(par.size() / (size_t)W);
+        g.n_par = nslot;
+        {
+          std::vector<uint32_t> of_slot(nslot, 0);  // table parity index per slot (0: none)
+          for (const auto& kv : slot)
+            if (kv.first > kSlOnes) of_slot[kv.second] = kv.first;
+          for (uint32_t sl = 0; sl < nslot; ++sl) {
+            // slot 0: the zero parity; kSlOnes: all ones (set on the device);
+            // unused slots: zero masks
+            if (of_slot[sl]) par.insert(par.end(), plist[of_slot[sl] - 1].begin(), plist[of_slot[sl] - 1].end());
+            else par.insert(par.end(), (size_t)W, 0ull);
+          }
+        }
+        for (uint32_t q : ps) {
+          uint64_t pop = 0;
+          for (uint64_t m : plist[q - 1]) pop += (uint64_t)__builtin_popcountll(m);
+          w32 += 3 + 3 * pop;
+        }
+        w32 += 3 * (uint64_t)(nslot - ps.size());
+        // rows hold byte offsets of the slots' words: 4 slot, or
+        // 4 slot_a | 4 slot_b << 16 for pi-pairs; groups of 4 rows are
+        // [group][lane][4], so a lane's 4 rows are 16 contiguous bytes
+        g.sb_off = (uint32_t)sbs.size();
+        size_t ri = 0;
+        for (const PBatch& P : pb) {
+          DSBatch B{};
+          B.row_off = (uint32_t)rows.size();
+          B.d = lt[P.b0].d;
+          for (size_t l = 0; l < P.b1 - P.b0; ++l) {
+            const SlTerm& t = lt[P.b0 + l];
+            B.valid |= 1u << l;
+            for (int bit = 0; bit < 3; ++bit) B.j0m[bit] |= (uint32_t)((t.j >> bit) & 1) << l;
+          }
+          uint32_t nrows = 0;
+          for (int c = 0; c < kSlCodes; ++c) {
+            const size_t n = P.cnt[c];
+            B.cnt[c] = (uint16_t)n;
+            for (size_t gi = 0; gi < n / 4; ++gi)
               for (size_t l = 0; l < 32; ++l)
-                for (size_t k = 4 * g; k < 4 * g + 4; ++k) {
-                  const size_t ti = b0 + l;
-                  uint32_t r = c == SL_ZEROC ? 4 * kSlOnes : 0u;  // padding leaves J and Z unchanged
-                  if (ti < b1 && k < lt[ti].ops[c].size()) {
-                    r = (uint32_t)lt[ti].ops[c][k];
-                    ++real_ops;
-                  }
+                for (size_t k = 4 * gi; k < 4 * gi + 4; ++k) {
+                  const uint64_t v = prow[ri + k][l];
+                  uint32_t r;
+                  if (c == SL_XOR4AB) r = (4 * slot.at((uint32_t)v)) | ((4 * slot.at((uint32_t)(v >> 32))) << 16);
+                  else r = 4 * slot.at((uint32_t)v);
+                  const size_t ti = P.b0 + l;
+                  if (ti < P.b1 && k < lt[ti].ops[c].size()) ++real_ops;
                   rows.push_back(r);
                 }
+            ri += n;
             padded_rows += n;
             nrows += (uint32_t)n;
             w32 += (uint64_t)n * 32 * (uint64_t)kRowOps[c];
@@ -1555,7 +1621,6 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
           most = std::max(most, nrows);
           if (rows.size() > 0xFFFFFFFFull) throw PackError{TSIM_ERR_ARG, "sliced tables too large"};
           sbs.push_back(B);
-          b0 = b1;
         }
         g.n_sb = (uint32_t)(sbs.size() - g.sb_off);
         nbatches += g.n_sb;
