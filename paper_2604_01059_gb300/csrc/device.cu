@@ -1097,9 +1097,6 @@ struct FacKey {
   bool operator<(const FacKey& o) const {
     return std::tie(kind, alpha, beta, ia, ib) < std::tie(o.kind, o.alpha, o.beta, o.ia, o.ib);
   }
-  bool operator==(const FacKey& o) const {
-    return kind == o.kind && alpha == o.alpha && beta == o.beta && ia == o.ia && ib == o.ib;
-  }
 };
 
 // A term of a sliced table: constant phase j, magnitude exponent d, and the

@@ -38,10 +38,10 @@ def _layouts(prog):
 
 def _check_layouts(tmp_path, prog, shots, seed, offset, oracle_shots):
     ref = _records(prog, shots, seed, offset)
-    prog.set_table_layout(1)
+    prog.set_table_layout(1, 128)  # rows staged through shared memory by bulk copies
     forced = _layouts(prog)
     sl = _records(prog, shots, seed, offset)
-    prog.set_table_layout(1, 0)  # rows read from global memory instead of staged
+    prog.set_table_layout(1, 0)  # rows read through L1
     _same(_records(prog, shots, seed, offset), sl)
     prog.set_table_layout(-1)
     assert T.TABLE_SLICED not in _layouts(prog)
