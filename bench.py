@@ -70,6 +70,23 @@ def parse():
     return args
 
 
+def shard_offsets(rank, shots):
+    """Weak scaling: rank r samples shots [r n, (r + 1) n) of every program
+    (the Philox counter is the global shot index, so the ranks' records
+    concatenate to one run over all of them)."""
+    return [rank * n for n in shots]
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest value over the ranks (timings: the slowest rank decides)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -329,7 +346,7 @@ def run_gpu(args):
     n = len(progs)
     assert n == len(plain_progs)
     shots = [shots_of(k) for k in range(n)]
-    offsets = [rank * shots[k] for k in range(n)]  # weak scaling: every rank its own shot range
+    offsets = shard_offsets(rank, shots)  # weak scaling: every rank its own shot range
     seeds = [SEED] * n
     stream = torch.cuda.current_stream()
     outs = _outputs(progs, shots)
@@ -370,11 +387,7 @@ def run_gpu(args):
             barrier()
             total += e0.elapsed_time(e1)
         T.tsim_sync(stream)
-        if dist is not None:
-            t = torch.tensor([total], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
-        return total
+        return max_over_ranks(total, dist, "cuda")
 
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     ids = [v.strip() for v in vis.split(",") if v.strip()]
@@ -420,11 +433,7 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         e2e_step()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = shots_step * e2e_steps / e2e_s
     d2h = sum(ns * (p.info["det_words"] * 8 + p.info["obs_words"] * 8 + 1) for p, ns in zip(progs, shots))
 
