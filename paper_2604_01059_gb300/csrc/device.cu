@@ -181,6 +181,20 @@ struct RoundKeys {
   uint32_t k0[10], k1[10];
 };
 
+// the round keys of key (seed lo, seed hi): key + r * (0x9E3779B9, 0xBB67AE85)
+__host__ __device__ __forceinline__ RoundKeys round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = k0;
+    rk.k1[r] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return rk;
+}
+
 __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                               const RoundKeys& rk, uint32_t o[4]) {
 #pragma unroll
@@ -773,21 +787,10 @@ __device__ __forceinline__ uint64_t get_xbits(const uint64_t (&X)[W], int x, int
 // whole warp); lanes past the end of the launch have valid = false and
 // compute a shot whose records are not written.  sm: the warp's shared words.
 template <int W, bool SL>
-__device__ void sample_one(const DevView& V, uint64_t s, bool valid, uint64_t seed, uint64_t shot0,
+__device__ void sample_one(const DevView& V, uint64_t s, bool valid, const RoundKeys& rk, uint64_t shot0,
                            uint64_t* __restrict__ meas, uint64_t* __restrict__ det,
                            uint64_t* __restrict__ obs, uint8_t* __restrict__ accept, const SlSmem& sm) {
   const uint64_t shot = shot0 + s;
-  RoundKeys rk;
-  {
-    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-      rk.k0[r] = k0;
-      rk.k1[r] = k1;
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-  }
   const uint32_t c0 = (uint32_t)shot, c1 = (uint32_t)(shot >> 32);
   int st = 0;
 
@@ -965,7 +968,7 @@ constexpr int min_blocks(int W, bool sl) {
 constexpr int min_blocks_batch(int W, bool sl) { return sl && W <= 4 ? 5 : min_blocks(W, sl); }
 
 template <int W, bool SL>
-__global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_sample(DevView V, uint64_t seed, uint64_t shot0,
+__global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_sample(DevView V, RoundKeys rk, uint64_t shot0,
                                                      uint64_t nshots, uint64_t* __restrict__ meas,
                                                      uint64_t* __restrict__ det,
                                                      uint64_t* __restrict__ obs,
@@ -976,7 +979,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_sample(DevView 
     sm = sl_smem(g_warp_smem + (threadIdx.x >> 5) * sl_warp_words(W, V.sl_par, V.sl_rb), W, V.sl_par, V.sl_rb);
     sl_init(sm);
   }
-  sample_one<W, SL>(V, s, s < nshots, seed, shot0, meas, det, obs, accept, sm);
+  sample_one<W, SL>(V, s, s < nshots, rk, shot0, meas, det, obs, accept, sm);
 }
 
 // ------------------------------------------------------- batched launch
@@ -1019,9 +1022,10 @@ __global__ void __launch_bounds__(kThreads, min_blocks_batch(W, SL)) k_batch(con
     const BatchProg& P = progs[lo];
     const uint64_t first = (it - item_start[lo]) * sb;
     const uint64_t last = min(first + sb, P.shots);
+    const RoundKeys rk = round_keys(P.seed);
     for (uint64_t s0 = first; s0 < last; s0 += 32) {
       const uint64_t s = s0 + lane;
-      sample_one<W, SL>(P.v, s, s < last, P.seed, P.shot_offset, P.meas, P.det, P.obs, P.accept, sm);
+      sample_one<W, SL>(P.v, s, s < last, rk, P.shot_offset, P.meas, P.det, P.obs, P.accept, sm);
     }
   }
 }
@@ -1853,9 +1857,10 @@ cudaError_t launch_w(const DevView& v, cudaStream_t s, uint64_t seed, uint64_t o
   if (v.sl_par > 0) {
     cudaError_t e = allow_smem(k_sample<W, true>, sh.smem);
     if (e != cudaSuccess) return e;
-    k_sample<W, true><<<(unsigned)blocks, sh.threads, sh.smem, s>>>(v, seed, off, shots, meas, det, obs, acc);
+    k_sample<W, true><<<(unsigned)blocks, sh.threads, sh.smem, s>>>(v, round_keys(seed), off, shots, meas, det, obs,
+                                                                     acc);
   } else {
-    k_sample<W, false><<<(unsigned)blocks, sh.threads, 0, s>>>(v, seed, off, shots, meas, det, obs, acc);
+    k_sample<W, false><<<(unsigned)blocks, sh.threads, 0, s>>>(v, round_keys(seed), off, shots, meas, det, obs, acc);
   }
   return cudaGetLastError();
 }
