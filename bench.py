@@ -471,11 +471,22 @@ def run_gpu(args):
                 "speedup_vs_plain": value / plain,
                 "e2e": {"value": e2e, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                         "api": "tsim_sample_host (device staging, records copied to page-locked host memory inside the timed region)"},
-                "gpu_launches": args.steps, "roofline": roof, "clocks": clk,
+                "gpu_launches": args.steps * launches_per_step(progs, shots, binfo), "roofline": roof, "clocks": clk,
                 "cpu_baseline": base}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
+
+
+def launches_per_step(progs, shots, binfo):
+    """Kernel launches one replay of the batch graph makes: one per program in
+    the one-launch-per-program form; otherwise one persistent launch per group
+    (programs without and with bit-sliced tables)."""
+    live = [p for p, n in zip(progs, shots) if n > 0]
+    if binfo.get("form", 0) == 1:
+        return len(live)
+    sliced = [any(p.device_table_layout(t)[0] == 2 for t in range(p.info["num_tables"])) for p in live]
+    return int(any(sliced)) + int(not all(sliced))
 
 
 def kernel_int_ops(prog):
