@@ -69,8 +69,10 @@ typedef struct {
   int decomp;            /* stabilizer decomposition policy (Appendix "Stabilizer
                             decompositions"): HEURISTIC = pairs of non-Clifford
                             vertices in ascending order (2 terms per pair, alpha = 0.5),
-                            SINGLE_T = one T-state cut at a time, LEARNED = order scored
-                            by the cut-order network, heuristic as fallback. */
+                            SINGLE_T = one T-state cut at a time, LEARNED = the three
+                            first cuts the cut-order network ranks best, each followed
+                            by the heuristic order, against the heuristic itself
+                            (kept only with strictly fewer terms). */
   uint64_t chi_budget;   /* maximum stabilizer terms per marginal; 0 = 1<<20 */
   int channel_reduction; /* 1 = apply the four steps of Appendix "Channel reduction" */
   uint64_t total_budget; /* maximum stabilizer terms summed over all marginals; 0 = none.
@@ -353,13 +355,16 @@ tsim_status tsim_cut_train(const char* dataset_path, int epochs, int batch_graph
 /* Register (params != NULL) the network used by TSIM_DECOMP_LEARNED on the
  * current device, or remove it (NULL).  Without a model, or when scoring
  * fails, LEARNED compiles with the heuristic order.  With a model the
- * compiler decomposes each marginal in both orders and keeps the one with
- * fewer terms. */
+ * compiler decomposes each marginal in the heuristic order and with each of
+ * the three first cuts the network ranks best (the rest in the heuristic
+ * order, each bounded by the fewest terms so far), and keeps a learned first
+ * cut only when it has strictly fewer terms. */
 tsim_status tsim_cut_model_set(const float* params);
 
 /* out[0] = scorer calls, out[1] = calls that produced scores, out[2] =
- * marginals that kept the learned order, out[3] = marginals where the
- * heuristic order had fewer terms (counts since the library was loaded). */
+ * marginals where a learned first cut had strictly fewer terms, out[3] =
+ * marginals that kept the heuristic order (counts since the library was
+ * loaded). */
 tsim_status tsim_cut_policy_stats(uint64_t out[4]);
 
 #ifdef __cplusplus

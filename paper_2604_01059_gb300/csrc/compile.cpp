@@ -332,10 +332,11 @@ std::atomic<CutScorer> g_cut_scorer{nullptr};
 std::atomic<uint64_t> g_cut_stats[4];
 
 // Decompose one marginal diagram.  LEARNED: the spiders of the simplified
-// diagram are scored by the cut-order network and cut in ascending score;
-// the heuristic order is decomposed as well and judges (the order with fewer
-// terms wins; both give the same exact sum).  Without a scorer LEARNED falls
-// back to the heuristic.
+// diagram are scored by the cut-order network (trained on the term count of
+// each spider as the first cut), and the best-ranked first cuts are tried
+// against the heuristic order, which judges (a learned first cut is kept only
+// with strictly fewer terms; every order gives the same exact sum).  Without
+// a scorer LEARNED falls back to the heuristic.
 // When set, compile_program records each marginal's diagram after the
 // Clifford rewrites and stops before decomposing anything.
 thread_local std::vector<Graph>* g_marginal_capture = nullptr;
@@ -367,26 +368,59 @@ void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget,
     decompose(M, TSIM_DECOMP_HEURISTIC, out, st);
     return;
   }
-  // the heuristic order first; the learned order then runs with the
-  // heuristic's term count as its budget, so a worse order stops as soon as
-  // it has more terms (and costs no more than the heuristic did)
-  std::vector<Term> learned, heuristic;
-  DecompStats s1 = st, s2 = st;
-  uint64_t t1 = total ? *total : 0, t2 = t1;
-  s1.total = &t1;
+  // The network was trained to rank spiders as the FIRST cut (the rest in
+  // the heuristic order): decompose the heuristic order, then the three
+  // best-ranked first cuts, each with the fewest terms so far as its budget
+  // (a worse order stops as soon as it exceeds it).  The heuristic is the
+  // fallback and the judge: a learned first cut is kept only when it has
+  // strictly fewer terms.
+  std::vector<Term> heuristic;
+  DecompStats s2 = st;
+  uint64_t t2 = total ? *total : 0;
   s2.total = &t2;
-  bool ok1 = true, ok2 = true;
+  bool ok2 = true;
   try { decompose(M, TSIM_DECOMP_HEURISTIC, heuristic, s2); } catch (const Error& e) {
     if (e.code != TSIM_ERR_CHI_BUDGET) throw;
     ok2 = false;
   }
-  if (ok2) s1.budget = std::min<uint64_t>(s1.budget, std::max<uint64_t>(heuristic.size(), 1));
-  try { decompose(M, TSIM_DECOMP_LEARNED, learned, s1, &scores); } catch (const Error& e) {
-    if (e.code != TSIM_ERR_CHI_BUDGET || !ok2) throw;
-    ok1 = false;
+  std::vector<int> cand;  // non-Clifford spiders by predicted term count
+  int own_first = -1;     // the heuristic's own first cut: the lowest odd spider
+  for (int v = 0; v < M.n; ++v)
+    if (M.alive[(size_t)v] && (M.lam[(size_t)v] & 1)) {
+      if (own_first < 0) own_first = v;
+      cand.push_back(v);
+    }
+  std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
+    return scores[(size_t)a] < scores[(size_t)b];
+  });
+  std::vector<Term> learned;
+  uint64_t t1 = t2;
+  bool ok1 = false;
+  int tried = 0;
+  for (size_t k = 0; k < cand.size() && tried < 3; ++k) {
+    if (cand[k] == own_first) continue;
+    ++tried;
+    std::vector<Term> trial;
+    DecompStats s1 = st;
+    uint64_t tt = total ? *total : 0;
+    s1.total = &tt;
+    const uint64_t best = ok1 ? learned.size() : (ok2 ? heuristic.size() : 0);
+    if (best) s1.budget = std::min<uint64_t>(s1.budget ? s1.budget : best, best > 1 ? best - 1 : 1);
+    try {
+      decompose(M, TSIM_DECOMP_HEURISTIC, trial, s1, nullptr, cand[k]);
+    } catch (const Error& e) {
+      if (e.code != TSIM_ERR_CHI_BUDGET) throw;
+      continue;
+    }
+    if (!ok1 || trial.size() < learned.size()) {
+      learned.swap(trial);
+      t1 = tt;
+      ok1 = true;
+    }
   }
+  if (!ok1 && !ok2) fail(TSIM_ERR_CHI_BUDGET, "stabilizer terms exceed the budget");
   g_cut_stats[1]++;
-  const bool use_learned = ok1 && (!ok2 || learned.size() <= heuristic.size());
+  const bool use_learned = ok1 && (!ok2 || learned.size() < heuristic.size());
   g_cut_stats[use_learned ? 2 : 3]++;
   out = use_learned ? std::move(learned) : std::move(heuristic);
   if (total) *total = use_learned ? t1 : t2;

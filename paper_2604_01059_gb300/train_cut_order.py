@@ -9,6 +9,8 @@ compiler measures when a candidate spider is cut first (written by
 library's CUDA kernels (BF16 weights, FP32 accumulation, Adam).  Output:
 ``cut_order.f32`` (the parameter vector, little-endian float32, in the layout
 ``tsim_cut_num_params`` documents) and ``cut_order.json`` (how it was made).
+``--evaluate PATH`` reports the ranking quality of the weights on a held-out
+dataset.
 """
 import argparse
 import json
@@ -34,6 +36,33 @@ def load_weights(path=WEIGHTS):
     return p
 
 
+def evaluate(params, dataset_path):
+    """Ranking quality on a dataset: per graph with two or more labelled
+    spiders, the term count (log2) of the spider the network ranks first
+    against the mean over the labelled spiders (a random first cut) and the
+    best one; scores come from the library's CUDA forward pass."""
+    from . import tsim_cut_forward
+    x, rp, col, y, go = read_cut_dataset(dataset_path)
+    s = tsim_cut_forward(params, x, rp, col)
+    top, rnd, best, hits, n = [], [], [], 0, 0
+    for g in range(len(go) - 1):
+        idx = np.arange(go[g], go[g + 1])
+        lab = idx[~np.isnan(y[idx])]
+        if len(lab) < 2:
+            continue
+        n += 1
+        pick = lab[np.argmin(s[lab])]
+        top.append(float(y[pick]))
+        rnd.append(float(np.mean(y[lab])))
+        best.append(float(np.min(y[lab])))
+        hits += int(y[pick] == np.min(y[lab]))
+    top, rnd, best = np.array(top), np.array(rnd), np.array(best)
+    return {"graphs": n, "top_ranked_log2_terms": float(top.mean()), "random_log2_terms": float(rnd.mean()),
+            "best_log2_terms": float(best.mean()), "top_is_best": hits / max(n, 1),
+            "terms_ratio_random_over_top": float(np.mean(2.0 ** (rnd - top))),
+            "terms_ratio_top_over_best": float(np.mean(2.0 ** (top - best)))}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--dataset", default=None, help="dataset file (generated when missing)")
@@ -48,7 +77,11 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=WEIGHTS)
+    ap.add_argument("--evaluate", default=None, help="held-out dataset: report the ranking quality of --out")
     a = ap.parse_args(argv)
+    if a.evaluate:
+        print(json.dumps(evaluate(load_weights(a.out), a.evaluate)))
+        return
     ds = a.dataset or os.path.join(os.path.dirname(os.path.abspath(a.out)), "cut_order_dataset.bin")
     t0 = time.time()
     if not os.path.exists(ds):
