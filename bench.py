@@ -104,11 +104,10 @@ def cut_model():
     return load_weights()
 
 
-def config4_programs(n=256, decomp=0):
+def config4_programs(n=256):
     """Compile the batched workload in parallel host threads; circuits over the
     term budgets are skipped and the next seeds drawn (deterministic order).
-    The learned order never has more terms than the heuristic one, so the
-    same circuits pass the budgets in both forms."""
+    Returns (program, shots, circuit text) triples."""
     from concurrent.futures import ThreadPoolExecutor
 
     import paper_2604_01059_gb300 as T
@@ -123,15 +122,10 @@ def config4_programs(n=256, decomp=0):
             if e.code == 3:
                 return None
             raise
-        if p.info["total_terms"] > CFG4_PROGRAM_BUDGET:
-            return None
-        if decomp:
-            p = T.Program(txt, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
-        return (p, shots)
+        return (p, shots, txt) if p.info["total_terms"] <= CFG4_PROGRAM_BUDGET else None
 
     out = []
-    workers = 1 if decomp else (os.cpu_count() or 1)  # the learned order scores on the GPU
-    with ThreadPoolExecutor(max_workers=workers) as ex:
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
         for k in range(0, len(pool), 64):
             for r in ex.map(build, pool[k:k + 64]):
                 if r is not None and len(out) < n:
@@ -141,16 +135,27 @@ def config4_programs(n=256, decomp=0):
     return out
 
 
+CFG4_TEXTS = None
+
+
 def programs(decomp=0):
+    """The workload's programs.  The batched workload's circuits are selected
+    once with the heuristic order; another order compiles the same circuits
+    (it never has more terms, so they stay within the budgets)."""
     import paper_2604_01059_gb300 as T
     from paper_2604_01059_gb300 import workloads as Wk
-    global SHOTS_LIST
+    global SHOTS_LIST, CFG4_TEXTS
     if WORKLOAD_NAME == "cfg3":
         return [T.Program(Wk.config3_circuit(p=1e-3), decomp=decomp)]
     if WORKLOAD_NAME == "cfg4":
-        pr = config4_programs(decomp=decomp)
-        SHOTS_LIST = [s for _, s in pr]
-        return [p for p, _ in pr]
+        if CFG4_TEXTS is None or decomp == 0:
+            pr = config4_programs()
+            SHOTS_LIST = [s for _, s, _ in pr]
+            CFG4_TEXTS = [t for _, _, t in pr]
+            if decomp == 0:
+                return [p for p, _, _ in pr]
+        return [T.Program(t, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
+                for t in CFG4_TEXTS]
     return [T.Program(Wk.config2_circuit(p=p), decomp=decomp) for p in P_VALUES]
 
 
