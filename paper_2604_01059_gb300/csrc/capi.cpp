@@ -224,6 +224,7 @@ tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t 
           tsim::fail(TSIM_ERR_CUDA, "cudaEventCreate failed");
     }
     if (st.size < 2 * half) {
+      if (st.copy) cudaStreamSynchronize(st.copy);
       if (st.d) cudaFree(st.d);
       st.d = nullptr;
       st.size = 0;
@@ -235,6 +236,8 @@ tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t 
     auto ck = [](cudaError_t ce, const char* what) {
       if (ce != cudaSuccess) tsim::fail(TSIM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(ce));
     };
+    // copies left by a call that failed part-way must not race with this one
+    ck(cudaStreamSynchronize(st.copy), "cudaStreamSynchronize");
     for (uint64_t k = 0; k < nchunk; ++k) {
       const uint64_t first = k * chunk;
       if (first >= shots) break;
