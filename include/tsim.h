@@ -150,9 +150,11 @@ tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t 
 
 /* Batched launch: n programs, each with its own shots / seed / offset and its
  * own output pointers (arrays of n device pointers; entries may be NULL), in
- * one persistent-kernel launch over (program, shot-block) work items.  Every
- * record equals what tsim_sample gives for the same program, seed and shot.
- * Synchronises cuda_stream before returning (the plan it builds is freed). */
+ * persistent launches over (program, shot-block) work items: one for the
+ * programs without bit-sliced tables and one for those with (each with its
+ * own register budget).  Every record equals what tsim_sample gives for the
+ * same program, seed and shot.  Synchronises cuda_stream before returning (the
+ * plan it builds is freed). */
 tsim_status tsim_sample_batch(const tsim_program* const* progs, int n, const uint64_t* shots,
                               const uint64_t* seeds, const uint64_t* shot_offsets,
                               uint64_t* const* d_meas, uint64_t* const* d_det,
@@ -183,7 +185,7 @@ tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t shots, uint64
                                 uint64_t* d_obs, uint8_t* d_accept, void* cuda_stream);
 
 /* Reusable batched launch (Appendix "Additional benchmarks": batched sampling;
- * here heterogeneous programs share one persistent kernel).  tsim_batch_create
+ * here heterogeneous programs share persistent kernels).  tsim_batch_create
  * uploads every program, lays out the (program, shot-block) work items,
  * (autotune = 1) autotunes the shots per work item (32, 128 or 512; 128
  * without autotuning; each item is taken by one warp) and the resident
