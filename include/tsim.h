@@ -295,6 +295,15 @@ tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, ui
  * outputs covered by runs. */
 tsim_status tsim_program_device_output_stats(const tsim_program* prog, uint64_t out[3]);
 
+/* Self-check of the bit-sliced layout (host only, no GPU): every SLICED table
+ * of the packed program is evaluated by a host emulation of the
+ * warp-cooperative kernel, reading the packed segments, batches and rows
+ * exactly as the kernel does, for rounds x 32 seeded random per-shot vectors
+ * X, and compared exactly with the table's value from its term list (Eqs.
+ * parities, scalar_product).  TSIM_ERR_INTERNAL names the first table that
+ * differs. */
+tsim_status tsim_selftest_sliced(const tsim_program* prog, uint64_t seed, int rounds);
+
 /* Self-check of the compiler's rewrite rules against brute-force summation on
  * random small parameterised graphs (no GPU).  Returns TSIM_OK when all pass. */
 tsim_status tsim_selftest_rules(uint64_t seed, int iterations);

@@ -20,7 +20,7 @@ __all__ = [
     "tsim_raw_to_x", "tsim_program_save", "tsim_program_load", "tsim_program_free",
     "tsim_last_error", "tsim_selftest_rules", "tsim_measure_int_peak", "tsim_program_device_table_stats",
     "tsim_program_set_table_layout", "tsim_program_device_table_layout", "tsim_program_device_output_stats",
-    "load_library",
+    "tsim_selftest_sliced", "load_library",
     "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T",
 ]
 
@@ -102,6 +102,7 @@ def load_library(path: str | None = None):
     L.tsim_program_set_table_layout.argtypes = [vp, i64, i32, i32]
     L.tsim_program_device_table_layout.argtypes = [vp, i32, ctypes.POINTER(u64)]
     L.tsim_program_device_output_stats.argtypes = [vp, ctypes.POINTER(u64)]
+    L.tsim_selftest_sliced.argtypes = [vp, u64, i32]
     L.tsim_cut_num_params.argtypes = []
     L.tsim_cut_init_params.argtypes = [u64, vp]
     L.tsim_cut_dataset.argtypes = [u64, i32, i32, i32, u64, i32, ctypes.c_char_p]
@@ -116,7 +117,8 @@ def load_library(path: str | None = None):
               "tsim_batch_launch", "tsim_batch_info", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
               "tsim_program_save", "tsim_program_load", "tsim_selftest_rules", "tsim_measure_int_peak",
               "tsim_program_device_table_stats", "tsim_program_set_table_layout",
-              "tsim_program_device_table_layout", "tsim_program_device_output_stats", "tsim_cut_num_params",
+              "tsim_program_device_table_layout", "tsim_program_device_output_stats", "tsim_selftest_sliced",
+              "tsim_cut_num_params",
               "tsim_cut_init_params",
               "tsim_cut_dataset", "tsim_cut_forward", "tsim_cut_loss_grad", "tsim_cut_adam_step", "tsim_cut_train",
               "tsim_cut_model_set", "tsim_cut_policy_stats"):
@@ -313,6 +315,11 @@ def tsim_program_device_output_stats(h):
     out = (ctypes.c_uint64 * 3)()
     _check(load_library().tsim_program_device_output_stats(h, out))
     return tuple(out)
+
+
+def tsim_selftest_sliced(h, seed=0, rounds=2):
+    """Host emulation of the program's bit-sliced tables against their exact values."""
+    _check(load_library().tsim_selftest_sliced(h, seed, rounds))
 
 
 def tsim_selftest_rules(seed=0, iterations=200):

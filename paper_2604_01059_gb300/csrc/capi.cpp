@@ -399,6 +399,13 @@ void tsim_program_free(tsim_program* prog) {
   delete prog;
 }
 
+tsim_status tsim_selftest_sliced(const tsim_program* prog, uint64_t seed, int rounds) {
+  return guard([&] {
+    if (rounds < 0) tsim::fail(TSIM_ERR_ARG, "negative rounds");
+    tsim::selftest_sliced(prog_of(prog), seed, rounds);
+  });
+}
+
 tsim_status tsim_selftest_rules(uint64_t seed, int iterations) {
   return guard([&] {
     std::mt19937_64 rng(seed);

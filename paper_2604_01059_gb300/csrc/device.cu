@@ -1880,6 +1880,118 @@ cudaError_t launch(const DevView& v, cudaStream_t s, uint64_t seed, uint64_t off
 
 }  // namespace
 
+// Host emulation of the warp-cooperative evaluation of a sliced table, read
+// from the packed tables exactly as the kernel reads them: 32 per-shot
+// vectors X at once (bit s of every word belongs to vector s).  Returns the
+// exact value of table t for each vector.
+std::vector<ZW> emulate_sliced_table(const Program& p, const DeviceTables& T, int t,
+                                     const std::vector<std::vector<uint64_t>>& xs) {
+  const DeviceLayout& L = T.layout;
+  const unsigned char* b = T.blob.data();
+  const DTable& tb = ((const DTable*)(b + L.o_tab))[t];
+  const DSeg* seg = (const DSeg*)(b + L.o_seg);
+  const DSBatch* sbv = (const DSBatch*)(b + L.o_sb);
+  const uint32_t* rows = (const uint32_t*)(b + L.o_row);
+  const uint64_t* par = (const uint64_t*)(b + L.o_par);
+  const int W = L.W;
+  std::vector<ZW> val(32);
+  std::vector<uint32_t> Xs((size_t)64 * W, 0);
+  for (int sh = 0; sh < 32; ++sh)
+    for (int i = 0; i < 64 * W; ++i)
+      if ((xs[(size_t)sh][(size_t)i >> 6] >> (i & 63)) & 1) Xs[(size_t)i] |= 1u << sh;
+  for (int g = 0; g < tb.n_sb; ++g) {
+    const DSeg& sg = seg[tb.sb_off + g];
+    std::vector<uint32_t> Par(sg.n_par, 0);
+    for (uint32_t q = 0; q < sg.n_par; ++q) {
+      uint32_t acc = 0;
+      for (int w = 0; w < W; ++w)
+        for (int bit = 0; bit < 64; ++bit)
+          if ((par[((size_t)sg.par_off + q) * W + (size_t)w] >> bit) & 1) acc ^= Xs[(size_t)(64 * w + bit)];
+      Par[q] = q == kSlOnes ? 0xFFFFFFFFu : acc;
+    }
+    auto word = [&](uint32_t off) {
+      if (off % 4 || off / 4 >= sg.n_par) fail(TSIM_ERR_INTERNAL, "sliced row outside its segment's parity words");
+      return Par[off / 4];
+    };
+    for (uint32_t bi = 0; bi < sg.n_sb; ++bi) {
+      const DSBatch& B = sbv[sg.sb_off + bi];
+      uint32_t J0[32], J1[32], J2[32], Z[32];
+      for (int l = 0; l < 32; ++l) {
+        J0[l] = 0u - ((B.j0m[0] >> l) & 1u);
+        J1[l] = 0u - ((B.j0m[1] >> l) & 1u);
+        J2[l] = 0u - ((B.j0m[2] >> l) & 1u);
+        Z[l] = 0u - ((~B.valid >> l) & 1u);
+      }
+      size_t at = B.row_off;
+      for (int c = 0; c < kSlCodes; ++c) {
+        const uint32_t n = B.cnt[c];
+        if (n % 4) fail(TSIM_ERR_INTERNAL, "sliced rows not in groups of 4");
+        for (uint32_t k = 0; k < n; ++k)
+          for (int l = 0; l < 32; ++l) {
+            const uint32_t r = rows[at + (size_t)(k / 4) * 128 + (size_t)l * 4 + (k % 4)];
+            const uint32_t a = c == SL_XOR4AB ? word(r & 0xFFFFu) & word(r >> 16) : word(r);
+            auto add = [&](uint32_t m, int times) {  // J += times * m (mod 8), one plane step at a time
+              for (int i = 0; i < times; ++i) {
+                const uint32_t c0 = J0[l] & m;
+                J0[l] ^= m;
+                const uint32_t c1 = J1[l] & c0;
+                J1[l] ^= c0;
+                J2[l] ^= c1;
+              }
+            };
+            switch (c) {
+              case SL_XOR4: case SL_XOR4AB: add(a, 4); break;
+              case SL_ADD2: add(a, 2); break;
+              case SL_ADD6: add(a, 6); break;
+              case SL_ADD1: add(a, 1); break;
+              case SL_ZERO: Z[l] |= a; break;
+              case SL_ZEROC: Z[l] |= ~a; break;
+            }
+          }
+        at += (size_t)n * 32;
+      }
+      for (int sh = 0; sh < 32; ++sh)
+        for (int l = 0; l < 32; ++l) {
+          if ((Z[l] >> sh) & 1) continue;
+          const int J = (int)((J0[l] >> sh) & 1) | (int)(((J1[l] >> sh) & 1) << 1) | (int)(((J2[l] >> sh) & 1) << 2);
+          ZW term = ZW::omega(J);
+          term.k = B.d + tb.base;
+          val[(size_t)sh] = zw_add(val[(size_t)sh], term);
+        }
+    }
+  }
+  return val;
+}
+
+void selftest_sliced(const Program& p, uint64_t seed, int rounds) {
+  const DeviceTables& T = tables_of(p);
+  const int W = T.layout.W;
+  uint64_t st = seed ^ 0x5EED5EEDull;
+  auto rnd = [&]() {
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  for (size_t t = 0; t < p.tables.size(); ++t) {
+    if (T.layout.table_mode[t] != TAB_SLICED) continue;
+    for (int r = 0; r < rounds; ++r) {
+      std::vector<std::vector<uint64_t>> xs(32, std::vector<uint64_t>((size_t)W, 0));
+      for (auto& x : xs)
+        for (int i = 0; i < p.nx; ++i)  // X bits beyond n_x stay zero, as on the device
+          if (rnd() & 1) x[(size_t)i >> 6] |= 1ull << (i & 63);
+      const std::vector<ZW> got = emulate_sliced_table(p, T, (int)t, xs);
+      for (int sh = 0; sh < 32; ++sh) {
+        ZW want = eval_table_host(p, (int)t, xs[(size_t)sh].data());
+        for (auto& c : want.c) c = -c;
+        if (!zw_add(got[(size_t)sh], want).zero())
+          fail(TSIM_ERR_INTERNAL, "sliced table " + std::to_string(t) + " differs from the exact evaluation");
+      }
+    }
+  }
+}
+
 void prepare_device_tables(Program& p, int64_t sliced_min, int stage_rows, int seg_par) {
   auto* t = new DeviceTables();
   try {

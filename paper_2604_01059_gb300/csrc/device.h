@@ -70,6 +70,10 @@ constexpr int kDefaultSegmentParities = 1536;
 // the default); seg_par: parity words per segment (<= 0: the default).
 void prepare_device_tables(Program& p, int64_t sliced_min = kDefaultSlicedMin, int stage_rows = -1,
                            int seg_par = 0);
+// Host emulation of every bit-sliced table of the packed program, 32 random
+// per-shot vectors X per round, compared exactly with the host evaluation of
+// the same table; fails with TSIM_ERR_INTERNAL on any difference.
+void selftest_sliced(const Program& p, uint64_t seed, int rounds);
 void device_sample(const Program& p, const SampleArgs& a, void* stream);
 void device_sample_batch(const Program* const* progs, int n, const SampleArgs* args, void* stream);
 

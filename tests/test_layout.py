@@ -84,3 +84,29 @@ def test_output_entries_account_for_every_output():
         entries, runs, covered = prog.device_output_stats()
         i = prog.info
         assert covered <= i["num_outputs"] and entries + covered - runs == i["num_outputs"]
+
+
+@pytest.mark.parametrize("seg", [16, 64, 1536])
+def test_sliced_tables_match_exact_values_small_programs(seg):
+    # a host emulation of the warp-cooperative kernel, reading the packed
+    # segments, batches and rows, equals each table's exact value from its
+    # term list on random per-shot vectors; tiny segments force many
+    # segments and parity renumberings per table
+    import random
+    from tests.test_compile_semantics import PHASED_CHAIN, STEANE_CHECK, _random_circuit
+    texts = [WORKED_EXAMPLE, STEANE_CHECK, PHASED_CHAIN, Wk.config1_circuit()]
+    for k in range(4):
+        texts.append(_random_circuit(random.Random(600 + k), 5, 30, tcount=8))
+    for text in texts:
+        for mode in (T.MODE_DETECTORS, T.MODE_MEASUREMENTS):
+            try:
+                prog = T.Program(text, mode=mode)
+            except T.TsimError:
+                continue
+            prog.set_table_layout(1, 0, seg)
+            T.tsim_selftest_sliced(prog.h, seed=seg, rounds=3)
+
+
+def test_sliced_tables_match_exact_values_color_code(color_code):
+    color_code.set_table_layout(4, 0, 1536)
+    T.tsim_selftest_sliced(color_code.h, seed=7, rounds=1)
