@@ -1,24 +1,30 @@
-// GB300 (sm_103a) per-shot sampling kernel.
+// GB300 (sm_103a) per-shot sampling kernels.
 //
-// One thread evaluates one shot end to end (Sec. "Complexity", paragraph
+// One thread carries one shot end to end (Sec. "Complexity", paragraph
 // "Sampling"):
 //   1. error mechanisms: one Philox4x32-10 word per reduced channel, outcome by
 //      integer threshold compare, X ^= column signature (Eq. detector_sampling);
 //   2. outputs in autoregressive order: deterministic outputs are GF(2)
 //      parities of X = (f, random outputs); random outputs follow Algorithm 1,
-//      every marginal P = sum_t c^t prod_k h(...) evaluated exactly:
-//        - the distinct factor parities of the table (Eq. parities) are
-//          computed once per shot by AND + popcount into a register bitmask,
-//        - terms with identical factor lists are merged ahead of time into one
-//          class whose coefficient is the exact Z[w] sum of their c^t,
-//        - per class each factor's two parity bits select one of four packed
-//          (zero, sqrt2-exponent, w-exponent) increments; the class value is
-//          C w^J sqrt2^S or 0 and is accumulated into four int64 coefficients
-//          of Z[w] (no floating point);
+//      every marginal P = sum_t c^t prod_k h(...) evaluated exactly, in one of
+//      two ways:
+//        - per thread: the distinct factor parities of the table (Eq.
+//          parities) are computed once per shot by AND + popcount; terms with
+//          identical factor lists are merged ahead of time into one class;
+//          per class each factor's two parity bits select one of four packed
+//          (zero, sqrt2-exponent, w-exponent) increments, and the class value
+//          C w^J sqrt2^S or 0 is accumulated into four int64 coefficients of
+//          Z[w] (no floating point);
+//        - per warp, bit-sliced (tables of Node, phase and pi-pair factors):
+//          the warp's 32 shots share every 32-bit word, lane l carries term l
+//          of a batch of 32, and each factor is one or two word operations on
+//          the term's phase exponent mod 8 and vanishing flag (below);
 //   3. the Bernoulli draw compares U * P_prev with 2^32 * P_1 exactly (int128);
-//   4. bit-packed records streamed from registers.
-// The program tables are read-only and identical for every thread of a warp,
-// so every table load is a uniform (broadcast) load.
+//   4. bit-packed records (runs of single-bit detectors copied by word shifts).
+// The program tables are read-only; per-thread table loads are uniform
+// (broadcast) loads, the bit-sliced rows are lane-coalesced 16-byte loads.
+// k_sample launches one program; k_batch runs persistent warps over the
+// (program, shot-block) work items of many programs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
