@@ -30,7 +30,9 @@
  *   - Output is a pure function of (program, seed, global shot index): the
  *     Philox4x32-10 counter of shot s is (s lo, s hi, stream, block) with key
  *     (seed lo, seed hi); stream 0 drives noise channel c (word c%4 of block
- *     c/4), stream 1 drives autoregressive output i (word i%4 of block i/4).
+ *     c/4) or, in geometric-gap noise sampling, stream 2 gives the noise
+ *     words in the order they are used (word j = word j%4 of block j/4);
+ *     stream 1 drives autoregressive output i (word i%4 of block i/4).
  */
 #ifndef TSIM_H
 #define TSIM_H
@@ -169,20 +171,72 @@ tsim_status tsim_sample_batch(const tsim_program* const* progs, int n, const uin
  * device tables, which tsim_sample keeps in memory it allocates once per
  * program, are packed into a fixed 4 MiB array in the library's device
  * memory (every GPU that loads the library holds it until the process exits)
- * and copied there on cuda_stream before the kernel runs.
- *   - Programs whose packed tables exceed 4 MiB are rejected with
- *     TSIM_ERR_ARG; tsim_sample has no such limit.
+ * and copied there on cuda_stream before the kernel runs.  The array's first
+ * 256 bytes hold the call's device status word; the tables follow.
+ *   - Programs whose packed tables exceed 4 MiB - 256 bytes are rejected with
+ *     TSIM_ERR_ARG before anything is written; tsim_sample has no such limit.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.
+ *     before any stream capture.  Every later call made outside a stream
+ *     capture looks the address up again, so a cudaDeviceReset of the device
+ *     (which moves the array) is followed by the next such call; a call being
+ *     captured uses the address of the last call outside capture.
  *   - Every call reuses the same array and rewrites all of it that the kernel
  *     reads.  Calls whose work overlaps on the GPU (different streams without
  *     ordering between them) race on the array and must not be issued; calls
  *     on one stream are ordered and safe.  Host threads are serialised.
- * Device-side errors are reported by tsim_sync, as for tsim_sample. */
+ * Device-side errors are reported by tsim_sync, as for tsim_sample (which
+ * clears the status word after reading it). */
 tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t shots, uint64_t seed,
                                 uint64_t shot_offset, uint64_t* d_meas, uint64_t* d_det,
                                 uint64_t* d_obs, uint8_t* d_accept, void* cuda_stream);
+
+/* Validation form of tsim_sample (Appendix "Validation": probabilities of bit
+ * strings; Eqs. parities, phase_pair, scalar_product): the same kernel, grid
+ * and records as tsim_sample, and in addition, for the n_dump shots whose
+ * indices within the launch are dump_shots[0..n_dump) (host array, distinct,
+ * each < shots), an exact copy of every marginal table the kernel evaluated
+ * for that shot.  h_dump (host, caller-owned) receives, per dumped shot in the
+ * order given, per evaluation (each chain's normalisation in chain order,
+ * then the table of each random output in output order: num_chains +
+ * num_random evaluations), 6 + x_words int64 values: the table index, the
+ * four Z[w] coefficients c0..c3 and the sqrt2 exponent k of the kernel's
+ * value (c0 + c1 w + c2 w^2 + c3 w^3) sqrt2^k, then the words of X at which
+ * the kernel evaluated it.  Allocates and frees device scratch, and
+ * synchronises cuda_stream.  At most 2^31 shots. */
+tsim_status tsim_debug_sample(const tsim_program* prog, uint64_t shots, uint64_t seed, uint64_t shot_offset,
+                              uint64_t* d_meas, uint64_t* d_det, uint64_t* d_obs, uint8_t* d_accept,
+                              const uint64_t* dump_shots, int n_dump, int64_t* h_dump, void* cuda_stream);
+
+/* How the error mechanisms of a shot are drawn (Sec. "Detectors"):
+ *   0  one Philox word per reduced channel (stream 0, word c of the shot);
+ *   1  geometric gaps: the channels are split into groups of channels whose
+ *      firing probabilities lie within a factor 2 of the group's largest,
+ *      1 - Q/2^32; candidates are Bernoulli(1 - Q/2^32) trials along a
+ *      group, each gap drawn from one word U as the largest k (up to the
+ *      channels left) with U < T_k, T_0 = 2^32, T_k = floor(T_{k-1} Q / 2^32);
+ *      a candidate's word V, mapped onto [Q, 2^32) by Q + floor(V (2^32 - Q)
+ *      / 2^32), picks its outcome by the channel's own thresholds.  All words
+ *      come from stream 2 in the order they are used.  Cost per shot: one
+ *      word per group plus two per candidate, against one word per channel.
+ *  -1  whichever of the two is expected to draw fewer words (the default at
+ *      compile and load time: a program file records the mode it was saved
+ *      with).
+ * Re-packs the device tables (keeping their layout settings); the records
+ * change with the mode (both sample the same distribution, within 2^-32 per
+ * channel and gap step).  Must not be called while a launch of the program
+ * is in flight or while a batch created from it exists. */
+tsim_status tsim_program_set_noise_sampling(tsim_program* prog, int mode);
+
+/* Bytes of the program's packed device tables (what tsim_sample uploads once
+ * per program and tsim_sample_noalloc copies on every call). */
+tsim_status tsim_program_device_bytes(const tsim_program* prog, uint64_t* bytes);
+
+/* out[0] = noise sampling mode (0 or 1), out[1] = groups (mode 1), out[2] =
+ * random words per shot of mode 0 (channels that can fire), out[3] = expected
+ * random words per shot of mode 1 (an upper bound: one per group plus two per
+ * expected candidate). */
+tsim_status tsim_program_noise_info(const tsim_program* prog, double out[4]);
 
 /* Reusable batched launch (Appendix "Additional benchmarks": batched sampling;
  * here heterogeneous programs share persistent kernels).  tsim_batch_create

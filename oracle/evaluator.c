@@ -36,6 +36,23 @@
  *     c%4 of block c/4; stream 1 feeds output i from word i%4 of block i/4.
  *   - channel outcome = smallest o < n-1 with U < thr[o], else n-1.
  *   - Bernoulli rule, exact: bit = 1  iff  U * P_prev < 2^32 * P_1.
+ *   - Geometric gaps (a program option; Sec. "Detectors" samples the gap
+ *     between successive firing events from a geometric distribution, which
+ *     takes O(p E) work instead of O(E)).  The channels are split into
+ *     groups; group g lists its channels in order and a 32-bit Q_g no larger
+ *     than the outcome-0 threshold of any member, so that every member fires
+ *     with probability at most r_g = 1 - Q_g / 2^32.  Candidates are placed
+ *     along the group as Bernoulli(r_g) trials: the number of non-candidates
+ *     before the next candidate is the gap, with P(gap >= k) = T_k / 2^32,
+ *     T_0 = 2^32 and T_k = floor(T_{k-1} Q_g / 2^32) (a geometric law with
+ *     ratio Q_g / 2^32, each step rounded down).  At a candidate channel c a
+ *     second word V is mapped onto [Q_g, 2^32) by V' = Q_g +
+ *     floor(V (2^32 - Q_g) / 2^32), and the channel's own threshold rule is
+ *     applied to V' (so the candidate is rejected, outcome 0, with
+ *     probability (thr_c[0] - Q_g) / (2^32 - Q_g)).  All words of a shot come
+ *     from stream 2, in the order they are used: word j is word j%4 of block
+ *     j/4; groups in program order; within a group, while channels remain, a
+ *     gap word, and when it places a candidate, that candidate's word V.
  *
  * Arithmetic: __int128 with every operation overflow-checked; an overflow or
  * a non-real marginal aborts the call with an error message rather than
@@ -223,6 +240,8 @@ typedef struct { int s0, j0, nf; factor* f; } term;
 typedef struct { int nt; term* t; } table;
 typedef struct { int is_random; uint64_t* mask; int cst; int xbit, chain, table; } output;
 typedef struct { int n_out; uint32_t* thr; uint64_t* sig; } channel;
+/* geometric-gap group: members in order, Q, and T_1..T_n (T[k], T[0] unused) */
+typedef struct { uint32_t Q; int n; int* member; uint32_t* T; } group;
 
 struct oracle_prog {
   int mode;  /* 0 detectors, 1 measurements */
@@ -230,6 +249,8 @@ struct oracle_prog {
   int n_out; output* out;
   int n_chains; int* chain_norm;
   int n_ch; channel* ch;
+  int noise_mode;  /* 0 one word per channel, 1 geometric gaps */
+  int n_groups; group* groups;
   int n_tab; table* tab;
   int n_detmap; int* detmap_n; int** detmap;
   int n_obsmap; int* obsmap_n; int** obsmap;
@@ -258,7 +279,7 @@ struct oracle_prog* oracle_load(const char* path) {
   struct oracle_prog* p = calloc(1, sizeof *p);
   char mode[32];
   int ver;
-  if (expect(f, "TSIMPROG") || fscanf(f, "%d", &ver) != 1 || ver != 1) goto bad;
+  if (expect(f, "TSIMPROG") || fscanf(f, "%d", &ver) != 1 || ver != 2) goto bad;
   if (expect(f, "mode") || fscanf(f, "%31s", mode) != 1) goto bad;
   p->mode = strcmp(mode, "measurements") == 0;
   if (expect(f, "nx") || fscanf(f, "%d", &p->nx) != 1) goto bad;
@@ -302,6 +323,41 @@ struct oracle_prog* oracle_load(const char* path) {
     ch->sig = calloc((size_t)ch->n_out * W, 8);
     for (int o = 0; o < ch->n_out; ++o)
       if (expect(f, "S") || read_hex_words(f, W, ch->sig + (size_t)o * W)) goto bad;
+  }
+  if (expect(f, "noise") || fscanf(f, "%d %d", &p->noise_mode, &p->n_groups) != 2) goto bad;
+  if (p->noise_mode < 0 || p->noise_mode > 1 || p->n_groups < 0) goto bad;
+  if (p->noise_mode == 0 && p->n_groups != 0) goto bad;
+  p->groups = calloc((size_t)p->n_groups + 1, sizeof(group));
+  {
+    /* every channel that can fire belongs to exactly one group */
+    int* seen = calloc((size_t)p->n_ch + 1, sizeof(int));
+    int okg = 1;
+    for (int g = 0; g < p->n_groups && okg; ++g) {
+      group* G = &p->groups[g];
+      unsigned long long q;
+      if (expect(f, "G") || fscanf(f, "%llu %d", &q, &G->n) != 2 || q > 0xFFFFFFFFull || G->n < 1) { okg = 0; break; }
+      G->Q = (uint32_t)q;
+      G->member = calloc((size_t)G->n, sizeof(int));
+      G->T = calloc((size_t)G->n + 1, sizeof(uint32_t));
+      for (int k = 0; k < G->n; ++k) {
+        int c;
+        if (fscanf(f, "%d", &c) != 1 || c < 0 || c >= p->n_ch || seen[c]) { okg = 0; break; }
+        seen[c] = 1;
+        /* Q_g must not exceed the member's outcome-0 threshold */
+        if (p->ch[c].n_out < 2 || p->ch[c].thr[0] < G->Q) { okg = 0; break; }
+        G->member[k] = c;
+      }
+      /* T_k = floor(T_{k-1} Q / 2^32), T_0 = 2^32 */
+      uint64_t t = (uint64_t)1 << 32;
+      for (int k = 1; okg && k <= G->n; ++k) {
+        t = (t * (uint64_t)G->Q) >> 32;
+        G->T[k] = (uint32_t)t;
+      }
+    }
+    for (int c = 0; okg && p->noise_mode == 1 && c < p->n_ch; ++c)
+      if (p->ch[c].n_out >= 2 && !seen[c]) okg = 0;
+    free(seen);
+    if (!okg) goto bad;
   }
   if (expect(f, "tables") || fscanf(f, "%d", &p->n_tab) != 1) goto bad;
   p->tab = calloc((size_t)p->n_tab + 1, sizeof(table));
@@ -364,6 +420,8 @@ void oracle_free(struct oracle_prog* p) {
   free(p->chain_norm);
   for (int c = 0; p->ch && c < p->n_ch; ++c) { free(p->ch[c].thr); free(p->ch[c].sig); }
   free(p->ch);
+  for (int g = 0; p->groups && g < p->n_groups; ++g) { free(p->groups[g].member); free(p->groups[g].T); }
+  free(p->groups);
   for (int ti = 0; p->tab && ti < p->n_tab; ++ti) {
     table* tb = &p->tab[ti];
     for (int t = 0; tb->t && t < tb->nt; ++t) {
@@ -383,7 +441,53 @@ int oracle_info(const struct oracle_prog* p, int64_t* out) {
   out[0] = p->mode; out[1] = p->nx; out[2] = p->W; out[3] = p->nf; out[4] = p->nr;
   out[5] = p->nmeas; out[6] = p->ndet; out[7] = p->nobs; out[8] = p->n_out;
   out[9] = p->n_chains; out[10] = p->n_ch; out[11] = p->n_tab;
+  out[12] = p->noise_mode; out[13] = p->n_groups;
   return 0;
+}
+
+/* outcome of a channel for the uniform word U: the smallest o < n-1 with
+ * U < thr[o], else n-1 */
+static int channel_outcome(const channel* ch, uint32_t U) {
+  for (int j = 0; j + 1 < ch->n_out; ++j)
+    if (U < ch->thr[j]) return j;
+  return ch->n_out - 1;
+}
+
+/* Geometric gap: the number of non-candidates before the next candidate
+ * among the m channels left in a group, i.e. the largest k <= m with
+ * U < T_k (T_0 = 2^32 always holds), T_k given for k = 1..m. */
+static int geo_gap(const uint32_t* T, int m, uint32_t U) {
+  int k = 0;
+  while (k < m && U < T[k + 1]) ++k;
+  return k;
+}
+
+/* a word V mapped onto [Q, 2^32): Q + floor(V (2^32 - Q) / 2^32) */
+static uint32_t geo_map(uint32_t Q, uint32_t V) {
+  uint64_t R = ((uint64_t)1 << 32) - Q;
+  return Q + (uint32_t)(((uint64_t)V * R) >> 32);
+}
+
+/* Exported for the pins: the gap for a group of m channels with the given Q
+ * (the table built as the reader builds it), and the outcome of a candidate
+ * channel with thresholds thr[0..n_out-2] for the word V. */
+int oracle_geo_gap(uint32_t Q, int m, uint32_t U) {
+  if (m < 0 || m > 1000000) return fail("bad group size");
+  uint32_t* T = calloc((size_t)m + 1, sizeof(uint32_t));
+  uint64_t t = (uint64_t)1 << 32;
+  for (int k = 1; k <= m; ++k) {
+    t = (t * (uint64_t)Q) >> 32;
+    T[k] = (uint32_t)t;
+  }
+  int g = geo_gap(T, m, U);
+  free(T);
+  return g;
+}
+
+int oracle_geo_pick(uint32_t Q, const uint32_t* thr, int n_out, uint32_t V) {
+  channel ch = {n_out, (uint32_t*)thr, NULL};
+  if (n_out < 2 || thr[0] < Q) return fail("Q above the outcome-0 threshold");
+  return channel_outcome(&ch, geo_map(Q, V));
 }
 
 /* parity of (mask & X) over W words: XOR of all selected bits, bit by bit */
@@ -469,19 +573,46 @@ static int chain_phase(const zw* z, int* rot) {
   return fail("normalisation has no positive real phase");
 }
 
+/* 1-2: error mechanisms and f = T e, into X (W words, zeroed first) */
+static void sample_noise(const struct oracle_prog* p, uint64_t seed, uint64_t shot, uint64_t* X) {
+  int W = p->W;
+  memset(X, 0, (size_t)W * 8);
+  if (p->noise_mode == 0) {
+    for (int c = 0; c < p->n_ch; ++c) {
+      const channel* ch = &p->ch[c];
+      uint32_t U = philox_word(seed, shot, 0, (uint32_t)c);
+      int o = channel_outcome(ch, U);
+      for (int w = 0; w < W; ++w) X[w] ^= ch->sig[(size_t)o * W + w];
+    }
+  } else {
+    uint32_t j = 0;  /* next word of stream 2 */
+    for (int g = 0; g < p->n_groups; ++g) {
+      const group* G = &p->groups[g];
+      int pos = 0;
+      while (pos < G->n) {
+        uint32_t U = philox_word(seed, shot, 2, j++);
+        pos += geo_gap(G->T, G->n - pos, U);
+        if (pos >= G->n) break;
+        const channel* ch = &p->ch[G->member[pos]];
+        uint32_t V = philox_word(seed, shot, 2, j++);
+        int o = channel_outcome(ch, geo_map(G->Q, V));
+        for (int w = 0; w < W; ++w) X[w] ^= ch->sig[(size_t)o * W + w];
+        pos += 1;
+      }
+    }
+  }
+}
+
+/* Exported for the parity tests: X = T e of one shot, before any output. */
+int oracle_noise_x(const struct oracle_prog* p, uint64_t seed, uint64_t shot, uint64_t* X) {
+  sample_noise(p, seed, shot, X);
+  return 0;
+}
+
 static int sample_shot(const struct oracle_prog* p, uint64_t seed, uint64_t shot, uint64_t* X,
                        uint8_t* bits, rv* pprev, int* rot) {
   int W = p->W;
-  memset(X, 0, (size_t)W * 8);
-  /* 1-2: error mechanisms and f = T e */
-  for (int c = 0; c < p->n_ch; ++c) {
-    const channel* ch = &p->ch[c];
-    uint32_t U = philox_word(seed, shot, 0, (uint32_t)c);
-    int o = ch->n_out - 1;
-    for (int j = 0; j + 1 < ch->n_out; ++j)
-      if (U < ch->thr[j]) { o = j; break; }
-    for (int w = 0; w < W; ++w) X[w] ^= ch->sig[(size_t)o * W + w];
-  }
+  sample_noise(p, seed, shot, X);
   /* Algorithm 1: P_prev <- P for every chain (phase removed) */
   for (int c = 0; c < p->n_chains; ++c) {
     zw z;

@@ -51,6 +51,11 @@ def lib():
                                     ctypes.c_void_p, ctypes.c_void_p]
         L.oracle_decide.argtypes = [ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                     ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+        L.oracle_noise_x.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
+                                     ctypes.POINTER(ctypes.c_uint64)]
+        L.oracle_geo_gap.argtypes = [ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32]
+        L.oracle_geo_pick.argtypes = [ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), ctypes.c_int,
+                                      ctypes.c_uint32]
     return _lib
 
 
@@ -60,6 +65,25 @@ def philox4x32_10(ctr, key):
     o = (ctypes.c_uint32 * 4)()
     lib().oracle_philox4x32_10(c, k, o)
     return tuple(o)
+
+
+def geo_gap(Q, m, U):
+    """Geometric gap of the noise rule: non-candidates before the next
+    candidate among m channels of a group with parameter Q, for the word U."""
+    r = lib().oracle_geo_gap(Q, m, U)
+    if r < 0:
+        raise RuntimeError(lib().oracle_last_error().decode())
+    return r
+
+
+def geo_pick(Q, thr, V):
+    """Outcome of a candidate channel with cumulative thresholds thr (n-1
+    values) in a group with parameter Q, for the word V."""
+    arr = (ctypes.c_uint32 * len(thr))(*thr)
+    r = lib().oracle_geo_pick(Q, arr, len(thr) + 1, V)
+    if r < 0:
+        raise RuntimeError(lib().oracle_last_error().decode())
+    return r
 
 
 def decide(U, Ap, Bp, ep, A1, B1, e1):
@@ -79,7 +103,8 @@ class OracleProgram:
         info = (ctypes.c_int64 * 16)()
         lib().oracle_info(self._h, info)
         (self.mode, self.nx, self.words, self.nf, self.nr, self.nmeas, self.ndet,
-         self.nobs, self.n_out, self.n_chains, self.n_channels, self.n_tables) = info[:12]
+         self.nobs, self.n_out, self.n_chains, self.n_channels, self.n_tables,
+         self.noise_mode, self.n_groups) = info[:14]
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -100,6 +125,12 @@ class OracleProgram:
             c.append((hi << 64) | lo)
         # evaluator stores value * sqrt2^k ; DOmega stores / sqrt2^k
         return DOmega(c, -k.value)
+
+    def noise_x(self, seed, shot):
+        """X = T e of one shot after its error mechanisms, before any output."""
+        X = (ctypes.c_uint64 * self.words)()
+        lib().oracle_noise_x(self._h, seed, shot, X)
+        return list(X)
 
     def sample(self, seed, shot_begin, n):
         wm = (self.nmeas + 63) // 64

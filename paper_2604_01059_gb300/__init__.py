@@ -20,7 +20,8 @@ __all__ = [
     "tsim_raw_to_x", "tsim_program_save", "tsim_program_load", "tsim_program_free",
     "tsim_last_error", "tsim_selftest_rules", "tsim_measure_int_peak", "tsim_program_device_table_stats",
     "tsim_program_set_table_layout", "tsim_program_device_table_layout", "tsim_program_device_output_stats",
-    "tsim_selftest_sliced", "load_library",
+    "tsim_selftest_sliced", "tsim_debug_sample", "tsim_program_set_noise_sampling", "tsim_program_noise_info",
+    "tsim_program_device_bytes", "load_library",
     "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T",
 ]
 
@@ -103,6 +104,11 @@ def load_library(path: str | None = None):
     L.tsim_program_device_table_layout.argtypes = [vp, i32, ctypes.POINTER(u64)]
     L.tsim_program_device_output_stats.argtypes = [vp, ctypes.POINTER(u64)]
     L.tsim_selftest_sliced.argtypes = [vp, u64, i32]
+    L.tsim_debug_sample.argtypes = [vp, u64, u64, u64, vp, vp, vp, vp, ctypes.POINTER(u64), i32,
+                                    ctypes.POINTER(i64), vp]
+    L.tsim_program_set_noise_sampling.argtypes = [vp, i32]
+    L.tsim_program_noise_info.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.tsim_program_device_bytes.argtypes = [vp, ctypes.POINTER(u64)]
     L.tsim_cut_num_params.argtypes = []
     L.tsim_cut_init_params.argtypes = [u64, vp]
     L.tsim_cut_dataset.argtypes = [u64, i32, i32, i32, u64, i32, ctypes.c_char_p]
@@ -118,6 +124,8 @@ def load_library(path: str | None = None):
               "tsim_program_save", "tsim_program_load", "tsim_selftest_rules", "tsim_measure_int_peak",
               "tsim_program_device_table_stats", "tsim_program_set_table_layout",
               "tsim_program_device_table_layout", "tsim_program_device_output_stats", "tsim_selftest_sliced",
+              "tsim_debug_sample", "tsim_program_set_noise_sampling", "tsim_program_noise_info",
+              "tsim_program_device_bytes",
               "tsim_cut_num_params",
               "tsim_cut_init_params",
               "tsim_cut_dataset", "tsim_cut_forward", "tsim_cut_loss_grad", "tsim_cut_adam_step", "tsim_cut_train",
@@ -182,6 +190,44 @@ def tsim_sample_noalloc(h, shots, seed, shot_offset=0, meas=None, det=None, obs=
     s = stream if isinstance(stream, (int, type(None))) else stream.cuda_stream
     _check(load_library().tsim_sample_noalloc(h, shots, seed, shot_offset, _ptr(meas), _ptr(det), _ptr(obs),
                                               _ptr(accept), s))
+
+
+def tsim_debug_sample(h, shots, seed, shot_offset, dump_shots, meas=None, det=None, obs=None, accept=None,
+                      stream=None):
+    """tsim_sample plus an exact copy of every table evaluation of the shots
+    dump_shots (indices within the launch).  Returns an int64 array
+    [len(dump_shots)][num_chains + num_random][6 + x_words]: table, c0..c3,
+    sqrt2 exponent, X words."""
+    import numpy as np
+    info = tsim_program_info(h)
+    evals = info["num_chains"] + info["num_random"]
+    n = len(dump_shots)
+    out = np.zeros((n, evals, 6 + info["x_words"]), dtype=np.int64)
+    ds = (ctypes.c_uint64 * max(n, 1))(*[int(v) for v in dump_shots])
+    s = stream if isinstance(stream, (int, type(None))) else stream.cuda_stream
+    _check(load_library().tsim_debug_sample(h, shots, seed, shot_offset, _ptr(meas), _ptr(det), _ptr(obs),
+                                            _ptr(accept), ds, n,
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), s))
+    return out
+
+
+def tsim_program_set_noise_sampling(h, mode):
+    """0: one Philox word per channel; 1: geometric gaps; -1: the cheaper one."""
+    _check(load_library().tsim_program_set_noise_sampling(h, int(mode)))
+
+
+def tsim_program_noise_info(h):
+    out = (ctypes.c_double * 4)()
+    _check(load_library().tsim_program_noise_info(h, out))
+    return {"mode": int(out[0]), "groups": int(out[1]), "words_per_channel_mode": out[2],
+            "words_geometric_mode": out[3]}
+
+
+def tsim_program_device_bytes(h):
+    """Bytes of the program's packed device tables."""
+    n = ctypes.c_uint64()
+    _check(load_library().tsim_program_device_bytes(h, ctypes.byref(n)))
+    return n.value
 
 
 def tsim_sample_host(h, shots, seed, shot_offset=0, meas=None, det=None, obs=None, accept=None, stream=None):
@@ -475,6 +521,16 @@ class Program:
     def set_table_layout(self, sliced_min_terms, stage_rows=-1, segment_parities=0):
         tsim_program_set_table_layout(self.h, sliced_min_terms, stage_rows, segment_parities)
         self.info = tsim_program_info(self.h)
+
+    def set_noise_sampling(self, mode):
+        tsim_program_set_noise_sampling(self.h, mode)
+        self.info = tsim_program_info(self.h)
+
+    def noise_info(self):
+        return tsim_program_noise_info(self.h)
+
+    def device_bytes(self):
+        return tsim_program_device_bytes(self.h)
 
     def device_table_layout(self, t):
         return tsim_program_device_table_layout(self.h, t)

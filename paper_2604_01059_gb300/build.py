@@ -35,7 +35,7 @@ def _stale(srcs):
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = srcs + [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith(".h")]
+    deps = srcs + [os.path.join(SRC, f) for f in os.listdir(SRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "tsim.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stdout, r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 1, 1), len(srcs))) as ex:
         objs = list(ex.map(one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", "-o", tmp, *objs, *ARCH, "-lcudart"]

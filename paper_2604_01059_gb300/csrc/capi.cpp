@@ -186,6 +186,82 @@ tsim_status tsim_sample(const tsim_program* prog, uint64_t shots, uint64_t seed,
   });
 }
 
+// For callers that cannot allocate device memory: same records as
+// tsim_sample, with the program's tables in the library's fixed static
+// device array (device.cu); errors come back as a status, as everywhere.
+tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t shots, uint64_t seed, uint64_t shot_offset,
+                                uint64_t* d_meas, uint64_t* d_det, uint64_t* d_obs, uint8_t* d_accept,
+                                void* cuda_stream) {
+  return guard([&] {
+    tsim::SampleArgs a;
+    a.shots = shots;
+    a.seed = seed;
+    a.shot_offset = shot_offset;
+    a.meas = d_meas;
+    a.det = d_det;
+    a.obs = d_obs;
+    a.accept = d_accept;
+    tsim::device_sample_noalloc(prog_of(prog), a, cuda_stream);
+  });
+}
+
+tsim_status tsim_debug_sample(const tsim_program* prog, uint64_t shots, uint64_t seed, uint64_t shot_offset,
+                              uint64_t* d_meas, uint64_t* d_det, uint64_t* d_obs, uint8_t* d_accept,
+                              const uint64_t* dump_shots, int n_dump, int64_t* h_dump, void* cuda_stream) {
+  return guard([&] {
+    tsim::SampleArgs a;
+    a.shots = shots;
+    a.seed = seed;
+    a.shot_offset = shot_offset;
+    a.meas = d_meas;
+    a.det = d_det;
+    a.obs = d_obs;
+    a.accept = d_accept;
+    tsim::device_sample_debug(prog_of(prog), a, dump_shots, n_dump, h_dump, cuda_stream);
+  });
+}
+
+tsim_status tsim_program_set_noise_sampling(tsim_program* prog, int mode) {
+  return guard([&] {
+    tsim::Program& p = const_cast<tsim::Program&>(prog_of(prog));
+    tsim::device_release(p.dev);  // the uploaded copy of the old layout
+    p.dev = nullptr;
+    // re-pack with the table layout the program already has
+    int64_t smin = tsim::kDefaultSlicedMin;
+    int stage = -1, seg = 0;
+    if (p.devtab) {
+      smin = p.devtab->sliced_min;
+      stage = p.devtab->stage_rows;
+      seg = p.devtab->seg_par;
+    }
+    tsim::set_noise_sampling(p, mode);
+    tsim::prepare_device_tables(p, smin, stage, seg);
+    if (p.devtab->status != TSIM_OK) tsim::fail(p.devtab->status, p.devtab->message);
+  });
+}
+
+tsim_status tsim_program_device_bytes(const tsim_program* prog, uint64_t* bytes) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!bytes) tsim::fail(TSIM_ERR_ARG, "NULL output");
+    if (!p.devtab || p.devtab->status != TSIM_OK) tsim::fail(TSIM_ERR_ARG, "program has no device tables");
+    *bytes = p.devtab->layout.total;
+  });
+}
+
+tsim_status tsim_program_noise_info(const tsim_program* prog, double out[4]) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!out) tsim::fail(TSIM_ERR_ARG, "NULL output array");
+    double est[2];
+    tsim::noise_word_estimate(p, est);
+    out[0] = p.noise_mode;
+    out[1] = (double)p.groups.size();
+    out[2] = est[0];
+    out[3] = est[1];
+  });
+}
+
 tsim_status tsim_sample_host(const tsim_program* prog, uint64_t shots, uint64_t seed, uint64_t shot_offset,
                              uint64_t* h_meas, uint64_t* h_det, uint64_t* h_obs, uint8_t* h_accept,
                              void* cuda_stream) {

@@ -864,8 +864,67 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
     }
     P.channels.push_back(std::move(pc));
   }
+  set_noise_sampling(P, -1);
   prepare_device_tables(P);
   return prog.release();
+}
+
+namespace {
+
+// Groups for the geometric-gap noise rule: channels sorted by their
+// probability of firing (2^32 - thr[0], in units of 2^-32), largest first;
+// a group starts at the most likely channel left and takes every further
+// channel at least half as likely, so a candidate is accepted with
+// probability >= 1/2.  Q is the leader's outcome-0 threshold; members keep
+// program order.  Channels that cannot fire (one outcome) join no group.
+std::vector<NoiseGroup> noise_groups(const Program& p) {
+  std::vector<int> order;
+  for (size_t c = 0; c < p.channels.size(); ++c)
+    if (!p.channels[c].thr.empty()) order.push_back((int)c);
+  auto fire = [&](int c) { return (uint64_t(1) << 32) - p.channels[(size_t)c].thr[0]; };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return fire(a) > fire(b); });
+  std::vector<NoiseGroup> out;
+  for (size_t i = 0; i < order.size();) {
+    const uint64_t lead = fire(order[i]);
+    NoiseGroup g;
+    g.Q = p.channels[(size_t)order[i]].thr[0];
+    size_t j = i;
+    while (j < order.size() && 2 * fire(order[j]) >= lead) g.member.push_back(order[j++]);
+    std::sort(g.member.begin(), g.member.end());
+    out.push_back(std::move(g));
+    i = j;
+  }
+  return out;
+}
+
+double geometric_words(const std::vector<NoiseGroup>& gs) {
+  // per group one gap word, and per candidate its word and the next gap word
+  double w = 0;
+  for (const NoiseGroup& g : gs) w += 1.0 + 2.0 * (double)g.member.size() * (4294967296.0 - g.Q) / 4294967296.0;
+  return w;
+}
+
+}  // namespace
+
+void noise_word_estimate(const Program& p, double out[2]) {
+  double pc = 0;
+  for (const ProgChannel& c : p.channels) pc += c.thr.empty() ? 0.0 : 1.0;
+  out[0] = pc;
+  out[1] = geometric_words(noise_groups(p));
+}
+
+void set_noise_sampling(Program& p, int mode) {
+  if (mode < -1 || mode > 1) fail(TSIM_ERR_ARG, "noise sampling mode must be -1, 0 or 1");
+  std::vector<NoiseGroup> gs = noise_groups(p);
+  if (mode < 0) {
+    double est[2];
+    noise_word_estimate(p, est);
+    // a geometric word costs about twice a per-channel word (the gap search
+    // and the serial dependence between words)
+    mode = (!gs.empty() && 2.0 * est[1] < est[0]) ? 1 : 0;
+  }
+  p.noise_mode = mode;
+  p.groups = mode ? std::move(gs) : std::vector<NoiseGroup>();
 }
 
 ZW eval_table_host(const Program& p, int t, const uint64_t* x) {

@@ -1,30 +1,9 @@
-// GB300 (sm_103a) per-shot sampling kernels.
-//
-// One thread carries one shot end to end (Sec. "Complexity", paragraph
-// "Sampling"):
-//   1. error mechanisms: one Philox4x32-10 word per reduced channel, outcome by
-//      integer threshold compare, X ^= column signature (Eq. detector_sampling);
-//   2. outputs in autoregressive order: deterministic outputs are GF(2)
-//      parities of X = (f, random outputs); random outputs follow Algorithm 1,
-//      every marginal P = sum_t c^t prod_k h(...) evaluated exactly, in one of
-//      two ways:
-//        - per thread: the distinct factor parities of the table (Eq.
-//          parities) are computed once per shot by AND + popcount; terms with
-//          identical factor lists are merged ahead of time into one class;
-//          per class each factor's two parity bits select one of four packed
-//          (zero, sqrt2-exponent, w-exponent) increments, and the class value
-//          C w^J sqrt2^S or 0 is accumulated into four int64 coefficients of
-//          Z[w] (no floating point);
-//        - per warp, bit-sliced (tables of Node, phase and pi-pair factors):
-//          the warp's 32 shots share every 32-bit word, lane l carries term l
-//          of a batch of 32, and each factor is one or two word operations on
-//          the term's phase exponent mod 8 and vanishing flag (below);
-//   3. the Bernoulli draw compares U * P_prev with 2^32 * P_1 exactly (int128);
-//   4. bit-packed records (runs of single-bit detectors copied by word shifts).
-// The program tables are read-only; per-thread table loads are uniform
-// (broadcast) loads, the bit-sliced rows are lane-coalesced 16-byte loads.
-// k_sample launches one program; k_batch runs persistent warps over the
-// (program, shot-block) work items of many programs.
+// Host side of the GB300 sampler: packing a compiled program into one
+// read-only device blob (channels, noise groups, outputs, marginal tables in
+// their device layouts), uploading it, the per-device status word, batch
+// plans (persistent launches, autotuning, CUDA graphs), the debug dump of
+// table values, and sampling without device allocation.  The kernels live in
+// kernels.cuh, instantiated per X width in kern_w*.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +17,7 @@
 #include <unordered_map>
 
 #include "device.h"
+#include "devtypes.h"
 #include "zx.h"
 
 namespace tsim {
@@ -48,86 +28,51 @@ namespace tsim {
     if (e_ != cudaSuccess) fail(TSIM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
-enum : int { ST_NOT_REAL = 1, ST_OVERFLOW = 2, ST_ZERO_PROB = 4, ST_TIMEOUT = 8 };
+namespace {
 
-// device-wide status word: bits of the conditions above, read by tsim_sync
-__device__ int g_status;
+constexpr int kMaxDevices = 64;
 
-constexpr int kMaxChains = 16;
-constexpr int kMaxOutWords = 64;  // measurement mode: 4096 outputs
-constexpr int kMaxParities = 256;
-constexpr int kThreads = 128;
+// Status word of each device (bits ST_*), allocated on the first upload to
+// that device and read (then cleared) by tsim_sync.
+std::mutex g_status_mu;
+int* g_status_dev[kMaxDevices];
 
-// Output entries, in autoregressive order.  rec is the output index (its
-// record bit); a run (detector mode) covers outputs rec .. rec + chain - 1,
-// which are X bits a .. a + chain - 1 with no constant, in one record.
-enum : int { OUT_MASK = 0, OUT_BIT = 1, OUT_RANDOM = 2, OUT_RUN = 3 };
+int* status_word(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) fail(TSIM_ERR_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_status_mu);
+  if (!g_status_dev[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, 256);
+    if (e != cudaSuccess) fail(TSIM_ERR_OOM, std::string("cudaMalloc of the status word: ") + cudaGetErrorString(e));
+    e = cudaMemset(p, 0, 256);
+    if (e != cudaSuccess) {
+      cudaFree(p);
+      fail(TSIM_ERR_CUDA, std::string("cudaMemset of the status word: ") + cudaGetErrorString(e));
+    }
+    g_status_dev[dev] = (int*)p;
+  }
+  return g_status_dev[dev];
+}
 
-struct DChan { uint32_t n_out, thr_off, sig_off, thr0; };
-struct DOut { int32_t kind, cst, a, chain, table, rec; };
-// Table layouts: SCALAR = distinct parities indexed per factor (one thread
-// per shot), BASIS = parities as coordinates in a GF(2) basis of their span,
-// SLICED = warp-cooperative bit-sliced evaluation (below).
-enum : int { TAB_SCALAR = 0, TAB_BASIS = 1, TAB_SLICED = 2 };
-struct DTable { uint32_t par_off, n_par, cls_off, n_cls; int32_t base, mode, sb_off, n_sb, stage, pad[3]; };
-struct DClass { uint32_t fac_off, n_fac; int32_t mono, j0, d0, pad; long long c[4]; };
+// ---- sampling without device allocation.  Some callers cannot call
+// cudaMalloc: code running inside a memory pool or allocator it does not
+// own, real-time loops that must not touch the driver's allocator, or hosts
+// whose device memory is carved up ahead of time.  For them the program's
+// device tables -- the scratch that tsim_sample allocates once per program --
+// and a status word live in the fixed array below (kNoAllocBytes, 4 MiB;
+// every GPU that loads the library holds it until the process exits): the
+// status word in its first kNoAllocHead bytes, the tables after it.
+constexpr size_t kNoAllocBytes = (size_t)4 << 20;
+constexpr size_t kNoAllocHead = 256;
 
-// Bit-sliced tables.  A warp evaluates 32 shots at once: bit s of every
-// 32-bit word below belongs to shot (lane) s.  Per table the warp forms the
-// words Par[q] of all distinct factor parities q (Eq. parities), then walks
-// the terms in batches of 32, lane l carrying term l of the batch.  Every
-// factor of a Clifford term whose value is a monomial of fixed magnitude
-// reduces to operations on the term's phase exponent J (mod 8, three bit
-// planes J0 J1 J2) and vanishing flag Z:
-enum : int {
-  SL_XOR4 = 0,   // J += 4a          (a sign (-1)^a)
-  SL_ADD2 = 1,   // J += 2a          (i^a)
-  SL_ADD6 = 2,   // J += 6a          ((-i)^a)
-  SL_XOR4AB = 3, // J += 4ab         (pi-pair (-1)^(ab)); row = qa | qb << 16
-  SL_ZERO = 4,   // vanishes if a = 1 (Node 1 + (-1)^a)
-  SL_ZEROC = 5,  // vanishes if a = 0 (Node 1 - (-1)^a)
-  SL_ADD1 = 6,   // J += a           (w^a, odd phase)
-  kSlCodes = 7
-};
-constexpr uint32_t kSlOnes = 1;        // parity index whose word is all ones
-constexpr int kSlMaxPar = 16384;       // parity words of one segment (4q fits 16 bits)
-// One batch of 32 terms: rows of operation code c are cnt[c] (a multiple of
-// 4) x 32 parity offsets, padded with no-op offsets and stored in groups of 4
-// rows as [group][lane][4], starting at row_off.
-// All terms of a batch share the magnitude sqrt2^d; j0m[b] holds bit b of
-// each lane's constant phase; valid marks lanes that carry a term.
-struct DSBatch { uint32_t row_off; uint16_t cnt[8]; int32_t d; uint32_t j0m[3]; uint32_t valid; };
-// A sliced table is a list of segments: consecutive terms whose distinct
-// parities (par_off, n_par masks) fit one shared buffer, and their batches.
-struct DSeg { uint32_t par_off, n_par, sb_off, n_sb; };
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-struct DevView {
-  int W;
-  int n_ch, n_out, n_ent, n_chains, n_tab;
-  int nmeas, ndet, nobs, mode;
-  const DChan* ch;
-  const uint4* thr0;      // outcome-0 threshold per channel, 4 per block, padded with 2^32-1
-  const uint32_t* thr;
-  const uint64_t* sig;
-  const DOut* out;
-  const uint64_t* omask;
-  const int32_t* chain_norm;
-  const DTable* tab;
-  const uint64_t* par;    // per table: n_par masks of W words (mask 0 = zero)
-  const DClass* cls;
-  const uint32_t* fidx;   // per factor: parity index of a | parity index of b << 8
-  const uint32_t* finc;   // per factor: 4 packed increments
-  const uint64_t* fcoord; // basis tables: per factor the coordinates of a and b (2 words)
-  const DSeg* seg;        // sliced tables: segments
-  const DSBatch* sb;      // sliced tables: batches
-  const uint32_t* rows;   // sliced tables: operation rows
-  int sl_par;             // shared words for parity words per warp (0: no sliced table)
-  int sl_rb;              // shared words of one row staging buffer (0: no staging)
-  const int32_t* dmap_off;
-  const int32_t* dmap_idx;
-  const int32_t* omap_off;
-  const int32_t* omap_idx;
-};
+std::mutex g_noalloc_mutex;
+// device address of g_noalloc_scratch per device, from cudaGetSymbolAddress
+// (the host-side name of the array is not a device address)
+void* g_noalloc_dev[kMaxDevices];
+
+}  // namespace
 
 struct DeviceProgram {
   DevView v{};
@@ -178,862 +123,6 @@ bool monomial_of(const ZW& v, int* zero, int* s, int* j) {
     }
   }
   return false;
-}
-
-// ------------------------------------------------------------------ Philox
-// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 products;
-// the round keys (key + r * Weyl constants) are the same for every call.
-struct RoundKeys {
-  uint32_t k0[10], k1[10];
-};
-
-// the round keys of key (seed lo, seed hi): key + r * (0x9E3779B9, 0xBB67AE85)
-__host__ __device__ __forceinline__ RoundKeys round_keys(uint64_t seed) {
-  RoundKeys rk;
-  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    rk.k0[r] = k0;
-    rk.k1[r] = k1;
-    k0 += 0x9E3779B9u;
-    k1 += 0xBB67AE85u;
-  }
-  return rk;
-}
-
-__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                              const RoundKeys& rk, uint32_t o[4]) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-    c0 = hi1 ^ c1 ^ rk.k0[r];
-    c1 = lo1;
-    c2 = hi0 ^ c3 ^ rk.k1[r];
-    c3 = lo0;
-  }
-  o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
-}
-
-// ------------------------------------------------------- exact real values
-struct RV {
-  __int128 A, B;  // value = (A + B sqrt2) * 2^e
-  int e;
-};
-
-__device__ __forceinline__ __int128 shl_chk(__int128 x, int s, int* st) {
-  if (s <= 0) return x;
-  __int128 ax = x < 0 ? -x : x;
-  if (s >= 126 || (ax >> (126 - s)) != 0) { *st |= ST_OVERFLOW; return 0; }
-  return x * ((__int128)1 << s);
-}
-
-__device__ __forceinline__ int sign_xy(__int128 X, __int128 Y, int* st) {
-  if (X >= 0 && Y >= 0) return (X == 0 && Y == 0) ? 0 : 1;
-  if (X <= 0 && Y <= 0) return -1;
-  unsigned __int128 ax = X < 0 ? (unsigned __int128)(-X) : (unsigned __int128)X;
-  unsigned __int128 ay = Y < 0 ? (unsigned __int128)(-Y) : (unsigned __int128)Y;
-  if ((ax >> 63) || (ay >> 63)) { *st |= ST_OVERFLOW; return 0; }
-  unsigned __int128 x2 = ax * ax, y2 = 2 * ay * ay;
-  if (X > 0) return x2 > y2 ? 1 : -1;
-  return y2 > x2 ? 1 : -1;
-}
-
-// coefficient k (0..7) of w^k in Z[w] basis {1, w, w^2, w^3}: w^k = +-w^(k mod 4)
-__device__ __forceinline__ long long pick(const long long c[4], int k) {
-  k &= 7;
-  const int q = k & 3;
-  const long long v = q == 0 ? c[0] : (q == 1 ? c[1] : (q == 2 ? c[2] : c[3]));
-  return k < 4 ? v : -v;
-}
-
-// parity of (mask & X); masks are stored with ws words (ws <= W, the rest of X
-// is zero for such a program)
-template <int W>
-__device__ __forceinline__ int parity_w(const uint64_t* m, const uint64_t (&X)[W], int ws) {
-  uint64_t acc = 0;
-#pragma unroll
-  for (int w = 0; w < W; ++w)
-    if (w < ws) acc ^= __ldg(m + w) & X[w];
-  return __popcll(acc) & 1;
-}
-
-// exact table value (c0 + c1 w + c2 w^2 + c3 w^3) sqrt2^base
-struct ZC {
-  long long c[4];
-  int base;
-};
-
-// real part of w^-rot (c0 + c1 w + c2 w^2 + c3 w^3) sqrt2^base as
-// (A + B sqrt2) 2^e:  Re = (2 c0 + (c1 - c3) sqrt2) / 2.  A chain's tables
-// share one parameter-dependent phase w^rot (the discarded scalars that the
-// normalisation P restores, Sec. "Observables"); rotating it away leaves the
-// real marginal.
-__device__ __forceinline__ RV to_real_rot(const ZC& z, int rot, int* st) {
-  long long c[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) c[i] = pick(z.c, i + rot);
-  const int base = z.base;
-  if (c[2] != 0 || c[1] + c[3] != 0) *st |= ST_NOT_REAL;
-  RV r;
-  r.A = (__int128)2 * c[0];
-  r.B = (__int128)c[1] - c[3];
-  int K = base - 2;
-  if (K & 1) {
-    const __int128 t2 = r.A;
-    r.A = 2 * r.B;
-    r.B = t2;
-    K -= 1;
-  }
-  r.e = K / 2;
-  return r;
-}
-
-// value w^J sqrt2^d C of one merged term, added into the four Z[w] coefficients
-__device__ __forceinline__ void accumulate(const DClass& C, uint32_t acc, long long (&c)[4]) {
-  const int J = (C.j0 + (int)(acc & 0x7FF)) & 7;
-  const int d = C.d0 + (int)((acc >> 11) & 0x3FF);
-  const int sh = d >> 1;
-  if (C.mono) {
-    const long long mag = 1ll << sh;
-    if (d & 1) {  // sqrt2 w^J = w^(J+1) - w^(J+3)
-      const int a = (J + 1) & 7, b = (J + 3) & 7;
-      c[a & 3] += (a < 4) ? mag : -mag;
-      c[b & 3] -= (b < 4) ? mag : -mag;
-    } else {
-      c[J & 3] += (J < 4) ? mag : -mag;
-    }
-  } else {
-    // w^J C: coefficient i takes C's coefficient of w^(i - J)
-    long long r[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) r[i] = pick(C.c, i - J + 8);
-    if (d & 1) {  // times sqrt2 = w - w^3
-      const long long t0 = r[1] - r[3], t1 = r[0] + r[2], t2 = r[1] + r[3], t3 = r[2] - r[0];
-      r[0] = t0; r[1] = t1; r[2] = t2; r[3] = t3;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) c[i] += r[i] * (1ll << sh);
-  }
-}
-
-// ---- shared-memory staging of operation rows (bulk copies through the
-// tensor memory accelerator, completion tracked by an mbarrier per buffer)
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint32_t lds(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-  return v;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// one elected lane: expect `bytes` on the barrier and start the bulk copy
-// (global source and shared destination 16-byte aligned, bytes a multiple of 16)
-// (no copy for 0 bytes: the arrival alone completes the phase)
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-  if (bytes)
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Warp-uniform bounded wait for the phase of the given parity; false when it
-// did not complete within the limit (the caller reports ST_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
-    if (__all_sync(0xFFFFFFFFu, mbar_test(bar, parity))) return true;
-  return false;
-}
-
-// A warp's shared words for sliced tables: transposed X (64 W), parity words
-// (par), two row staging buffers (rb each), two mbarriers and a state word
-// (bit 0 / 1: next phase parity of buffer 0 / 1; bit 2: staging failed).
-struct SlSmem {
-  uint32_t xs, par, rb0, rb1, bar0, bar1, state;
-  int rb;
-};
-
-__host__ __device__ __forceinline__ int sl_round32(int x) { return (x + 31) & ~31; }
-
-__host__ __device__ __forceinline__ int sl_warp_words(int W, int par, int rb) {
-  if (par <= 0) return 0;
-  return sl_round32(64 * W + par) + (rb > 0 ? 2 * rb + 32 : 0);
-}
-
-__device__ __forceinline__ SlSmem sl_smem(uint32_t* warp_base, int W, int par, int rb) {
-  SlSmem m;
-  const uint32_t b = smem_u32(warp_base);
-  m.xs = b;
-  m.par = b + 4u * (uint32_t)(64 * W);
-  const uint32_t st = b + 4u * (uint32_t)sl_round32(64 * W + par);
-  m.rb0 = st;
-  m.rb1 = st + 4u * (uint32_t)rb;
-  m.bar0 = st + 8u * (uint32_t)rb;
-  m.bar1 = m.bar0 + 8;
-  m.state = m.bar0 + 16;
-  m.rb = rb;
-  return m;
-}
-
-// once per warp at kernel start, when rows are staged
-__device__ __forceinline__ void sl_init(const SlSmem& m) {
-  if (m.rb > 0) {
-    if ((threadIdx.x & 31) == 0) {
-      mbar_init(m.bar0, 1);
-      mbar_init(m.bar1, 1);
-      asm volatile("st.shared.u32 [%0], %1;" ::"r"(m.state), "r"(0u) : "memory");
-      fence_mbar_init();
-    }
-    __syncwarp();
-  }
-}
-
-// 32 x 32 bit-matrix transpose across the warp: on entry lane r holds row r
-// (bit c = column c), on exit lane c holds column c (bit r = row r).  Stage j
-// (16, 8, 4, 2, 1) swaps the off-diagonal j x j blocks between lanes r and
-// r ^ j: each lane sends the half its partner keeps, and rotates what it
-// receives into place (left by j in the lower lane, right by j in the upper
-// one; the received bits never wrap).
-struct Transposer {
-  uint32_t mk[5];   // the bits a lane keeps at each stage
-  uint32_t rot[5];  // left-rotation of the received bits
-  __device__ __forceinline__ explicit Transposer(int lane) {
-    const uint32_t keep[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int st = 0; st < 5; ++st) {
-      const int j = 16 >> st;
-      const bool upper = (lane & j) != 0;
-      mk[st] = upper ? ~keep[st] : keep[st];
-      rot[st] = upper ? 32u - (uint32_t)j : (uint32_t)j;
-    }
-  }
-  __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
-#pragma unroll
-    for (int st = 0; st < 5; ++st) {
-      const uint32_t recv = __shfl_xor_sync(0xFFFFFFFFu, x & ~mk[st], 16 >> st);
-      x = (x & mk[st]) | __funnelshift_l(recv, recv, rot[st]);
-    }
-    return x;
-  }
-};
-
-// Operation rows read from global memory (through L1) or from a shared
-// staging buffer.  A row holds the byte offset of a parity word (4q), or two
-// of them (4qa | 4qb << 16) for pi-pairs.  Rows come in groups of 4: group g
-// of a code is 32 lanes x 4 consecutive rows, so one 16-byte load per lane
-// fetches 4 rows and a warp's load is 512 contiguous bytes.
-struct RowsG {
-  const uint4* p;  // this lane's current group
-  __device__ __forceinline__ uint4 get4(int g) const { return __ldg(p + 32 * g); }
-  __device__ __forceinline__ void adv4(int k) { p += 32 * k; }
-};
-struct RowsS {
-  uint32_t a;  // shared address of this lane's current group
-  __device__ __forceinline__ uint4 get4(int g) const {
-    uint4 v;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "r"(a + 512u * (uint32_t)g));
-    return v;
-  }
-  __device__ __forceinline__ void adv4(int k) { a += 512u * (uint32_t)k; }
-};
-
-// The n rows (a multiple of 4) of one operation code, in chunks whose row
-// loads and parity loads are all issued before the updates; f(way, a, b)
-// spreads consecutive rows over 4 independent accumulators (way = row & 3)
-// so that the update chains overlap.
-template <bool PAIR, class Rows, class F>
-__device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
-  int k = 0;
-  for (; k + 16 <= n; k += 16, R.adv4(4)) {
-    uint32_t r[16], a[16], b[16];
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      const uint4 v = R.get4(g);
-      r[4 * g] = v.x;
-      r[4 * g + 1] = v.y;
-      r[4 * g + 2] = v.z;
-      r[4 * g + 3] = v.w;
-    }
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      a[i] = lds(par + (PAIR ? (r[i] & 0xFFFFu) : r[i]));
-      b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
-    }
-#pragma unroll
-    for (int i = 0; i < 16; ++i) f(i & 3, a[i], b[i]);
-  }
-  for (; k < n; k += 4, R.adv4(1)) {
-    const uint4 v = R.get4(0);
-    const uint32_t r[4] = {v.x, v.y, v.z, v.w};
-    uint32_t a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      a[i] = lds(par + (PAIR ? (r[i] & 0xFFFFu) : r[i]));
-      b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) f(i, a[i], b[i]);
-  }
-}
-
-// (x1, x2) += (y1, y2) for 2-bit bit-sliced counters mod 4
-__device__ __forceinline__ void add2bit(uint32_t& x1, uint32_t& x2, uint32_t y1, uint32_t y2) {
-  x2 ^= y2 ^ (x1 & y1);
-  x1 ^= y1;
-}
-
-// All operation rows of one batch; returns the planes (J0, J1, J2, Z).
-template <class Rows>
-__device__ __forceinline__ void sl_batch(const DSBatch& B, Rows R, uint32_t par, int lane, uint32_t& J0, uint32_t& J1,
-                                         uint32_t& J2, uint32_t& Z) {
-  J0 = 0u - ((B.j0m[0] >> lane) & 1u);
-  J1 = 0u - ((B.j0m[1] >> lane) & 1u);
-  J2 = 0u - ((B.j0m[2] >> lane) & 1u);
-  Z = 0u - ((~B.valid >> lane) & 1u);
-  // per way: J2 flips k, vanishing flags z, and a 2-bit counter (c1, c2) of
-  // the rows that add 2 to J (J2 flips and vanishing flags commute with it)
-  uint32_t k[4] = {0, 0, 0, 0}, z[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0}, c2[4] = {0, 0, 0, 0};
-  sl_loop<false>(B.cnt[SL_XOR4], R, par, [&](int w, uint32_t a, uint32_t) { k[w] ^= a; });
-  sl_loop<false>(B.cnt[SL_ADD2], R, par, [&](int w, uint32_t a, uint32_t) {
-    c2[w] ^= c1[w] & a;
-    c1[w] ^= a;
-  });
-  // J += 6a = 2a + 4a
-  sl_loop<false>(B.cnt[SL_ADD6], R, par, [&](int w, uint32_t a, uint32_t) {
-    c2[w] ^= c1[w] & a;
-    c1[w] ^= a;
-    k[w] ^= a;
-  });
-  sl_loop<true>(B.cnt[SL_XOR4AB], R, par, [&](int w, uint32_t a, uint32_t b) { k[w] ^= a & b; });
-  sl_loop<false>(B.cnt[SL_ZERO], R, par, [&](int w, uint32_t a, uint32_t) { z[w] |= a; });
-  sl_loop<false>(B.cnt[SL_ZEROC], R, par, [&](int w, uint32_t a, uint32_t) { z[w] |= ~a; });
-  add2bit(c1[0], c2[0], c1[1], c2[1]);
-  add2bit(c1[2], c2[2], c1[3], c2[3]);
-  add2bit(c1[0], c2[0], c1[2], c2[2]);
-  add2bit(J1, J2, c1[0], c2[0]);
-  J2 ^= (k[0] ^ k[1]) ^ (k[2] ^ k[3]);
-  Z |= (z[0] | z[1]) | (z[2] | z[3]);
-  // J += a (odd phases; rare): a three-plane increment
-  sl_loop<false>(B.cnt[SL_ADD1], R, par, [&](int, uint32_t a, uint32_t) {
-    const uint32_t cy = J0 & a;
-    J0 ^= a;
-    J2 ^= J1 & cy;
-    J1 ^= cy;
-  });
-}
-
-__device__ __forceinline__ uint32_t sl_batch_rows(const DSBatch& B) {
-  uint32_t n = 0;
-#pragma unroll
-  for (int c = 0; c < kSlCodes; ++c) n += B.cnt[c];
-  return n;
-}
-
-// Warp-cooperative exact value of a sliced table for the 32 shots of the
-// warp (every lane must call it; lane s receives shot s's value).
-template <int W>
-__device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64_t (&X)[W], const SlSmem& S) {
-  const int lane = threadIdx.x & 31;
-  const Transposer transpose32(lane);
-  __syncwarp();
-  uint32_t state = S.rb > 0 ? lds(S.state) : 4u;
-  const bool staged = tb.stage && !(state & 4u);
-#pragma unroll
-  for (int w = 0; w < W; ++w) {
-    const uint32_t lo = transpose32((uint32_t)X[w]), hi = transpose32((uint32_t)(X[w] >> 32));
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)(64 * w + lane)), "r"(lo) : "memory");
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)(64 * w + 32 + lane)), "r"(hi) : "memory");
-  }
-  ZC z{{0, 0, 0, 0}, tb.base};
-  long long (&c)[4] = z.c;
-  bool ok = true;
-  // signed counts of the batches since the magnitude sqrt2^d last changed
-  // (batches are sorted by d within a segment; |n| <= 32 per batch)
-  int n[4] = {0, 0, 0, 0};
-  int d_cur = 0;
-  auto flush = [&]() {
-    const int sh = d_cur >> 1;
-    long long r[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      r[q] = (long long)n[q] << sh;
-      n[q] = 0;
-    }
-    if (d_cur & 1) {  // times sqrt2 = w - w^3
-      c[0] += r[1] - r[3];
-      c[1] += r[0] + r[2];
-      c[2] += r[1] + r[3];
-      c[3] += r[2] - r[0];
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) c[q] += r[q];
-    }
-  };
-  const int ws = V.W;  // masks have V.W <= W words (a batched launch may run with a larger W)
-  uint32_t bi = 0;     // batches so far: the staging buffer alternates with it
-  for (int g = 0; g < tb.n_sb; ++g) {
-    const DSeg sg = V.seg[tb.sb_off + g];
-    const DSBatch* bt = V.sb + sg.sb_off;
-    DSBatch next = sg.n_sb > 0 ? bt[0] : DSBatch{};
-    __syncwarp();  // every lane is done with the previous segment's parity words
-    // rows of batches that fit the buffers go through shared memory; the
-    // segment's first copy overlaps its parity computation below
-    if (staged && ok && lane == 0 && sg.n_sb > 0) {
-      fence_proxy_async();
-      bulk_load((bi & 1) ? S.rb1 : S.rb0, V.rows + next.row_off, 128u * sl_batch_rows(next), (bi & 1) ? S.bar1 : S.bar0);
-    }
-    // the segment's parities as XORs of the X bits in their masks, 32 shots
-    // at once; four per lane at a time so that their mask loads overlap
-    const uint64_t* pm = V.par + (size_t)sg.par_off * ws;
-    for (uint32_t q0 = lane; q0 < sg.n_par; q0 += 128) {
-      uint64_t m[4][W];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t q = q0 + 32u * (uint32_t)u;
-#pragma unroll
-        for (int w = 0; w < W; ++w) m[u][w] = (w < ws && q < sg.n_par) ? __ldg(pm + (size_t)q * ws + w) : 0ull;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t q = q0 + 32u * (uint32_t)u;
-        uint32_t acc = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-          uint64_t x = m[u][w];
-          while (x) {
-            acc ^= lds(S.xs + 4u * (uint32_t)(64 * w + __ffsll((long long)x) - 1));
-            x &= x - 1;
-          }
-        }
-        if (q < sg.n_par)
-          asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.par + 4u * q), "r"(q == kSlOnes ? 0xFFFFFFFFu : acc)
-                       : "memory");
-      }
-    }
-    __syncwarp();
-    for (uint32_t b = 0; b < sg.n_sb; ++b, ++bi) {
-      const DSBatch B = next;
-      if (b + 1 < sg.n_sb) next = bt[b + 1];  // the next header's load overlaps this batch
-      uint32_t J0, J1, J2, Z;
-      if (staged && ok) {
-        const uint32_t buf = bi & 1;
-        // the other buffer held the previous batch, which every lane has finished
-        if (lane == 0 && b + 1 < sg.n_sb) {
-          fence_proxy_async();
-          bulk_load(buf ? S.rb0 : S.rb1, V.rows + next.row_off, 128u * sl_batch_rows(next), buf ? S.bar0 : S.bar1);
-        }
-        const uint32_t bar = buf ? S.bar1 : S.bar0;
-        if (!mbar_wait_bounded(bar, (state >> buf) & 1u)) {
-          // a copy that does not land in time: report it, let the copies in
-          // flight finish (bounded), and read rows from global memory
-          if (lane == 0) atomicOr(&g_status, ST_TIMEOUT);
-          mbar_wait_bounded(S.bar0, state & 1u);
-          mbar_wait_bounded(S.bar1, (state >> 1) & 1u);
-          ok = false;
-          state |= 4u;
-        } else {
-          state ^= 1u << buf;
-          sl_batch(B, RowsS{(buf ? S.rb1 : S.rb0) + 16u * (uint32_t)lane}, S.par, lane, J0, J1, J2, Z);
-        }
-      }
-      if (!staged || !ok)
-        sl_batch(B, RowsG{reinterpret_cast<const uint4*>(V.rows + B.row_off) + lane}, S.par, lane, J0, J1, J2, Z);
-      if (staged) __syncwarp();  // the buffer just read is refilled next batch
-      // lane s now needs, for each of the 32 terms, its phase and flag at shot s
-      const uint32_t T0 = transpose32(J0), T1 = transpose32(J1);
-      const uint32_t T2 = transpose32(J2), TZ = transpose32(Z);
-      const uint32_t nz = ~TZ;
-      const uint32_t M[4] = {~T0 & ~T1 & nz, T0 & ~T1 & nz, ~T0 & T1 & nz, T0 & T1 & nz};
-      if (B.d != d_cur) {
-        flush();
-        d_cur = B.d;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)  // terms with J = q count +1, with J = q + 4 count -1
-        n[q] += __popc(M[q]) - 2 * __popc(M[q] & T2);
-    }
-  }
-  flush();
-  if (S.rb > 0) {
-    __syncwarp();
-    if (lane == 0) asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.state), "r"(state) : "memory");
-    __syncwarp();
-  }
-  return z;
-}
-
-// SL: the program has sliced tables (kernels without them never contain the
-// warp-cooperative code and keep their register budget)
-template <int W, bool SL>
-__device__ ZC eval_table(const DevView& V, int t, const uint64_t (&X)[W], const SlSmem& sm) {
-  const DTable tb = V.tab[t];
-  if constexpr (SL) {
-    if (tb.mode == TAB_SLICED) return eval_table_sliced<W>(V, tb, X, sm);
-  }
-  ZC z{{0, 0, 0, 0}, tb.base};
-  long long (&c)[4] = z.c;
-  if (tb.mode == TAB_BASIS) {
-    // parities in a GF(2) basis of the table's mask span: Y holds the basis
-    // parities and every factor parity is <coordinates, Y>
-    uint64_t Y = 0;
-    for (uint32_t q = 0; q < tb.n_par; ++q)
-      Y |= (uint64_t)parity_w<W>(V.par + (size_t)(tb.par_off + q) * V.W, X, V.W) << q;
-    for (uint32_t q = 0; q < tb.n_cls; ++q) {
-      const DClass& C = V.cls[tb.cls_off + q];
-      const uint32_t fo = C.fac_off, nf = C.n_fac;
-      uint32_t acc = 0;
-      for (uint32_t k = 0; k < nf; ++k) {
-        const uint64_t ua = __ldg(V.fcoord + 2 * (size_t)(fo + k)), ub = __ldg(V.fcoord + 2 * (size_t)(fo + k) + 1);
-        const uint32_t a = __popcll(ua & Y) & 1, b = __popcll(ub & Y) & 1;
-        acc += __ldg(V.finc + (size_t)(fo + k) * 4 + (a | (b << 1)));
-      }
-      if (acc >> 21) continue;
-      accumulate(C, acc, c);
-    }
-    return z;
-  }
-  // distinct factor parities of this table, once per shot, into 256 bits
-  // (q is the same for every thread of a warp, so the word choice is uniform)
-  uint64_t P0 = 0, P1 = 0, P2 = 0, P3 = 0;
-  for (uint32_t q = 1; q < tb.n_par; ++q) {
-    const uint64_t bit = (uint64_t)parity_w<W>(V.par + (size_t)(tb.par_off + q) * V.W, X, V.W) << (q & 63);
-    if (q < 64) P0 |= bit;
-    else if (q < 128) P1 |= bit;
-    else if (q < 192) P2 |= bit;
-    else P3 |= bit;
-  }
-  auto pbit = [&](uint32_t i) -> uint32_t {
-    const uint64_t w = i < 128 ? (i < 64 ? P0 : P1) : (i < 192 ? P2 : P3);
-    return (uint32_t)((w >> (i & 63)) & 1);
-  };
-  for (uint32_t q = 0; q < tb.n_cls; ++q) {
-    const DClass& C = V.cls[tb.cls_off + q];
-    const uint32_t fo = C.fac_off, nf = C.n_fac;
-    uint32_t acc = 0;
-    for (uint32_t k = 0; k < nf; ++k) {
-      const uint32_t ix = __ldg(V.fidx + fo + k);
-      const uint32_t ia = ix & 0xFF, ib = (ix >> 8) & 0xFF;
-      const uint32_t a = pbit(ia), b = pbit(ib);
-      acc += __ldg(V.finc + (size_t)(fo + k) * 4 + (a | (b << 1)));
-    }
-    if (acc >> 21) continue;  // some factor vanished
-    accumulate(C, acc, c);
-  }
-  return z;
-}
-
-// the power of w that makes a chain's normalisation real and positive
-__device__ __forceinline__ int chain_rotation(const ZC& z, int* st) {
-  for (int rot = 0; rot < 8; ++rot) {
-    long long c[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) c[i] = pick(z.c, i + rot);
-    if (c[2] == 0 && c[1] + c[3] == 0) {
-      const __int128 A = (__int128)2 * c[0], B = (__int128)c[1] - c[3];
-      if (sign_xy(A, B, st) > 0) return rot;
-    }
-  }
-  *st |= ST_NOT_REAL;
-  return 0;
-}
-
-template <int W>
-__device__ __forceinline__ void set_xbit(uint64_t (&X)[W], int b, bool on) {
-#pragma unroll
-  for (int w = 0; w < W; ++w)
-    if (w == (b >> 6)) X[w] = on ? (X[w] | (1ull << (b & 63))) : (X[w] & ~(1ull << (b & 63)));
-}
-
-template <int W>
-__device__ __forceinline__ int get_xbit(const uint64_t (&X)[W], int b) {
-  uint64_t v = 0;
-#pragma unroll
-  for (int w = 0; w < W; ++w)
-    if (w == (b >> 6)) v = X[w];
-  return (int)((v >> (b & 63)) & 1);
-}
-
-// `take` (1..64) bits of X starting at bit x
-template <int W>
-__device__ __forceinline__ uint64_t get_xbits(const uint64_t (&X)[W], int x, int take) {
-  const int wi = x >> 6, sh = x & 63;
-  uint64_t lo = 0, hi = 0;
-#pragma unroll
-  for (int w = 0; w < W; ++w) {
-    if (w == wi) lo = X[w];
-    if (w == wi + 1) hi = X[w];
-  }
-  const uint64_t v = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
-  return take >= 64 ? v : v & ((1ull << take) - 1);
-}
-
-// One shot s of a launch (global shot index shot0 + s), records at row s.
-// Every lane of a warp calls it together (sliced tables are evaluated by the
-// whole warp); lanes past the end of the launch have valid = false and
-// compute a shot whose records are not written.  sm: the warp's shared words.
-template <int W, bool SL>
-__device__ void sample_one(const DevView& V, uint64_t s, bool valid, const RoundKeys& rk, uint64_t shot0,
-                           uint64_t* __restrict__ meas, uint64_t* __restrict__ det,
-                           uint64_t* __restrict__ obs, uint8_t* __restrict__ accept, const SlSmem& sm) {
-  const uint64_t shot = shot0 + s;
-  const uint32_t c0 = (uint32_t)shot, c1 = (uint32_t)(shot >> 32);
-  int st = 0;
-
-  // 1. error mechanisms and f = T e
-  uint64_t X[W];
-#pragma unroll
-  for (int w = 0; w < W; ++w) X[w] = 0;
-  // four channels per Philox block: their outcome-0 thresholds in one
-  // 16-byte load and one test; the rare block where some channel fires walks
-  // its channels
-  for (int c = 0; c < V.n_ch; c += 4) {
-    uint32_t u[4];
-    philox4x32_10(c0, c1, 0u, (uint32_t)(c >> 2), rk, u);
-    const uint4 t0 = __ldg(V.thr0 + (c >> 2));
-    if (!((u[0] >= t0.x) | (u[1] >= t0.y) | (u[2] >= t0.z) | (u[3] >= t0.w))) continue;
-#pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      const int ci = c + l;
-      if (ci >= V.n_ch) break;
-      const DChan ch = V.ch[ci];
-      const uint32_t U = u[l];
-      if (U < ch.thr0) continue;  // outcome 0: nothing fires
-      const uint32_t* thr = V.thr + ch.thr_off;
-      uint32_t o = 1;
-      while (o + 1 < ch.n_out && U >= __ldg(thr + o)) ++o;
-      if (o >= ch.n_out) continue;
-      const uint64_t* sg = V.sig + ch.sig_off + (size_t)o * V.W;
-#pragma unroll
-      for (int w = 0; w < W; ++w)
-        if (w < V.W) X[w] ^= __ldg(sg + w);
-    }
-  }
-
-  // 2-3. outputs in autoregressive order (Algorithm 1 per chain)
-  RV pp[kMaxChains];
-  int rot[kMaxChains];
-  for (int c = 0; c < V.n_chains; ++c) {
-    const ZC z = eval_table<W, SL>(V, V.chain_norm[c], X, sm);
-    rot[c] = chain_rotation(z, &st);
-    pp[c] = to_real_rot(z, rot[c], &st);
-  }
-  const int dw = (V.ndet + 63) >> 6, mw = (V.nmeas + 63) >> 6, ow = (V.nobs + 63) >> 6;
-  uint64_t ob[kMaxOutWords];  // measurement mode only
-  uint64_t cur = 0;  // detector mode: record word cw (detector words, then observable words)
-  int cw = -1;
-  bool any_det = false;
-  auto flush = [&]() {
-    if (cw < 0) return;
-    if (cw < dw) {
-      any_det |= cur != 0;
-      if (det && valid) det[s * dw + cw] = cur;
-    } else if (obs && valid) {
-      obs[s * ow + (cw - dw)] = cur;
-    }
-    cur = 0;
-  };
-  // bits of outputs i, i + 1, ... (within one record word) into the record
-  auto put = [&](int i, uint64_t bits) {
-    const bool is_det = i < V.ndet;
-    const int j = is_det ? i : i - V.ndet;
-    const int gw = is_det ? (j >> 6) : dw + (j >> 6);
-    if (gw != cw) {
-      flush();
-      cw = gw;
-    }
-    cur |= bits << (j & 63);
-  };
-  for (int e = 0; e < V.n_ent; ++e) {
-    const DOut o = V.out[e];
-    const int i = o.rec;
-    if (o.kind == OUT_RUN) {  // consecutive X bits straight into the record
-      int ii = i, x = o.a, n = o.chain;
-      while (n > 0) {
-        const int j = ii < V.ndet ? ii : ii - V.ndet;
-        const int take = min(n, 64 - (j & 63));
-        put(ii, get_xbits<W>(X, x, take));
-        ii += take;
-        x += take;
-        n -= take;
-      }
-      continue;
-    }
-    int bit;
-    if (o.kind == OUT_BIT) {
-      bit = get_xbit<W>(X, o.a) ^ o.cst;
-    } else if (o.kind == OUT_MASK) {
-      bit = parity_w<W>(V.omask + o.a, X, V.W) ^ o.cst;
-    } else {
-      set_xbit<W>(X, o.a, true);
-      const RV p1 = to_real_rot(eval_table<W, SL>(V, o.table, X, sm), rot[o.chain], &st);
-      const RV pv = pp[o.chain];
-      if (sign_xy(pv.A, pv.B, &st) <= 0) st |= ST_ZERO_PROB;
-      uint32_t u[4];
-      philox4x32_10(c0, c1, 1u, (uint32_t)(i >> 2), rk, u);
-      const uint32_t U = u[i & 3];
-      // bit = 1 iff U * P_prev < 2^32 * P_1
-      const int e = min(pv.e, p1.e + 32);
-      const __int128 LA = shl_chk(pv.A * (__int128)U, pv.e - e, &st);
-      const __int128 LB = shl_chk(pv.B * (__int128)U, pv.e - e, &st);
-      const __int128 RA = shl_chk(p1.A, p1.e + 32 - e, &st);
-      const __int128 RB = shl_chk(p1.B, p1.e + 32 - e, &st);
-      bit = sign_xy(LA - RA, LB - RB, &st) < 0;
-      if (bit) {
-        pp[o.chain] = p1;
-      } else {
-        const int e2 = min(pv.e, p1.e);
-        RV d;
-        d.A = shl_chk(pv.A, pv.e - e2, &st) - shl_chk(p1.A, p1.e - e2, &st);
-        d.B = shl_chk(pv.B, pv.e - e2, &st) - shl_chk(p1.B, p1.e - e2, &st);
-        d.e = e2;
-        pp[o.chain] = d;
-        set_xbit<W>(X, o.a, false);
-      }
-    }
-    if (V.mode == 0) {
-      put(i, (uint64_t)bit);  // detectors are outputs [0, ndet), observables [ndet, ndet + nobs)
-    } else {
-      if ((i & 63) == 0) ob[i >> 6] = 0;
-      ob[i >> 6] |= (uint64_t)bit << (i & 63);
-    }
-  }
-  if (V.mode == 0) flush();
-
-  // 4. measurement-mode records
-  if (V.mode != 0) {
-    if (meas && valid)
-      for (int w = 0; w < mw; ++w) meas[s * mw + w] = ob[w];
-    for (int w = 0; w < dw; ++w) {
-      uint64_t v = 0;
-      for (int b = 0; b < 64 && 64 * w + b < V.ndet; ++b) {
-        const int d = 64 * w + b;
-        int x = 0;
-        for (int q = V.dmap_off[d]; q < V.dmap_off[d + 1]; ++q) {
-          const int j = V.dmap_idx[q];
-          x ^= (int)((ob[j >> 6] >> (j & 63)) & 1);
-        }
-        v |= (uint64_t)x << b;
-      }
-      any_det |= v != 0;
-      if (det && valid) det[s * dw + w] = v;
-    }
-    if (obs && valid)
-      for (int w = 0; w < ow; ++w) {
-        uint64_t v = 0;
-        for (int b = 0; b < 64 && 64 * w + b < V.nobs; ++b) {
-          const int d = 64 * w + b;
-          int x = 0;
-          for (int q = V.omap_off[d]; q < V.omap_off[d + 1]; ++q) {
-            const int j = V.omap_idx[q];
-            x ^= (int)((ob[j >> 6] >> (j & 63)) & 1);
-          }
-          v |= (uint64_t)x << b;
-        }
-        obs[s * ow + w] = v;
-      }
-  }
-  if (!valid) return;
-  if (accept) accept[s] = any_det ? 0 : 1;
-  if (st) atomicOr(&g_status, st);
-}
-
-// dynamic shared memory: sl_warp_words(...) per warp for programs with sliced tables
-extern __shared__ __align__(128) uint32_t g_warp_smem[];
-
-// Register bounds (resident blocks of up to 128 threads per SM) for X of up
-// to 4 words: kernels for programs with sliced tables at 80 registers (6
-// blocks: occupancy hides the latency of the operation rows read through
-// L1), the others at 48 (10 blocks for the Philox-bound noise loop).  Wider X
-// needs 2W registers of its own, so the bounds relax with W.
-constexpr int min_blocks(int W, bool sl) {
-  return sl ? (W <= 4 ? 6 : W <= 8 ? 4 : 2) : (W <= 4 ? 10 : W <= 8 ? 6 : 2);
-}
-// the batched kernel keeps its work-item state live across the whole shot
-// loop: one block less for programs with sliced tables (96 registers)
-constexpr int min_blocks_batch(int W, bool sl) { return sl && W <= 4 ? 5 : min_blocks(W, sl); }
-
-template <int W, bool SL>
-__global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_sample(DevView V, RoundKeys rk, uint64_t shot0,
-                                                     uint64_t nshots, uint64_t* __restrict__ meas,
-                                                     uint64_t* __restrict__ det,
-                                                     uint64_t* __restrict__ obs,
-                                                     uint8_t* __restrict__ accept) {
-  const uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  SlSmem sm{};
-  if constexpr (SL) {
-    sm = sl_smem(g_warp_smem + (threadIdx.x >> 5) * sl_warp_words(W, V.sl_par, V.sl_rb), W, V.sl_par, V.sl_rb);
-    sl_init(sm);
-  }
-  sample_one<W, SL>(V, s, s < nshots, rk, shot0, meas, det, obs, accept, sm);
-}
-
-// ------------------------------------------------------- batched launch
-// One persistent launch over many programs: work item i is a block of `sb`
-// shots (a multiple of 32) of one program; warps take items from an atomic
-// counter until all are done (no waiting on other warps or blocks).  Program p owns items
-// [item_start[p], item_start[p+1]).
-struct BatchProg {
-  DevView v;
-  uint64_t shots, seed, shot_offset;
-  uint64_t* meas;
-  uint64_t* det;
-  uint64_t* obs;
-  uint8_t* accept;
-};
-
-template <int W, bool SL>
-__global__ void __launch_bounds__(kThreads, min_blocks_batch(W, SL)) k_batch(const BatchProg* __restrict__ progs, int n,
-                                                    const uint64_t* __restrict__ item_start,
-                                                    uint64_t total_items, uint32_t sb,
-                                                    unsigned long long* counter, int sl_par, int sl_rb) {
-  SlSmem sm{};
-  if constexpr (SL) {
-    sm = sl_smem(g_warp_smem + (threadIdx.x >> 5) * sl_warp_words(W, sl_par, sl_rb), W, sl_par, sl_rb);
-    sl_init(sm);
-  }
-  // every warp takes its own work items (no block-wide synchronisation)
-  const int lane = threadIdx.x & 31;
-  for (;;) {
-    unsigned long long it = 0;
-    if (lane == 0) it = atomicAdd(counter, 1ull);
-    it = __shfl_sync(0xFFFFFFFFu, it, 0);
-    if (it >= total_items) return;
-    int lo = 0, hi = n - 1;  // last program with item_start <= it
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (item_start[mid] <= it) lo = mid;
-      else hi = mid - 1;
-    }
-    const BatchProg& P = progs[lo];
-    const uint64_t first = (it - item_start[lo]) * sb;
-    const uint64_t last = min(first + sb, P.shots);
-    const RoundKeys rk = round_keys(P.seed);
-    for (uint64_t s0 = first; s0 < last; s0 += 32) {
-      const uint64_t s = s0 + lane;
-      sample_one<W, SL>(P.v, s, s < last, rk, P.shot_offset, P.meas, P.det, P.obs, P.accept, sm);
-    }
-  }
 }
 
 // ------------------------------------------------------ host-side packing
@@ -1276,6 +365,32 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
       s.put(&d, sizeof d);
       for (size_t w = 0; !c.sig.empty() && w < c.sig[0].size(); ++w)
         if (c.sig[0][w]) throw PackError{TSIM_ERR_INTERNAL, "channel outcome 0 must not flip anything"};
+    }
+  }
+  // geometric-gap groups: descriptors, member channel indices, and per
+  // group T_k = floor(T_{k-1} Q / 2^32) for k = 1..n (T_0 = 2^32)
+  L.o_grp = s.section();
+  {
+    uint32_t moff = 0;
+    for (const NoiseGroup& g : p.groups) {
+      DGroup d{g.Q, (uint32_t)g.member.size(), moff, moff};
+      moff += (uint32_t)g.member.size();
+      s.put(&d, sizeof d);
+    }
+  }
+  L.o_gmem = s.section();
+  for (const NoiseGroup& g : p.groups)
+    for (int c : g.member) {
+      const uint32_t v = (uint32_t)c;
+      s.put(&v, 4);
+    }
+  L.o_gT = s.section();
+  for (const NoiseGroup& g : p.groups) {
+    uint64_t t = 1ull << 32;
+    for (size_t k = 0; k < g.member.size(); ++k) {
+      t = (t * (uint64_t)g.Q) >> 32;
+      const uint32_t v = (uint32_t)t;
+      s.put(&v, 4);
     }
   }
   L.o_t0 = s.section();
@@ -1767,6 +882,12 @@ DevView make_view(const unsigned char* base, const DeviceLayout& L, const Progra
   v.ndet = p.ndet;
   v.nobs = p.nobs;
   v.mode = p.mode;
+  v.status = nullptr;  // set by the caller: the status word of the device the view lives on
+  v.noise_mode = p.noise_mode;
+  v.n_grp = (int)p.groups.size();
+  v.grp = (const DGroup*)(base + L.o_grp);
+  v.gmem = (const uint32_t*)(base + L.o_gmem);
+  v.gT = (const uint32_t*)(base + L.o_gT);
   v.ch = (const DChan*)(base + L.o_ch);
   v.thr0 = (const uint4*)(base + L.o_t0);
   v.thr = (const uint32_t*)(base + L.o_thr);
@@ -1814,6 +935,7 @@ DeviceProgram* upload(const Program& p) {
     fail(TSIM_ERR_CUDA, std::string("cudaMemcpy of program tables: ") + cudaGetErrorString(e));
   }
   d->v = make_view((const unsigned char*)d->blob, T.layout, p);
+  d->v.status = status_word(d->device);
   return d;
 }
 
@@ -1829,62 +951,36 @@ const DevView& ensure_uploaded(const Program& p) {
   return slot->v;
 }
 
-// Threads per block and dynamic shared memory of a launch: programs with
-// sliced tables get sl_words words per warp (sl_warp_words) and as many warps
-// per block (1 to 4) as fit in kSmemPerBlock; the others use kThreads
-// threads and none.
-constexpr int kSmemPerBlock = 48 * 1024;
-
-struct LaunchShape {
-  unsigned threads;
-  size_t smem;
-};
-
-LaunchShape shape_of(int sl_words) {
-  if (sl_words <= 0) return {(unsigned)kThreads, 0};
-  const size_t per_warp = (size_t)sl_words * 4;
-  const int warps = (int)std::max<size_t>(1, std::min<size_t>(kThreads / 32, kSmemPerBlock / per_warp));
-  return {(unsigned)(32 * warps), per_warp * (size_t)warps};
-}
-
-// allow a kernel more than the default 48 KB of dynamic shared memory
-template <class K>
-cudaError_t allow_smem(K kernel, size_t smem) {
-  if (smem <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-template <int W>
-cudaError_t launch_w(const DevView& v, cudaStream_t s, uint64_t seed, uint64_t off, uint64_t shots, uint64_t* meas,
-                     uint64_t* det, uint64_t* obs, uint8_t* acc) {
-  const LaunchShape sh = shape_of(sl_warp_words(W, v.sl_par, v.sl_rb));
-  const uint64_t blocks = (shots + sh.threads - 1) / sh.threads;
-  if (blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
-  if (v.sl_par > 0) {
-    cudaError_t e = allow_smem(k_sample<W, true>, sh.smem);
-    if (e != cudaSuccess) return e;
-    k_sample<W, true><<<(unsigned)blocks, sh.threads, sh.smem, s>>>(v, round_keys(seed), off, shots, meas, det, obs,
-                                                                     acc);
-  } else {
-    k_sample<W, false><<<(unsigned)blocks, sh.threads, 0, s>>>(v, round_keys(seed), off, shots, meas, det, obs, acc);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch(const DevView& v, cudaStream_t s, uint64_t seed, uint64_t off, uint64_t shots, uint64_t* meas,
-                   uint64_t* det, uint64_t* obs, uint8_t* acc) {
-  switch (v.W) {
-    case 1: return launch_w<1>(v, s, seed, off, shots, meas, det, obs, acc);
-    case 2: return launch_w<2>(v, s, seed, off, shots, meas, det, obs, acc);
-    case 4: return launch_w<4>(v, s, seed, off, shots, meas, det, obs, acc);
-    case 8: return launch_w<8>(v, s, seed, off, shots, meas, det, obs, acc);
-    case 16: return launch_w<16>(v, s, seed, off, shots, meas, det, obs, acc);
-    case 32: return launch_w<32>(v, s, seed, off, shots, meas, det, obs, acc);
+// one program's sampling launch, dispatched on the padded width of X
+cudaError_t launch(const LaunchArgs& a) {
+  switch (a.v.W) {
+    case 1: return launch_sample<1>(a);
+    case 2: return launch_sample<2>(a);
+    case 4: return launch_sample<4>(a);
+    case 8: return launch_sample<8>(a);
+    case 16: return launch_sample<16>(a);
+    case 32: return launch_sample<32>(a);
     default: return cudaErrorInvalidValue;
   }
 }
 
+cudaError_t launch(const DevView& v, cudaStream_t s, uint64_t seed, uint64_t off, uint64_t shots, uint64_t* meas,
+                   uint64_t* det, uint64_t* obs, uint8_t* acc) {
+  LaunchArgs a{};
+  a.v = v;
+  a.stream = s;
+  a.seed = seed;
+  a.shot_offset = off;
+  a.shots = shots;
+  a.meas = meas;
+  a.det = det;
+  a.obs = obs;
+  a.accept = acc;
+  return launch(a);
+}
+
 }  // namespace
+
 
 // Host emulation of the warp-cooperative evaluation of a sliced table, read
 // from the packed tables exactly as the kernel reads them: 32 per-shot
@@ -2000,6 +1096,9 @@ void selftest_sliced(const Program& p, uint64_t seed, int rounds) {
 
 void prepare_device_tables(Program& p, int64_t sliced_min, int stage_rows, int seg_par) {
   auto* t = new DeviceTables();
+  t->sliced_min = sliced_min;
+  t->stage_rows = stage_rows;
+  t->seg_par = seg_par;
   try {
     pack(p, *t, sliced_min, stage_rows < 0 ? kDefaultStageRows : stage_rows,
          seg_par <= 0 ? kDefaultSegmentParities : std::max(seg_par, 16));
@@ -2063,22 +1162,6 @@ void plan_items(BatchPlan& b, cudaStream_t s) {
   TSIM_CUDA(cudaStreamSynchronize(s));
 }
 
-template <int W>
-cudaError_t launch_group_w(const BatchPlan& b, const BatchGroup& g, cudaStream_t s, unsigned grid) {
-  // every warp gets room for the transposed X at the launch's W, the
-  // largest sliced parity buffer and the largest row buffers of the group
-  const LaunchShape sh = shape_of(sl_warp_words(W, g.sl_par, g.sl_rb));
-  if (g.sl_par > 0) {
-    cudaError_t e = allow_smem(k_batch<W, true>, sh.smem);
-    if (e != cudaSuccess) return e;
-    k_batch<W, true><<<grid, sh.threads, sh.smem, s>>>(b.d_progs + g.off, g.n, g.d_item_start, g.total_items, b.sb,
-                                                       g.d_counter, g.sl_par, g.sl_rb);
-  } else {
-    k_batch<W, false><<<grid, sh.threads, 0, s>>>(b.d_progs + g.off, g.n, g.d_item_start, g.total_items, b.sb,
-                                                  g.d_counter, 0, 0);
-  }
-  return cudaGetLastError();
-}
 
 cudaError_t launch_batch(const BatchPlan& b, cudaStream_t s) {
   if (b.form == 1) {  // the programs' own sampling launches, one after another
@@ -2094,14 +1177,24 @@ cudaError_t launch_batch(const BatchPlan& b, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(g.d_counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const uint64_t want = (uint64_t)b.sms * (uint64_t)b.blocks_per_sm;
-    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, g.total_items));
+    BatchLaunchArgs a{};
+    a.progs = b.d_progs + g.off;
+    a.n = g.n;
+    a.item_start = g.d_item_start;
+    a.total_items = g.total_items;
+    a.sb = b.sb;
+    a.counter = g.d_counter;
+    a.sl_par = g.sl_par;
+    a.sl_rb = g.sl_rb;
+    a.stream = s;
+    a.grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, g.total_items));
     switch (g.wmax) {
-      case 1: e = launch_group_w<1>(b, g, s, grid); break;
-      case 2: e = launch_group_w<2>(b, g, s, grid); break;
-      case 4: e = launch_group_w<4>(b, g, s, grid); break;
-      case 8: e = launch_group_w<8>(b, g, s, grid); break;
-      case 16: e = launch_group_w<16>(b, g, s, grid); break;
-      case 32: e = launch_group_w<32>(b, g, s, grid); break;
+      case 1: e = launch_batch_group<1>(a); break;
+      case 2: e = launch_batch_group<2>(a); break;
+      case 4: e = launch_batch_group<4>(a); break;
+      case 8: e = launch_batch_group<8>(a); break;
+      case 16: e = launch_batch_group<16>(a); break;
+      case 32: e = launch_batch_group<32>(a); break;
       default: e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
@@ -2261,13 +1354,32 @@ void device_sample_batch(const Program* const* progs, int n, const SampleArgs* a
   TSIM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
 }
 
+
 void device_sync(void* stream) {
   TSIM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  int dev = -1;
+  TSIM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) fail(TSIM_ERR_ARG, "device index out of range");
+  int* words[2] = {nullptr, nullptr};
+  {
+    std::lock_guard<std::mutex> lock(g_status_mu);
+    words[0] = g_status_dev[dev];
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    words[1] = (int*)g_noalloc_dev[dev];
+  }
   int st = 0;
-  TSIM_CUDA(cudaMemcpyFromSymbol(&st, g_status, sizeof st));
+  for (int* w : words) {
+    if (!w) continue;
+    int v = 0;
+    TSIM_CUDA(cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost));
+    if (v) {
+      st |= v;
+      TSIM_CUDA(cudaMemset(w, 0, sizeof v));
+    }
+  }
   if (st) {
-    int z = 0;
-    TSIM_CUDA(cudaMemcpyToSymbol(g_status, &z, sizeof z));
     if (st & ST_TIMEOUT) fail(TSIM_ERR_TIMEOUT, "device: a shared-memory staging copy did not complete in time");
     if (st & ST_ZERO_PROB) fail(TSIM_ERR_ZERO_PROB, "device: a sampled prefix had P_prev <= 0");
     if (st & ST_NOT_REAL) fail(TSIM_ERR_INTERNAL, "device: a marginal was not real");
@@ -2275,74 +1387,94 @@ void device_sync(void* stream) {
   }
 }
 
-}  // namespace tsim
-
-// ------------------------------------------------------------------------
-// Sampling without device allocation.
-//
-// Some callers cannot call cudaMalloc: code running inside a memory pool or
-// allocator they do not own, real-time loops that must not touch the driver's
-// allocator, or hosts whose device memory is carved up ahead of time.  For
-// them tsim_sample_noalloc runs the same sampling kernel, but the program's
-// device tables -- the scratch that tsim_sample allocates once per program --
-// live in the fixed array below instead.  Its size is kNoAllocBytes (4 MiB);
-// every GPU that loads the library holds it until the process exits.
-namespace tsim {
-namespace {
-
-constexpr size_t kNoAllocBytes = (size_t)4 << 20;
-constexpr int kNoAllocMaxDevices = 64;
-
-__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-std::mutex g_noalloc_mutex;
-// device address of g_noalloc_scratch, per device, from cudaGetSymbolAddress
-void* g_noalloc_dev[kNoAllocMaxDevices];
-
-tsim_status noalloc_error(tsim_status st, const char* msg) {
-  set_last_error(msg);
-  return st;
+void device_sample_debug(const Program& p, const SampleArgs& a, const uint64_t* dump_shots, int n_dump,
+                         int64_t* h_dump, void* stream) {
+  if (p.mode == TSIM_MODE_DETECTORS && a.meas) fail(TSIM_ERR_ARG, "measurement records requested from a detector-mode program");
+  const DeviceTables& T = tables_of(p);
+  if (n_dump < 0 || (n_dump > 0 && (!dump_shots || !h_dump))) fail(TSIM_ERR_ARG, "bad dump arguments");
+  if (a.shots == 0) return;
+  if (a.shots > ((uint64_t)1 << 31)) fail(TSIM_ERR_ARG, "debug launches are limited to 2^31 shots");
+  std::vector<int32_t> row(a.shots, -1);
+  for (int k = 0; k < n_dump; ++k) {
+    if (dump_shots[k] >= a.shots || row[(size_t)dump_shots[k]] >= 0) fail(TSIM_ERR_ARG, "dump shots must be distinct and inside the launch");
+    row[(size_t)dump_shots[k]] = k;
+  }
+  const DevView& v = ensure_uploaded(p);
+  const int evals = (int)p.chain_norm.size() + p.nr;
+  const int wdev = T.layout.W;
+  const int stride = evals * (kDumpHead + wdev);
+  struct Buf {
+    void* p = nullptr;
+    ~Buf() { if (p) cudaFree(p); }
+  } drow, ddump;
+  TSIM_CUDA(cudaMalloc(&drow.p, row.size() * sizeof(int32_t)));
+  TSIM_CUDA(cudaMalloc(&ddump.p, std::max<size_t>(1, (size_t)n_dump * (size_t)stride) * sizeof(long long)));
+  cudaStream_t s = (cudaStream_t)stream;
+  TSIM_CUDA(cudaMemcpyAsync(drow.p, row.data(), row.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  TSIM_CUDA(cudaMemsetAsync(ddump.p, 0, std::max<size_t>(1, (size_t)n_dump * (size_t)stride) * sizeof(long long), s));
+  LaunchArgs la{};
+  la.v = v;
+  la.stream = s;
+  la.seed = a.seed;
+  la.shot_offset = a.shot_offset;
+  la.shots = a.shots;
+  la.meas = a.meas;
+  la.det = a.det;
+  la.obs = a.obs;
+  la.accept = a.accept;
+  la.dump = (long long*)ddump.p;
+  la.dump_row = (const int32_t*)drow.p;
+  la.dump_stride = stride;
+  cudaError_t e = launch(la);
+  if (e != cudaSuccess) fail(TSIM_ERR_CUDA, std::string("debug sampling launch: ") + cudaGetErrorString(e));
+  std::vector<long long> buf((size_t)n_dump * (size_t)stride);
+  if (!buf.empty())
+    TSIM_CUDA(cudaMemcpyAsync(buf.data(), ddump.p, buf.size() * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  TSIM_CUDA(cudaStreamSynchronize(s));
+  // host layout: per shot, per evaluation, kDumpHead + x_words values
+  const int wout = p.W;
+  for (int k = 0; k < n_dump; ++k)
+    for (int ev = 0; ev < evals; ++ev) {
+      const long long* src = buf.data() + (size_t)k * stride + (size_t)ev * (kDumpHead + wdev);
+      int64_t* dst = h_dump + ((size_t)k * evals + (size_t)ev) * (size_t)(kDumpHead + wout);
+      for (int i = 0; i < kDumpHead + wout; ++i) dst[i] = src[i];
+    }
 }
 
-}  // namespace
-}  // namespace tsim
-
-extern "C" tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t shots, uint64_t seed,
-                                           uint64_t shot_offset, uint64_t* d_meas, uint64_t* d_det,
-                                           uint64_t* d_obs, uint8_t* d_accept, void* cuda_stream) {
-  using namespace tsim;
-  if (!prog || !prog->p) return noalloc_error(TSIM_ERR_ARG, "NULL program");
-  const Program& p = *prog->p;
-  if (p.mode == TSIM_MODE_DETECTORS && d_meas)
-    return noalloc_error(TSIM_ERR_ARG, "measurement records requested from a detector-mode program");
-  if (!p.devtab) return noalloc_error(TSIM_ERR_INTERNAL, "program has no device tables");
+void device_sample_noalloc(const Program& p, const SampleArgs& a, void* stream) {
+  if (p.mode == TSIM_MODE_DETECTORS && a.meas) fail(TSIM_ERR_ARG, "measurement records requested from a detector-mode program");
   // the packed tables were built on the host when the program was compiled
   // or loaded; this call only copies them
-  const DeviceTables& T = *p.devtab;
-  if (T.status != TSIM_OK) return noalloc_error(T.status, "program tables cannot run on the device");
-  if (T.layout.total > kNoAllocBytes)
-    return noalloc_error(TSIM_ERR_ARG, "program tables exceed the 4 MiB maximum of tsim_sample_noalloc");
-  if (shots == 0) return TSIM_OK;
-  if (shots > 0x7FFFFFFFull * 32) return noalloc_error(TSIM_ERR_ARG, "too many shots for one launch");
+  const DeviceTables& T = tables_of(p);
+  if (T.layout.total > kNoAllocBytes - kNoAllocHead)
+    fail(TSIM_ERR_ARG, "program tables exceed the 4 MiB maximum of tsim_sample_noalloc");
+  if (a.shots == 0) return;
+  if (a.shots > 0x7FFFFFFFull * 32) fail(TSIM_ERR_ARG, "too many shots for one launch");
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
-    return noalloc_error(TSIM_ERR_CUDA, "cudaGetDevice failed or device index out of range");
+  TSIM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) fail(TSIM_ERR_ARG, "device index out of range");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TSIM_CUDA(cudaStreamIsCapturing(s, &cs));
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_dev[dev]) {
-    // once per device, with that device current: the host-side symbol is not
-    // a device address, so the kernel must be given the address looked up here
+  if (cs == cudaStreamCaptureStatusNone) {
+    // with the device current: looked up again on every call that is not
+    // being captured, so a device reset (which moves the array) is picked up
     void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
-      return noalloc_error(TSIM_ERR_CUDA, "cudaGetSymbolAddress of the no-alloc scratch array failed");
+    TSIM_CUDA(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+    if (!ptr) fail(TSIM_ERR_CUDA, "cudaGetSymbolAddress of the no-alloc scratch array returned NULL");
     g_noalloc_dev[dev] = ptr;
+  } else if (!g_noalloc_dev[dev]) {
+    fail(TSIM_ERR_ARG, "the first tsim_sample_noalloc call on a device must come before any stream capture");
   }
-  cudaStream_t s = (cudaStream_t)cuda_stream;
+  unsigned char* base = (unsigned char*)g_noalloc_dev[dev];
   // every byte the kernel reads is rewritten here, so nothing stale from the
-  // previous call survives
-  if (cudaMemcpyAsync(g_noalloc_dev[dev], T.blob.data(), T.layout.total, cudaMemcpyHostToDevice, s) != cudaSuccess)
-    return noalloc_error(TSIM_ERR_CUDA, "cudaMemcpyAsync into the no-alloc scratch array failed");
-  const DevView v = make_view((const unsigned char*)g_noalloc_dev[dev], T.layout, p);
-  if (launch(v, s, seed, shot_offset, shots, d_meas, d_det, d_obs, d_accept) != cudaSuccess)
-    return noalloc_error(TSIM_ERR_CUDA, "launch of the sampling kernel failed");
-  return TSIM_OK;
+  // previous call survives; the status word is cleared by tsim_sync
+  TSIM_CUDA(cudaMemcpyAsync(base + kNoAllocHead, T.blob.data(), T.layout.total, cudaMemcpyHostToDevice, s));
+  DevView v = make_view(base + kNoAllocHead, T.layout, p);
+  v.status = (int*)base;
+  cudaError_t e = launch(v, s, a.seed, a.shot_offset, a.shots, a.meas, a.det, a.obs, a.accept);
+  if (e != cudaSuccess) fail(TSIM_ERR_CUDA, std::string("sampling kernel launch: ") + cudaGetErrorString(e));
 }
+
+}  // namespace tsim

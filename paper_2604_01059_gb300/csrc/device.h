@@ -17,8 +17,14 @@ struct SampleArgs {
   uint8_t* accept = nullptr;
 };
 
+// Tables with at least this many terms (after merging equal factor lists)
+// use the bit-sliced warp-cooperative layout when their factors allow it
+// (measured: 4 beats 2, 16 and 64 on the colour-code and mirror workloads).
+constexpr int64_t kDefaultSlicedMin = 4;
+
 // Byte offsets of the sections of the packed device tables (256-byte aligned)
 struct DeviceLayout {
+  size_t o_grp = 0, o_gmem = 0, o_gT = 0;  // geometric-gap noise groups, members, gap tables
   size_t o_ch = 0, o_t0 = 0, o_thr = 0, o_sig = 0, o_out = 0, o_om = 0, o_cn = 0, o_tab = 0, o_par = 0,
          o_cls = 0, o_fidx = 0, o_finc = 0, o_fco = 0, o_seg = 0, o_sb = 0, o_row = 0, o_dmo = 0, o_dmi = 0, o_omo = 0,
          o_omi = 0, total = 0;
@@ -40,11 +46,6 @@ struct DeviceLayout {
   std::vector<uint64_t> table_work32;  // sliced: integer lane-operations of one warp (32 shots)
 };
 
-// Tables with at least this many terms (after merging equal factor lists)
-// use the bit-sliced warp-cooperative layout when their factors allow it
-// (measured: 4 beats 2, 16 and 64 on the colour-code and mirror workloads).
-constexpr int64_t kDefaultSlicedMin = 4;
-
 // Host-side packed tables of one program, built once when the program is
 // compiled or loaded.  status != TSIM_OK when the program cannot run on the
 // device (message says why); sampling then fails with that status.
@@ -53,6 +54,9 @@ struct DeviceTables {
   DeviceLayout layout;
   tsim_status status = TSIM_OK;
   std::string message;
+  // the packing arguments, as given to prepare_device_tables
+  int64_t sliced_min = kDefaultSlicedMin;
+  int stage_rows = -1, seg_par = 0;
 };
 
 // Sliced batches with at most this many operation rows are staged through
@@ -75,6 +79,15 @@ void prepare_device_tables(Program& p, int64_t sliced_min = kDefaultSlicedMin, i
 // the same table; fails with TSIM_ERR_INTERNAL on any difference.
 void selftest_sliced(const Program& p, uint64_t seed, int rounds);
 void device_sample(const Program& p, const SampleArgs& a, void* stream);
+// tsim_sample without device allocation: the tables go into the library's
+// fixed static device array (see tsim_sample_noalloc).
+void device_sample_noalloc(const Program& p, const SampleArgs& a, void* stream);
+// tsim_sample plus a copy of every table evaluation of the chosen shots
+// (indices within the launch): per shot, per evaluation (chain
+// normalisations, then random outputs in order), [table, c0, c1, c2, c3,
+// sqrt2 exponent, X words (x_words)].  Synchronises the stream.
+void device_sample_debug(const Program& p, const SampleArgs& a, const uint64_t* dump_shots, int n_dump,
+                         int64_t* h_dump, void* stream);
 void device_sample_batch(const Program* const* progs, int n, const SampleArgs* args, void* stream);
 
 struct BatchPlan;

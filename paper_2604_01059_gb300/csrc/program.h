@@ -43,6 +43,17 @@ struct ProgChannel {
   std::vector<double> probs;            // outcome probabilities (double, before quantisation)
 };
 
+// Noise by geometric gaps (Sec. "Detectors": the gap between successive
+// firing events is geometric).  Group g holds channels whose outcome-0
+// thresholds are all >= Q; candidates are Bernoulli(1 - Q / 2^32) trials
+// along the group, placed by one geometric gap per word, and a candidate
+// channel keeps its own outcome distribution through a second word mapped
+// onto [Q, 2^32).
+struct NoiseGroup {
+  uint32_t Q = 0;
+  std::vector<int> member;  // channel indices, in sampling order
+};
+
 struct RawInfo {
   int nbits = 0;
   std::vector<double> probs;                 // 2^nbits
@@ -59,6 +70,8 @@ struct Program {
   std::vector<ProgOutput> outputs;
   std::vector<int> chain_norm;           // normalisation table of each chain
   std::vector<ProgChannel> channels;
+  int noise_mode = 0;                    // 0: one word per channel; 1: geometric gaps over `groups`
+  std::vector<NoiseGroup> groups;
   std::vector<ProgTable> tables;
   std::vector<std::vector<int>> detmap, obsmap;  // measurement mode only
   std::vector<RawInfo> raw;
@@ -71,6 +84,12 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
 void save_program(const Program& p, const std::string& path);
 Program* load_program(const std::string& path);
 ZW eval_table_host(const Program& p, int t, const uint64_t* x);
+// Noise sampling mode: 0 one word per channel, 1 geometric gaps, -1 the
+// cheaper of the two by expected random words per shot (groups are formed
+// from the channels' outcome-0 thresholds).  Does not re-pack device tables.
+void set_noise_sampling(Program& p, int mode);
+// expected random words per shot of each mode: [0] one per channel, [1] geometric
+void noise_word_estimate(const Program& p, double out[2]);
 
 struct Graph;
 // The diagram of every marginal of a circuit after the Clifford rewrites, in

@@ -1,7 +1,7 @@
 // Program text format (save / load).  Line-oriented, whitespace separated;
 // masks are W words of 16 hex digits (word 0 first), thresholds decimal:
 //
-//   TSIMPROG 1
+//   TSIMPROG 2
 //   mode detectors|measurements
 //   nx <n_x>  words <W>  nf <n_f>  nr <n_random>
 //   nmeas <N_m>  ndet <N_d>  nobs <N_o>
@@ -12,6 +12,8 @@
 //   channels <n>         then per channel:
 //     K <n_outcomes> <thr_0> .. <thr_{n-2}>    outcome o iff U < thr[o] (first)
 //     S <signature words>                      one line per outcome: X ^= sig
+//   noise <mode> <groups>  mode 0: one word per channel; mode 1: geometric
+//                        gaps, then per group  G <Q> <n> <channel indices>
 //   tables <n>           then per table  T <terms>, per term  t <s0> <j0> <m>
 //     (c^t = w^j0 sqrt2^s0) and per factor
 //     f <kind> <alpha> <beta> <u words> <v words>
@@ -83,7 +85,7 @@ struct Reader {
 void save_program(const Program& p, const std::string& path) {
   std::ofstream os(path);
   if (!os) fail(TSIM_ERR_ARG, "cannot open " + path + " for writing");
-  os << "TSIMPROG 1\nmode " << (p.mode == TSIM_MODE_MEASUREMENTS ? "measurements" : "detectors") << "\n";
+  os << "TSIMPROG 2\nmode " << (p.mode == TSIM_MODE_MEASUREMENTS ? "measurements" : "detectors") << "\n";
   os << "nx " << p.nx << "\nwords " << p.W << "\nnf " << p.nf << "\nnr " << p.nr << "\n";
   os << "nmeas " << p.nmeas << "\nndet " << p.ndet << "\nnobs " << p.nobs << "\n";
   os << "outputs " << p.outputs.size() << "\n";
@@ -108,6 +110,12 @@ void save_program(const Program& p, const std::string& path) {
       put_words(os, s);
       os << "\n";
     }
+  }
+  os << "noise " << p.noise_mode << " " << p.groups.size() << "\n";
+  for (const NoiseGroup& g : p.groups) {
+    os << "G " << g.Q << " " << g.member.size();
+    for (int c : g.member) os << " " << c;
+    os << "\n";
   }
   os << "tables " << p.tables.size() << "\n";
   for (const ProgTable& tb : p.tables) {
@@ -160,7 +168,7 @@ Program* load_program(const std::string& path) {
   Reader R{is};
   auto p = std::make_unique<Program>();
   R.expect("TSIMPROG");
-  if (R.integer() != 1) fail(TSIM_ERR_PARSE, "unknown program version");
+  if (R.integer() != 2) fail(TSIM_ERR_PARSE, "unknown program version");
   R.expect("mode");
   std::string m = R.tok();
   if (m != "detectors" && m != "measurements") fail(TSIM_ERR_PARSE, "bad mode");
@@ -204,6 +212,34 @@ Program* load_program(const std::string& path) {
     if (k < 1 || k > 64) fail(TSIM_ERR_PARSE, "bad outcome count");
     for (long long i = 0; i + 1 < k; ++i) c.thr.push_back((uint32_t)R.integer());
     for (long long i = 0; i < k; ++i) { R.expect("S"); c.sig.push_back(R.words()); }
+  }
+  R.expect("noise");
+  p->noise_mode = (int)R.integer();
+  n = R.integer();
+  if (p->noise_mode < 0 || p->noise_mode > 1 || n < 0 || (p->noise_mode == 0 && n != 0))
+    fail(TSIM_ERR_PARSE, "bad noise section");
+  {
+    std::vector<char> seen(p->channels.size(), 0);
+    for (long long g = 0; g < n; ++g) {
+      R.expect("G");
+      NoiseGroup G;
+      long long q = R.integer();
+      long long m = R.integer();
+      if (q < 0 || q > 0xFFFFFFFFll || m < 1) fail(TSIM_ERR_PARSE, "bad noise group");
+      G.Q = (uint32_t)q;
+      for (long long k = 0; k < m; ++k) {
+        long long c = R.integer();
+        if (c < 0 || c >= (long long)p->channels.size() || seen[(size_t)c]) fail(TSIM_ERR_PARSE, "bad noise group member");
+        const ProgChannel& ch = p->channels[(size_t)c];
+        if (ch.thr.empty() || ch.thr[0] < G.Q) fail(TSIM_ERR_PARSE, "noise group Q above a member's outcome-0 threshold");
+        seen[(size_t)c] = 1;
+        G.member.push_back((int)c);
+      }
+      p->groups.push_back(std::move(G));
+    }
+    if (p->noise_mode == 1)
+      for (size_t c = 0; c < p->channels.size(); ++c)
+        if (!p->channels[c].thr.empty() && !seen[c]) fail(TSIM_ERR_PARSE, "a channel is in no noise group");
   }
   R.expect("tables");
   n = R.integer();

@@ -51,6 +51,13 @@ def read(path):
             expect("S")
             sigs.append(words())
         channels.append((thr, sigs))
+    expect("noise")
+    noise_mode, ngroups = int(tok()), int(tok())
+    groups = []
+    for _ in range(ngroups):
+        expect("G")
+        q, m = int(tok()), int(tok())
+        groups.append((q, [int(tok()) for _ in range(m)]))
     expect("tables")
     tables = []
     for _ in range(int(tok())):
@@ -92,6 +99,7 @@ def read(path):
         raw.append((nb, probs, cols))
     expect("end")
     return dict(mode=mode, outputs=outs, chains=chains, channels=channels, tables=tables,
+                noise_mode=noise_mode, groups=groups,
                 raw=raw, meta=meta, **hdr, **maps)
 
 

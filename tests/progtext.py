@@ -12,12 +12,13 @@ def hexw(words):
 
 
 def program_text(*, mode="detectors", nx=1, nf=0, nr=0, nmeas=0, ndet=0, nobs=0,
-                 outputs=(), chains=(), channels=(), tables=(), detmap=(), obsmap=()):
+                 outputs=(), chains=(), channels=(), tables=(), detmap=(), obsmap=(), groups=None):
     """outputs: ("D", mask_words, const) | ("R", xbit, chain, table)
     channels: (thresholds, [sig words per outcome])
+    groups: None (one word per channel) or [(Q, [channel indices])] (geometric gaps)
     tables: [terms], term = (s0, j0, [(kind, alpha, beta, u_words, v_words)])"""
     W = max(1, (nx + 63) // 64)
-    L = ["TSIMPROG 1", f"mode {mode}", f"nx {nx}", f"words {W}", f"nf {nf}", f"nr {nr}",
+    L = ["TSIMPROG 2", f"mode {mode}", f"nx {nx}", f"words {W}", f"nf {nf}", f"nr {nr}",
          f"nmeas {nmeas}", f"ndet {ndet}", f"nobs {nobs}", f"outputs {len(outputs)}"]
     for o in outputs:
         if o[0] == "D":
@@ -32,6 +33,12 @@ def program_text(*, mode="detectors", nx=1, nf=0, nr=0, nmeas=0, ndet=0, nobs=0,
         L.append(f"K {len(sigs)} " + " ".join(str(t) for t in thr))
         for s in sigs:
             L.append(f"S {hexw(s)}")
+    if groups is None:
+        L.append("noise 0 0")
+    else:
+        L.append(f"noise 1 {len(groups)}")
+        for Q, members in groups:
+            L.append(f"G {Q} {len(members)} " + " ".join(str(c) for c in members))
     L.append(f"tables {len(tables)}")
     for terms in tables:
         L.append(f"T {len(terms)}")

@@ -80,17 +80,23 @@ def test_batch_matches_single_launches(tmp_path, autotune):
                         np.testing.assert_array_equal(a, c)
     finally:
         T.tsim_batch_free(batch)
-    # direct oracle check of two members
-    for k in (len(progs) - 1, len(progs) - 2):
+    # direct oracle check of every member, the random programs included: the
+    # first 256 shots of each and the last 64 (the ragged end of its items)
+    for k in range(len(progs)):
         path = str(tmp_path / f"b{k}.prog")
         progs[k].save(path)
-        o = OracleProgram(path).sample(seeds[k], offs[k], shots[k])
+        orc = OracleProgram(path)
         g = _np(got[k])
-        if g[1] is not None:
-            np.testing.assert_array_equal(g[1].view(np.uint64), o["det"])
-        if g[2] is not None:
-            np.testing.assert_array_equal(g[2].view(np.uint64), o["obs"])
-        np.testing.assert_array_equal(g[3], o["accept"])
+        n = shots[k]
+        for lo, hi in ((0, min(n, 256)), (max(0, n - 64), n)):
+            o = orc.sample(seeds[k], offs[k] + lo, hi - lo)
+            if g[0] is not None:
+                np.testing.assert_array_equal(g[0][lo:hi].view(np.uint64), o["meas"])
+            if g[1] is not None:
+                np.testing.assert_array_equal(g[1][lo:hi].view(np.uint64), o["det"])
+            if g[2] is not None:
+                np.testing.assert_array_equal(g[2][lo:hi].view(np.uint64), o["obs"])
+            np.testing.assert_array_equal(g[3][lo:hi], o["accept"])
 
 
 def test_simple_batch_entry_point():

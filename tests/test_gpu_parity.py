@@ -51,9 +51,11 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("noise", [0, 1])  # one word per channel / geometric gaps
 @pytest.mark.parametrize("name,text,mode", CASES, ids=[c[0] for c in CASES])
-def test_small_programs_bit_exact(tmp_path, name, text, mode):
+def test_small_programs_bit_exact(tmp_path, name, text, mode, noise):
     prog = T.Program(text, mode=mode)
+    prog.set_noise_sampling(noise)
     path = str(tmp_path / "p.prog")
     prog.save(path)
     _compare(prog, path, 3001, seed=11, offset=(1 << 32) - 1000)  # ragged, crosses 2^32
@@ -67,16 +69,18 @@ def test_random_circuits_bit_exact(tmp_path, seed):
     if mode == T.MODE_DETECTORS:
         text += "\nDETECTOR rec[-1] rec[-2]\nDETECTOR rec[-3]\nOBSERVABLE_INCLUDE(0) rec[-1]\nOBSERVABLE_INCLUDE(1) rec[-2]"
     prog = T.Program(text, mode=mode)
+    prog.set_noise_sampling(seed % 3 == 0)
     path = str(tmp_path / "p.prog")
     prog.save(path)
     _compare(prog, path, 1537, seed=seed, offset=seed * 7919)
 
 
-@pytest.mark.parametrize("p", [5e-4, 1e-3, 2e-3])
-def test_config2_full_size_sampled_shots(tmp_path, p):
+@pytest.mark.parametrize("p,noise", [(5e-4, 1), (1e-3, 1), (2e-3, 1), (2e-3, 0)])
+def test_config2_full_size_sampled_shots(tmp_path, p, noise):
     # the benchmark's launch: 10^6 shots per p in one call; check 256 shots
     # spread over the whole launch against the oracle, one shot at a time
     prog = T.Program(Wk.config2_circuit(p=p))
+    prog.set_noise_sampling(noise)
     path = str(tmp_path / "c2.prog")
     prog.save(path)
     shots, seed = 1_000_000, 0

@@ -1,5 +1,9 @@
 """tsim_sample_noalloc -- sampling for callers that cannot allocate device
-memory -- must produce exactly the records of tsim_sample.
+memory (code inside an allocator or memory pool it does not own, or a host
+that carved up device memory in advance) -- must produce exactly the records
+of tsim_sample, in both kernel variants (per-thread tables and bit-sliced
+warp tables), and must refuse programs whose tables exceed its fixed array
+without writing any output.
 
 Kept in a file that pytest collects last, so that a run stopping at the first
 failure has already run every other test.  It must pass on its own in a
@@ -63,3 +67,36 @@ def test_noalloc_matches_tsim_sample_on_consecutive_calls():
     for a, b in zip(want[0], again):
         if a is not None:
             np.testing.assert_array_equal(a, b)
+
+
+def test_noalloc_sliced_tables_and_size_limit():
+    # a small program forced into the bit-sliced warp layout (tables read with
+    # 16-byte loads from the static array), twice in a row
+    prog = T.Program(WORKED_EXAMPLE)
+    prog.set_table_layout(0, 0, 16)
+    assert any(prog.device_table_layout(t)[0] == 2 for t in range(prog.info["num_tables"]))
+    shots, seed, off = 3001, 23, 1 << 32
+    want = _call("tsim_sample", prog, shots, seed, off, _buffers(prog.info, shots))
+    for _ in range(2):
+        got = _call("tsim_sample_noalloc", prog, shots, seed, off, _buffers(prog.info, shots))
+        for a, b in zip(want, got):
+            if a is not None:
+                np.testing.assert_array_equal(a, b)
+    # the colour-code program: its packed tables (about 6.6 MB) exceed the
+    # array, so the call is refused before any output is written
+    big = T.Program(Wk.config3_circuit())
+    assert big.device_bytes() > (4 << 20)
+    bufs = _buffers(big.info, 64)
+    for t in bufs:
+        if t is not None:
+            t.fill_(0x5A)
+    lib = T.load_library()
+    ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    rc = lib.tsim_sample_noalloc(ctypes.c_void_p(big.h), ctypes.c_uint64(64), ctypes.c_uint64(1),
+                                 ctypes.c_uint64(0), *[ptr(t) for t in bufs], None)
+    assert rc == 7, lib.tsim_last_error().decode()   # TSIM_ERR_ARG
+    assert b"exceed" in lib.tsim_last_error()
+    T.tsim_sync()
+    for t in bufs:
+        if t is not None:
+            assert bool((t.view(torch.uint8) == 0x5A).all())
