@@ -49,7 +49,11 @@ def _conj(op, x, z):
                 x[a], x[b] = x[b], x[a]
                 z[a], z[b] = z[b], z[a]
     elif n in ("T", "T_DAG"):
-        raise ValueError("frame propagation needs a Clifford circuit")
+        # T commutes with Z (both diagonal), so a frame without an X part on
+        # the qubit passes unchanged; an X part would leave the Pauli group
+        for q in t:
+            if x[q]:
+                raise ValueError("an X component reaches a T gate: the frame is not a Pauli")
     else:
         raise ValueError(n)
 

@@ -66,7 +66,8 @@ def _cx_layers(faces, anc):
     return layers
 
 
-def surface_code_t_injection(d=3, rounds=3, p=1e-3, rotation=("T",), final_basis="X"):
+def surface_code_t_injection(d=3, rounds=3, p=1e-3, rotation=("T",), final_basis="X", teleport=None,
+                             teleport_after=None):
     """d x d rotated surface-code memory with a magic state injected at a corner.
 
     Round 0 prepares a product state (Li-style injection): data qubits above
@@ -81,7 +82,17 @@ def surface_code_t_injection(d=3, rounds=3, p=1e-3, rotation=("T",), final_basis
     consecutive rounds (first round: faces deterministic on the product state
     only).  The final data measurement is in `final_basis` with Z_ERROR(p) or
     X_ERROR(p) before it; its faces give the last detectors and the matching
-    logical operator is observable 0.  Returns Stim text.
+    logical operator is observable 0.
+    teleport: a second gate sequence, applied to the logical qubit by gate
+    teleportation after round `teleport_after` (default: the middle round):
+    a free ancilla m is prepared in teleport |+>, the joint parity Z_L Z_m is
+    measured through a second free ancilla (CX from every qubit of the
+    logical-Z row and from m), m is measured in X, and the Pauli part of the
+    teleportation correction, Z_L conditioned on that X outcome, is applied by
+    classically controlled CZ gates (the Clifford part is left out, so the
+    logical receives the sequence or its inverse, as the parity says).  The
+    parity measurement commutes with every stabilizer, so all detectors stay
+    deterministic.  Returns Stim text.
     """
     data, faces = rotated_surface_layout(d)
     nd = len(data)
@@ -100,11 +111,15 @@ def surface_code_t_injection(d=3, rounds=3, p=1e-3, rotation=("T",), final_basis
     state.update({q: "+" for q in plus})
     state[inj] = "T"
 
+    tele_done_after = -2
+
     def deterministic_first(f):
         want = "+" if f["kind"] == "X" else "0"
         return all(q is None or state[q] == want for q in f["q"])
 
     nf = len(faces)
+    if teleport is not None and teleport_after is None:
+        teleport_after = max(0, rounds // 2 - 1)
     for r in range(rounds):
         if xa:
             L.append("H " + " ".join(map(str, xa)))
@@ -121,16 +136,38 @@ def surface_code_t_injection(d=3, rounds=3, p=1e-3, rotation=("T",), final_basis
             if r == 0:
                 if deterministic_first(f):
                     L.append(f"DETECTOR {cur}")
+            elif tele_done_after == r - 1:
+                # the teleportation's two measurements sit between the rounds
+                L.append(f"DETECTOR {cur} rec[-{2 * nf + 2 - k}]")
             else:
                 L.append(f"DETECTOR {cur} rec[-{2 * nf - k}]")
+        if teleport is not None and r == teleport_after:
+            m, a = anc[0], anc[1]           # free between rounds (reset by MR)
+            row0 = [data[(0, j)] for j in range(d)]
+            L.append(f"RX {m}")
+            for g in teleport:
+                L.append(f"{g} {m}")
+            L.append(f"DEPOLARIZE1({p}) {m}")
+            for q in row0 + [m]:
+                L.append(f"CX {q} {a}")
+                L.append(f"DEPOLARIZE2({p}) {q} {a}")
+            L.append(f"X_ERROR({p}) {a}")
+            L.append(f"MR {a}")
+            L.append(f"Z_ERROR({p}) {m}")
+            L.append(f"MX {m}")
+            L.append(f"R {m}")
+            for q in row0:
+                L.append(f"CZ rec[-1] {q}")
+            tele_done_after = r
     flip = "X_ERROR" if final_basis == "Z" else "Z_ERROR"
     L.append(f"{flip}({p}) " + " ".join(map(str, range(nd))))
     L.append(("M " if final_basis == "Z" else "MX ") + " ".join(map(str, range(nd))))
+    last_gap = 2 if tele_done_after == rounds - 1 else 0
     for k, f in enumerate(faces):
         if f["kind"] != final_basis:
             continue
         recs = [f"rec[-{nd - q}]" for q in f["q"] if q is not None]
-        recs.append(f"rec[-{nd + nf - k}]")
+        recs.append(f"rec[-{nd + last_gap + nf - k}]")
         L.append("DETECTOR " + " ".join(recs))
     if final_basis == "Z":
         logical = [data[(0, j)] for j in range(d)]
@@ -315,9 +352,13 @@ def config1_circuit(p=1e-3):
 
 
 def config2_circuit(p=1e-3, n_t=16, seed=0):
-    """d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG gates in the
-    rotation that prepares the injected state."""
-    return surface_code_t_injection(d=5, rounds=5, p=p, rotation=t_rotation_sequence(n_t, seed))
+    """d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG gates: two
+    injected logical rotations of n_t/2 T/T_DAG each, the first by the corner
+    injection of round 0, the second by gate teleportation after round 2
+    (Pauli corrections by classically controlled CZ)."""
+    half = n_t // 2
+    return surface_code_t_injection(d=5, rounds=5, p=p, rotation=t_rotation_sequence(half, seed),
+                                    teleport=t_rotation_sequence(n_t - half, seed + 1), teleport_after=2)
 
 
 def config3_circuit(p=1e-3):

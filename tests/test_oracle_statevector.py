@@ -174,3 +174,32 @@ def test_frame_flips_match_state_vector(seed):
             k2 = tuple(b ^ f for b, f in zip(key, fd + fo))
             want[k2] = p
         assert d == want, (j, flips[j])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_frame_flips_through_t_gates_match_state_vector(seed):
+    # A Z error that meets T or T_DAG passes unchanged (T Z T^dag = Z), so the
+    # frame picture still holds on a non-Clifford circuit where every T sees
+    # only Z-type frames: Z_ERROR before the T layer, X_ERROR after it.  The
+    # shifted outcome distribution on the exact state vector must match.
+    rng = random.Random(300 + seed)
+    L = ["RX 0 1 2", "CX 0 1", "Z_ERROR(0.1) 0 1 2"]
+    for q in range(3):
+        L.append(f"{rng.choice(['T', 'T_DAG'])} {q}")
+    L += ["CX 1 2", "H 0", "S 1", "X_ERROR(0.1) 0 2", "CX 2 0", "H 1", "M 0 1 2",
+          "DETECTOR rec[-1]", "DETECTOR rec[-2] rec[-3]", "OBSERVABLE_INCLUDE(0) rec[-1] rec[-2]"]
+    text = "\n".join(L)
+    c = circuit.parse(text)
+    base = statevector.output_distribution(c, [0] * c.num_error_bits, "detectors")
+    flips = frame.detector_flips(c)
+    assert any(any(fd) or any(fo) for fd, fo in flips)
+    for j in range(c.num_error_bits):
+        e = [0] * c.num_error_bits
+        e[j] = 1
+        d = statevector.output_distribution(c, e, "detectors")
+        fd, fo = flips[j]
+        want = {tuple(b ^ f for b, f in zip(key, fd + fo)): p for key, p in base.items()}
+        assert d == want, (j, flips[j])
+    # an X error in front of a T gate is refused rather than propagated
+    with pytest.raises(ValueError):
+        frame.detector_flips(circuit.parse("RX 0\nX_ERROR(0.1) 0\nT 0\nH 0\nM 0\nDETECTOR rec[-1]"))

@@ -89,7 +89,7 @@ def test_noalloc_sliced_tables_and_size_limit():
     bufs = _buffers(big.info, 64)
     for t in bufs:
         if t is not None:
-            t.fill_(0x5A)
+            t.view(torch.uint8).fill_(0x5A)
     lib = T.load_library()
     ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
     rc = lib.tsim_sample_noalloc(ctypes.c_void_p(big.h), ctypes.c_uint64(64), ctypes.c_uint64(1),
