@@ -61,7 +61,8 @@ typedef enum {
 typedef struct tsim_program tsim_program;
 
 enum { TSIM_MODE_DETECTORS = 0, TSIM_MODE_MEASUREMENTS = 1 };
-enum { TSIM_DECOMP_HEURISTIC = 0, TSIM_DECOMP_LEARNED = 1, TSIM_DECOMP_SINGLE_T = 2 };
+enum { TSIM_DECOMP_HEURISTIC = 0, TSIM_DECOMP_LEARNED = 1, TSIM_DECOMP_SINGLE_T = 2, TSIM_DECOMP_PAIRS = 3,
+       TSIM_DECOMP_CAT5 = 4 };
 
 typedef struct {
   int mode;              /* TSIM_MODE_DETECTORS: records are detector + observable bits
@@ -69,9 +70,16 @@ typedef struct {
                             records are the measurement outcomes (plus detectors /
                             observables computed from them by Eq. xor). */
   int decomp;            /* stabilizer decomposition policy (Appendix "Stabilizer
-                            decompositions"): HEURISTIC = pairs of non-Clifford
-                            vertices in ascending order (2 terms per pair, alpha = 0.5),
-                            SINGLE_T = one T-state cut at a time, LEARNED = the three
+                            decompositions"), non-Clifford vertices in ascending order:
+                            CAT5 = the partial Cat5 decomposition (Eq. cat5) on groups
+                            of five (3 terms per group, each keeping one non-Clifford
+                            vertex: alpha = log2(3)/4), BSS pairs (2 terms, alpha = 0.5)
+                            when two to four remain, a T-state cut for the last one;
+                            HEURISTIC (default) = as CAT5, except that the first two are
+                            split as a BSS pair while two consecutive vertices have
+                            phases that cancel (a T gate's ket and bra copies, which
+                            the pair split removes together); PAIRS = BSS pairs only;
+                            SINGLE_T = one T-state cut at a time; LEARNED = the three
                             first cuts the cut-order network ranks best, each followed
                             by the heuristic order, against the heuristic itself
                             (kept only with strictly fewer terms). */

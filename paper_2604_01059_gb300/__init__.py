@@ -22,11 +22,12 @@ __all__ = [
     "tsim_program_set_table_layout", "tsim_program_device_table_layout", "tsim_program_device_output_stats",
     "tsim_selftest_sliced", "tsim_debug_sample", "tsim_program_set_noise_sampling", "tsim_program_noise_info",
     "tsim_program_device_bytes", "load_library",
-    "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T",
+    "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T", "DECOMP_PAIRS",
+    "DECOMP_CAT5",
 ]
 
 MODE_DETECTORS, MODE_MEASUREMENTS = 0, 1
-DECOMP_HEURISTIC, DECOMP_LEARNED, DECOMP_SINGLE_T = 0, 1, 2
+DECOMP_HEURISTIC, DECOMP_LEARNED, DECOMP_SINGLE_T, DECOMP_PAIRS, DECOMP_CAT5 = 0, 1, 2, 3, 4
 
 STATUS = {0: "TSIM_OK", 1: "TSIM_ERR_PARSE", 2: "TSIM_ERR_UNSUPPORTED_GATE", 3: "TSIM_ERR_CHI_BUDGET",
           4: "TSIM_ERR_OVERFLOW_BOUND", 5: "TSIM_ERR_CUDA", 6: "TSIM_ERR_OOM", 7: "TSIM_ERR_ARG",

@@ -63,7 +63,7 @@ tsim_status tsim_compile(const char* text, size_t len, const tsim_compile_opts* 
     o.total_budget = 0;
     if (opts) o = *opts;
     if (o.mode != TSIM_MODE_DETECTORS && o.mode != TSIM_MODE_MEASUREMENTS) tsim::fail(TSIM_ERR_ARG, "bad mode");
-    if (o.decomp < 0 || o.decomp > 2) tsim::fail(TSIM_ERR_ARG, "bad decomposition policy");
+    if (o.decomp < 0 || o.decomp > 4) tsim::fail(TSIM_ERR_ARG, "bad decomposition policy");
     tsim::Program* p = tsim::compile_program(std::string(text, len), o);
     *out = new tsim_program{p};
   });
@@ -488,7 +488,7 @@ tsim_status tsim_selftest_rules(uint64_t seed, int iterations) {
     for (int it = 0; it < iterations; ++it) {
       const size_t np = 1 + rng() % 4;
       tsim::Graph g(np);
-      int nv = 1 + (int)(rng() % 7);
+      int nv = 1 + (int)(rng() % 11);  // up to 11: groups of five odd spiders (Cat5) occur
       for (int v = 0; v < nv; ++v) {
         int l = (int)(rng() % 8);
         g.add_var(l);
@@ -521,11 +521,11 @@ tsim_status tsim_selftest_rules(uint64_t seed, int iterations) {
                                               std::to_string(it));
         }
       };
-      for (int policy : {0, 2}) {
+      for (int policy : {0, 4, 3, 2}) {
         std::vector<tsim::Term> terms;
         tsim::DecompStats st;
         tsim::decompose(g, policy, terms, st);
-        check(terms, policy == 0 ? "pairs" : "single cuts");
+        check(terms, policy == 0 ? "heuristic" : policy == 4 ? "cat5" : policy == 3 ? "pairs" : "single cuts");
       }
       {
         // a score-ordered cut sequence (random scores, a forced first cut)

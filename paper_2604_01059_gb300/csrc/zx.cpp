@@ -410,6 +410,42 @@ struct Decomposer {
     out->push_back(g.as_term());
   }
 
+  // Partial Cat5 decomposition (Appendix "Stabilizer decompositions", Eq.
+  // cat5) of five odd spiders z_0..z_4, at theta = pi/4, in path-sum form.
+  // Each spider's weight is w^(lam_k z_k) = w^(z_k) w^((lam_k - 1) z_k); the
+  // product of the five w^(z_k), a function of the Hamming weight k = |z|,
+  // equals  2 A + (w^3 / sqrt2^3) B + (w^5 / sqrt2^3) C  with
+  //   A = [k = 0] + w^5 [k = 5]                  (the five spiders fused),
+  //   B = sum_{c,y} (-1)^(c k + c y) w^(-y)      (= 2 for even k, 2 w^-1 odd),
+  //   C = i^k sum_{c,y} (-1)^(c k + c y) w^(y)   (= 2 i^k for even k, 2 w i^k odd),
+  // i.e. the paper's three terms with coefficients 1 - e^(4i theta) = 2,
+  // 2 e^(3i theta) cos(theta) and 2 e^(3i theta) i sin(theta) up to the
+  // normalisation of its Hadamard edges.  Every branch keeps one odd spider
+  // (the fused z_0, or y), so five become one at three terms: growth
+  // 2^(alpha T) with alpha = log2(3) / 4.
+  void cat5(Graph& g, const int* v, int depth) {
+    {  // 2 A: z_1..z_4 fused into z_0, whose phase becomes the sum of the five
+      Graph h = g;
+      for (int k = 1; k < 5; ++k) h.substitute(v[k], form_var(g.np, v[0]));
+      h.s2 += 2;
+      run(h, depth + 1);
+    }
+    for (int br = 0; br < 2; ++br) {
+      // B: lam_k - 1, new c (phase 0) joined to every z_k and to y (phase -pi/4);
+      // C: lam_k + 1 (the i^(z_k)), y with phase +pi/4
+      Graph h = g;
+      const int dl = br == 0 ? 7 : 1;
+      for (int k = 0; k < 5; ++k) h.lam[(size_t)v[k]] = (h.lam[(size_t)v[k]] + dl) & 7;
+      const int c = h.add_var(0);
+      const int y = h.add_var(br == 0 ? 7 : 1);
+      for (int k = 0; k < 5; ++k) h.toggle(c, v[k]);
+      h.toggle(c, y);
+      h.s2 -= 3;
+      h.ph = (h.ph + (br == 0 ? 3 : 5)) & 7;
+      run(h, depth + 1);
+    }
+  }
+
   void run(Graph& g, int depth) {
     // branches that vanish are pruned without a term; bound the search too
     if (st->budget && ++st->nodes > 64 * st->budget)
@@ -437,6 +473,19 @@ struct Decomposer {
     };
     if (first >= 0 || (policy == 1 && scores)) {
       std::stable_sort(odd.begin(), odd.end(), [&](int a, int b) { return score(a) < score(b); });
+    }
+    // Cat5 (policy 4 always; the heuristic only when no pair of consecutive
+    // odd spiders has phases that cancel, lam_x + lam_y = 0 mod 8: such a
+    // pair -- typically a T gate's ket and bra copies in the doubled diagram
+    // -- fuses away in the pair split, which then beats Cat5 by far)
+    if ((policy == 0 || policy == 1 || policy == 4) && odd.size() >= 5) {
+      bool cancelling = false;
+      for (size_t i = 0; policy != 4 && i + 1 < odd.size() && !cancelling; ++i)
+        cancelling = ((g.lam[(size_t)odd[i]] + g.lam[(size_t)odd[i + 1]]) & 7) == 0;
+      if (!cancelling) {
+        cat5(g, odd.data(), depth);
+        return;
+      }
     }
     if (policy == 2 || odd.size() == 1) {
       int v = odd[0];

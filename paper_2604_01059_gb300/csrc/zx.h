@@ -111,10 +111,15 @@ struct DecompStats {
 };
 
 // Decompose into Clifford terms (Appendix "Stabilizer decompositions").
-// policy: 0 = pairs of odd spiders in ascending id (2 terms per pair),
-// 2 = single cuts, 1 = pairs in ascending `scores[uid]` (a learned cut order;
-// spiders without a score go last).  `first` >= 0 forces the spider with that
-// uid into the first cut.  Every order gives the same sum.
+// policy: 0 = the heuristic: odd spiders in ascending id; the first two are
+// split as a BSS pair (2 terms) while some two consecutive ones have phases
+// that cancel (lam sum = 0 mod 8), otherwise Cat5 takes the first five (3
+// terms, one odd spider left per term); pairs for two to four, a single cut
+// for the last; 4 = Cat5 on the first five whenever five remain; 3 = pairs
+// only; 2 = single cuts; 1 = as 0 with the spiders in ascending
+// `scores[uid]` (a learned cut order; spiders without a score go last).
+// `first` >= 0 forces the spider with that uid into the first cut.  Every
+// order and policy gives the same sum.
 void decompose(Graph g, int policy, std::vector<Term>& out, DecompStats& st,
                const std::vector<double>* scores = nullptr, int first = -1);
 

@@ -249,9 +249,25 @@ def test_no_channel_reduction_same_semantics(tmp_path):
     check_program(REPETITION, T.MODE_DETECTORS, tmp_path, max_e=24, reduction=False)
 
 
-@pytest.mark.parametrize("decomp", [T.DECOMP_SINGLE_T, T.DECOMP_HEURISTIC])
+@pytest.mark.parametrize("decomp", [T.DECOMP_SINGLE_T, T.DECOMP_HEURISTIC, T.DECOMP_PAIRS, T.DECOMP_CAT5])
 def test_decomposition_policy_invariance(tmp_path, decomp):
     check_program(WORKED_EXAMPLE, T.MODE_DETECTORS, tmp_path, max_e=12, decomp=decomp)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_cat5_groups_exact_against_state_vector(tmp_path, seed):
+    # three T gates on entangled qubits: six odd spiders in the doubled
+    # diagram, so Cat5 (Eq. cat5) takes a group of five; every marginal must
+    # still equal the state-vector probability exactly, as with pairs
+    rng = random.Random(4000 + seed)
+    L = ["RX 0 1 2", "CX 0 1", "CZ 1 2"]
+    for q in range(3):
+        L.append(f"{rng.choice(['T', 'T_DAG'])} {q}")
+        L.append(f"{rng.choice(['H', 'SQRT_X'])} {q}")
+    L += ["CX 2 0", "DEPOLARIZE1(0.05) 0 1", "T 1", "H 1", "X_ERROR(0.04) 2", "M 0 1 2"]
+    text = "\n".join(L)
+    for decomp in (T.DECOMP_CAT5, T.DECOMP_PAIRS):
+        check_program(text, T.MODE_MEASUREMENTS, tmp_path, max_e=8, seed=seed, decomp=decomp)
 
 
 def _random_circuit(rng, nq, depth, tcount):
