@@ -1,22 +1,30 @@
-"""Benchmark: shots/s and Z[w] term-evals/s of the GB300 per-shot sampler.
+"""Benchmark: shots/s and Z[w] term-evals/s of the GB300 per-shot sampler,
+learned + batched against the plain GPU form, at identical records.
 
-Workload (the configuration the headline metric is quoted on): d=5 rotated
-surface code, 49 qubits, 5 syndrome rounds, 16 T/T_DAG gates in the injected
-rotation, depolarising p in {5e-4, 1e-3, 2e-3}, 10^6 shots per p, detector
-sampling with bit-packed uint64 records.  One step = one pass of the whole
-hot path (noise, f, detectors, exact marginals, Algorithm 1, records) over
-10^6 shots for each of the three p.
+Headline workload (the line's `value`): the batched launch -- 256 seeded
+random noisy Clifford+T mirror circuits of uneven size (20-60 qubits, depth
+20-100, 8-40 T/T_DAG, two-qubit density 0.3, depolarising p in U[1e-4,
+3e-3]) with shot counts log-uniform in [1e3, 1e6].  One step = one pass of
+the whole hot path (noise, f = T e, detectors, exact marginals, Algorithm 1,
+records) over every shot of every program.
 
 Two forms are timed on the same GPU and must write identical records:
   value  learned + batched: programs compiled with the learned cut order (the
-         committed network weights; heuristic order when they are absent), all
-         programs in one persistent launch replayed from a CUDA graph;
+         committed network weights; heuristic order when they are absent),
+         all programs in persistent launches replayed from a CUDA graph, the
+         launch shapes picked by the autotuner;
   plain  heuristic cut order, one tsim_sample launch per program.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+The same line reports, each with its own timing, roofline and CPU baseline,
+the d=5 surface code with two injected logical rotations (3 x 10^6 shots)
+and the d=3 colour-code T-check (10^7 shots, the term-evaluation workload).
 
-Under torchrun (N > 1) every rank samples its own shot range (weak scaling,
-no collective on the data path); rank 0 prints one JSON line.
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+                    [--only cfg2|cfg3|cfg4] [--profile]
+
+Under torchrun (N > 1) every rank samples its own shot range of every
+program (weak scaling, no collective on the data path); timings take the
+maximum over ranks and rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -32,42 +40,42 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-P_VALUES = (5e-4, 1e-3, 2e-3)
-SHOTS_PER_P = 1_000_000
 SEED = 0
 METRIC = "shots/sec and Z[w] term-evals/sec, learned+batched vs plain GPU form, bit-exact"
+HEADLINE = "cfg4"
 WORKLOADS = {
-    "cfg2": "d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG, p in {5e-4,1e-3,2e-3}, 1e6 shots per p",
-    "cfg3": "d=3 triangular colour-code T-check, 19 qubits, 42 T/T_DAG, 3 check rounds, p=1e-3, postselected, 1e7 shots",
+    "cfg2": "d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG (two injected logical rotations, the "
+            "second by gate teleportation), p in {5e-4,1e-3,2e-3}, 1e6 shots per p",
+    "cfg3": "d=3 triangular colour-code T-check, 19 qubits, 42 T/T_DAG, 3 check rounds, p=1e-3, postselected, "
+            "1e7 shots",
     "cfg4": "batched launch: 256 seeded random noisy Clifford+T mirror circuits (20-60 qubits, depth 20-100, "
             "8-40 T/T_DAG, 2-qubit density 0.3, p in U[1e-4,3e-3]), shots log-uniform in [1e3,1e6], "
-            "one persistent launch replayed from a CUDA graph, autotuned shot block",
+            "persistent launches replayed from a CUDA graph, autotuned shot block and residency",
 }
+CFG2_P = (5e-4, 1e-3, 2e-3)
 CFG4_TABLE_BUDGET = 2048     # terms per marginal table
 CFG4_PROGRAM_BUDGET = 8192   # terms per program
-WORKLOAD = WORKLOADS["cfg2"]
+H2D_NOTE = ("0: a sampling step has no per-step input beyond scalars (seed, shot offset); each program's "
+            "tables are uploaded once, before the timed region")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: about 0.2 s per form)")
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=8.0, help="bound on the oracle baseline's CPU work")
-    ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
-    ap.add_argument("--shots", type=int, default=None, help="shots per program per step")
-    ap.add_argument("--profile", action="store_true", help="only run two launches per program (for ncu)")
-    args = ap.parse_args()
-    global WORKLOAD, SHOTS_PER_P
-    WORKLOAD = WORKLOADS[args.workload]
-    if args.workload == "cfg3":
-        SHOTS_PER_P = 10_000_000
-    if args.shots:
-        SHOTS_PER_P = args.shots
-    if args.steps is None:
-        args.steps = {"cfg2": 100, "cfg3": 3, "cfg4": 20}[args.workload]
-    return args
+    ap.add_argument("--cpu-seconds", type=float, default=6.0, help="bound on each oracle baseline's CPU work")
+    ap.add_argument("--only", default=None, choices=sorted(WORKLOADS), help="one workload (it becomes the value)")
+    ap.add_argument("--profile", action="store_true", help="only two plain launches per program (for ncu)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
 
 
 def shard_offsets(rank, shots):
@@ -87,105 +95,185 @@ def max_over_ranks(x, dist=None, device="cpu"):
     return float(t.item())
 
 
-def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
-
-
-WORKLOAD_NAME = "cfg2"
-SHOTS_LIST = None
-
-
+# ------------------------------------------------------------------ workloads
 def cut_model():
     """The committed cut-order network weights, or None."""
     from paper_2604_01059_gb300.train_cut_order import load_weights
     return load_weights()
 
 
-def config4_programs(n=256):
-    """Compile the batched workload in parallel host threads; circuits over the
-    term budgets are skipped and the next seeds drawn (deterministic order).
-    Returns (program, shots, circuit text) triples."""
+def config4_programs(n=256, decomp=0, texts=None):
+    """The batched workload, compiled in parallel host threads.  Circuits over
+    the term budgets are skipped and the next seeds drawn (deterministic
+    order); `texts` recompiles a chosen list.  Returns (program, shots, text)."""
     from concurrent.futures import ThreadPoolExecutor
 
     import paper_2604_01059_gb300 as T
     from paper_2604_01059_gb300 import workloads as Wk
-    pool = Wk.config4_batch(n=4 * n, seed=0)
+    pool = Wk.config4_batch(n=4 * n, seed=0) if texts is None else texts
 
     def build(item):
         txt, shots = item
         try:
-            p = T.Program(txt, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET)
+            p = T.Program(txt, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
         except T.TsimError as e:
             if e.code == 3:
                 return None
             raise
         return (p, shots, txt) if p.info["total_terms"] <= CFG4_PROGRAM_BUDGET else None
 
+    # a sliding window of compilations in pool order: results are taken in
+    # order (the first n that fit the budgets), while a slow circuit does not
+    # hold up the ones behind it
     out = []
-    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-        for k in range(0, len(pool), 64):
-            for r in ex.map(build, pool[k:k + 64]):
-                if r is not None and len(out) < n:
-                    out.append(r)
-            if len(out) >= n:
-                break
+    workers = os.cpu_count() or 1
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futs, nxt = [], 0
+        while len(out) < n and (futs or nxt < len(pool)):
+            while nxt < len(pool) and len(futs) < 4 * workers:
+                futs.append(ex.submit(build, pool[nxt]))
+                nxt += 1
+            r = futs.pop(0).result()
+            if r is not None:
+                out.append(r)
+        for f in futs:
+            f.cancel()
     return out
 
 
-CFG4_TEXTS = None
+class Workload:
+    """The programs of one configuration, in the plain (heuristic) and the
+    learned cut order, and their shot counts."""
 
-
-def programs(decomp=0):
-    """The workload's programs.  The batched workload's circuits are selected
-    once with the heuristic order; another order compiles the same circuits
-    (it never has more terms, so they stay within the budgets)."""
-    import paper_2604_01059_gb300 as T
-    from paper_2604_01059_gb300 import workloads as Wk
-    global SHOTS_LIST, CFG4_TEXTS
-    if WORKLOAD_NAME == "cfg3":
-        return [T.Program(Wk.config3_circuit(p=1e-3), decomp=decomp)]
-    if WORKLOAD_NAME == "cfg4":
-        if CFG4_TEXTS is None or decomp == 0:
+    def __init__(self, name):
+        import paper_2604_01059_gb300 as T
+        from paper_2604_01059_gb300 import workloads as Wk
+        self.name = name
+        t0 = time.perf_counter()
+        if name == "cfg4":
             pr = config4_programs()
-            SHOTS_LIST = [s for _, s, _ in pr]
-            CFG4_TEXTS = [t for _, _, t in pr]
-            if decomp == 0:
-                return [p for p, _, _ in pr]
-        return [T.Program(t, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
-                for t in CFG4_TEXTS]
-    return [T.Program(Wk.config2_circuit(p=p), decomp=decomp) for p in P_VALUES]
+            self.plain = [p for p, _, _ in pr]
+            self.shots = [s for _, s, _ in pr]
+            self.texts = [(t, s) for _, s, t in pr]
+        elif name == "cfg3":
+            self.texts = [(Wk.config3_circuit(p=1e-3), 10_000_000)]
+        else:
+            self.texts = [(Wk.config2_circuit(p=p), 1_000_000) for p in CFG2_P]
+        if name != "cfg4":
+            self.plain = [T.Program(t) for t, _ in self.texts]
+            self.shots = [s for _, s in self.texts]
+        self.compile_s = {"heuristic": time.perf_counter() - t0}
+        t0 = time.perf_counter()
+        self.learned, self.cut = self._learned()
+        self.compile_s["learned"] = time.perf_counter() - t0
+
+    def _compile(self, decomp):
+        import paper_2604_01059_gb300 as T
+        if self.name == "cfg4":
+            return [T.Program(t, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
+                    for t, _ in self.texts]
+        return [T.Program(t, decomp=decomp) for t, _ in self.texts]
+
+    def _learned(self):
+        import paper_2604_01059_gb300 as T
+        w = cut_model()
+        if w is None:
+            return self._compile(T.DECOMP_HEURISTIC), {"cut_order": "heuristic (no trained weights)"}
+        before = T.tsim_cut_policy_stats()
+        T.tsim_cut_model_set(w)
+        try:
+            progs = self._compile(T.DECOMP_LEARNED)
+        finally:
+            T.tsim_cut_model_set(None)
+        d = [a - b for a, b in zip(T.tsim_cut_policy_stats(), before)]
+        return progs, {"cut_order": "learned (GNN scores, heuristic as fallback and judge)", "scorer_calls": d[0],
+                       "scored": d[1], "marginals_learned_kept": d[2], "marginals_heuristic_kept": d[3]}
 
 
-def learned_programs():
-    """Programs in the learned cut order, with the order's bookkeeping."""
-    import paper_2604_01059_gb300 as T
-    w = cut_model()
-    if w is None:
-        return programs(), {"cut_order": "heuristic (no trained weights)"}
-    before = T.tsim_cut_policy_stats()
-    T.tsim_cut_model_set(w)
-    try:
-        progs = programs(decomp=T.DECOMP_LEARNED)
-    finally:
-        T.tsim_cut_model_set(None)
-    after = T.tsim_cut_policy_stats()
-    d = [a - b for a, b in zip(after, before)]
-    return progs, {"cut_order": "learned (GNN scores, heuristic as fallback and judge)",
-                   "scorer_calls": d[0], "scored": d[1], "marginals_learned_kept": d[2],
-                   "marginals_heuristic_kept": d[3]}
+# ------------------------------------------------------------------ counting
+def device_terms_per_shot(prog):
+    """Terms the device evaluates for one shot: every table a shot evaluates
+    (each chain's normalisation and one table per random output), counted
+    after terms with equal factor lists are merged into one class (the
+    kernel evaluates each class once)."""
+    return sum(prog.device_table_stats(t)[0] for t in range(prog.info["num_tables"]))
 
 
-def shots_of(k):
-    return SHOTS_LIST[k] if SHOTS_LIST else SHOTS_PER_P
-
-
-def term_evals_per_shot(prog):
-    """Sum over the marginals one shot evaluates of their stabilizer terms
-    (normalisation of every chain + one table per random output)."""
+def premerge_terms_per_shot(prog):
+    """Stabilizer terms of the same tables before merging."""
     return sum(prog.table_terms())
+
+
+def kernel_int_ops(prog):
+    """Integer operations one shot needs in the fused sampling kernel, counted
+    on the packed device tables it evaluates:
+      noise, one word per channel: ceil(C/4) Philox4x32-10 calls x 10 rounds x
+               (2 wide multiplies + 2 three-input XORs) = 40 per call, plus one
+               compare per channel;
+      noise, geometric gaps: 10 per word (a quarter Philox call) + 4 (compare,
+               table load, branch) for its expected words, + 12 per expected
+               candidate (map, threshold walk, signature XOR);
+      outputs: 3 per deterministic output outside runs, 6 per run of
+               single-bit outputs (+4 per further 64 of its bits), 60 per
+               Bernoulli decision;
+      tables:  per distinct parity 2W+2 (AND, XOR, popcount, insert), per merged
+               term 12 (+5 per factor: two bit extracts, index, lookup, add);
+               bit-sliced tables: the lane-operations of one warp for its 32
+               shots, as the library counts them, divided by 32."""
+    i = prog.info
+    C = i["num_channels"]
+    W = next(p for p in (1, 2, 4, 8, 16, 32) if i["x_words"] <= p)
+    nz = prog.noise_info()
+    if nz["mode"] == 1:
+        words = nz["words_geometric_mode"]
+        cand = max(0.0, (words - nz["groups"]) / 2)
+        ops = 14 * words + 12 * cand
+    else:
+        ops = 40 * ((C + 3) // 4) + C
+    entries, runs, run_outputs = prog.device_output_stats()
+    ops += 3 * (i["num_outputs"] - i["num_random"] - run_outputs) + 60 * i["num_random"]
+    ops += 6 * runs + 4 * (run_outputs // 64)
+    for t in range(i["num_tables"]):
+        layout = prog.device_table_layout(t)
+        if layout[0] == 2:
+            ops += layout[4] / 32
+            continue
+        classes, factors, parities = prog.device_table_stats(t)
+        ops += parities * (2 * W + 2) + 12 * classes + 5 * factors
+    return ops
+
+
+def int_peak(sm_mhz=None):
+    """Integer-issue peak of the current GPU: SMs (read from the device) x 4
+    sub-partitions x 16 INT32 lanes x the maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    clk = sm_mhz or measured_peaks().get("sm_max_mhz") or 2070.0
+    return sms * 4 * 16 * clk * 1e6, sms, clk
+
+
+def int_peaks_measured():
+    import paper_2604_01059_gb300 as T
+    names = ["lop3", "imad", "imad_wide", "popc"]
+    return {n: T.tsim_measure_int_peak(k) / 1e12 for k, n in enumerate(names)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def launches_per_step(progs, shots, binfo):
+    """Kernel launches one replay of the batch graph makes: one per program in
+    the one-launch-per-program form; otherwise one persistent launch per group
+    (programs without and with bit-sliced tables)."""
+    live = [p for p, n in zip(progs, shots) if n > 0]
+    if binfo.get("form", 0) == 1:
+        return len(live)
+    sliced = [any(p.device_table_layout(t)[0] == 2 for t in range(p.info["num_tables"])) for p in live]
+    return int(any(sliced)) + int(not all(sliced))
 
 
 class ClockSampler:
@@ -233,24 +321,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
-def measured_peaks():
-    try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        return {}
-
-
-def int_peak_ops(sm_mhz=None):
-    """Integer-issue peak: 152 SMs x 4 SM sub-partitions x 16 INT32 lanes x clock
-    (2070 MHz maximum SM clock)."""
-    clk = 2070.0
-    return 152 * 4 * 16 * clk * 1e6
-
-
+# ------------------------------------------------------------- CPU baseline
 class OracleBench:
     """The oracle's C evaluator on the host cores, on the programs of the
-    workload (at most 16 of them): calibrated once, then timed on bounded
-    samples."""
+    workload (at most 16 of them, spread over the list): calibrated once on
+    one thread, then timed on bounded samples on every core."""
 
     def __init__(self, progs):
         import tempfile
@@ -261,11 +336,12 @@ class OracleBench:
         self.cores = os.cpu_count() or 1
         tmp = tempfile.mkdtemp()
         self.orcs = []
-        for k, p in enumerate(progs[:16]):
-            path = os.path.join(tmp, f"c2_{k}.prog")
+        step = max(1, len(progs) // 16)
+        for k, p in enumerate(progs[::step][:16]):
+            path = os.path.join(tmp, f"w{k}.prog")
             p.save(path)
             self.orcs.append(evaluator.OracleProgram(path))
-        n_cal = 4
+        n_cal = 1
         while True:  # per-shot time of one thread
             t0 = time.perf_counter()
             for o in self.orcs:
@@ -275,6 +351,7 @@ class OracleBench:
                 break
             n_cal *= 4
         self.per_shot = dt / (n_cal * len(self.orcs))
+        self.cal_shots = n_cal * len(self.orcs)
 
     def run(self, seconds):
         """About `seconds` of oracle work on all cores; shots per second."""
@@ -287,42 +364,13 @@ class OracleBench:
         dt = time.perf_counter() - t0
         shots = chunk * len(jobs)
         return {"value": shots / dt, "unit": "shots/s", "cores": self.cores, "kind": "oracle",
+                "value_1thread": 1.0 / self.per_shot,
                 "sample": f"{shots} shots ({chunk} per thread x {self.cores} threads x {len(self.orcs)} programs) "
-                          f"of the same workload, oracle C evaluator, exact arithmetic"}
+                          f"of the same workload, oracle C evaluator, exact arithmetic; value_1thread: one thread "
+                          f"on {self.cal_shots} shots"}
 
 
-def oracle_baseline(seconds, progs=None):
-    """Time the oracle's C evaluator on a bounded sample of the same workload."""
-    return OracleBench(progs if progs is not None else programs()).run(seconds)
-
-
-def run_reference(args):
-    """The reference arm: the oracle (plain C, exact) on the host cores, on the
-    same programs, each step a bounded sample of the workload (the whole run
-    about --cpu-seconds of oracle work plus one calibration)."""
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return
-    ob = OracleBench(programs())
-    per_step = max(0.05, args.cpu_seconds / max(args.steps, 1))
-    for _ in range(args.warmup):
-        ob.run(0.02)
-    vals = []
-    b = None
-    for _ in range(args.steps):
-        b = ob.run(per_step)
-        vals.append(b["value"])
-    val = statistics.median(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "shots/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
-            "cpu_baseline": {"kind": "oracle", "cores": b["cores"], "sample": b["sample"] + " (per step)",
-                             "value": val},
-            "e2e": {"value": val, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
-
-
+# ------------------------------------------------------------------ GPU arm
 def _outputs(progs, shots):
     import torch
     outs = []
@@ -334,29 +382,20 @@ def _outputs(progs, shots):
     return outs
 
 
-def run_gpu(args):
+def bench_config(wl, steps, args, dist, rank, world, flush, clocks_index):
+    """Time one workload in both forms; returns its result dictionary."""
     import numpy as np
     import torch
 
     import paper_2604_01059_gb300 as T
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    plain_progs = programs()
-    progs, cut = learned_programs()
+    progs, plain_progs, shots = wl.learned, wl.plain, wl.shots
     n = len(progs)
-    assert n == len(plain_progs)
-    shots = [shots_of(k) for k in range(n)]
-    offsets = shard_offsets(rank, shots)  # weak scaling: every rank its own shot range
+    offsets = shard_offsets(rank, shots)
     seeds = [SEED] * n
     stream = torch.cuda.current_stream()
     outs = _outputs(progs, shots)
     plain_outs = _outputs(plain_progs, shots)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def plain_step():
         for k, (p, (d, o, a)) in enumerate(zip(plain_progs, plain_outs)):
@@ -380,7 +419,7 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(step_fn, steps):
+    def timed(step_fn):
         total = 0.0
         for _ in range(steps):
             flush.fill_(1)  # evict L2 between timed iterations
@@ -394,24 +433,22 @@ def run_gpu(args):
         T.tsim_sync(stream)
         return max_over_ranks(total, dist, "cuda")
 
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
-    ids = [v.strip() for v in vis.split(",") if v.strip()]
-    clocks = ClockSampler(ids[local] if local < len(ids) else str(local))
+    clocks = ClockSampler(clocks_index)
     clocks.start()
-    batch_ms = timed(batch_step, args.steps)
-    plain_ms = timed(plain_step, args.steps)
+    batch_ms = timed(batch_step)
+    plain_ms = timed(plain_step)
     clk = clocks.stop()
     T.tsim_batch_free(batch)
-    # both forms wrote every record of the step: they must agree bit for bit
     identical = all(torch.equal(a[:, :p.info["det_words"]], b[:, :p.info["det_words"]]) and
                     torch.equal(x[:, :p.info["obs_words"]], y[:, :p.info["obs_words"]]) and torch.equal(u, v)
                     for p, (a, x, u), (b, y, v) in zip(progs, outs, plain_outs))
+    del outs, plain_outs
     shots_step = sum(shots) * world
-    value = shots_step * args.steps / (batch_ms / 1e3)
-    plain = shots_step * args.steps / (plain_ms / 1e3)
-    terms_step = sum(term_evals_per_shot(p) * ns for p, ns in zip(progs, shots)) * world
-    plain_terms_step = sum(term_evals_per_shot(p) * ns for p, ns in zip(plain_progs, shots)) * world
-    tev = terms_step * args.steps / (batch_ms / 1e3)
+    value = shots_step * steps / (batch_ms / 1e3)
+    plain = shots_step * steps / (plain_ms / 1e3)
+    dev_terms = sum(device_terms_per_shot(p) * ns for p, ns in zip(progs, shots)) * world
+    pre_terms = sum(premerge_terms_per_shot(p) * ns for p, ns in zip(progs, shots)) * world
+    plain_dev_terms = sum(device_terms_per_shot(p) * ns for p, ns in zip(plain_progs, shots)) * world
 
     # end to end through the host-buffer entry point: copies inside the timed
     # region, into page-locked host buffers
@@ -432,7 +469,7 @@ def run_gpu(args):
                                o if i["obs_words"] else None, a, stream)
 
     e2e_step()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(steps, 3))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -441,116 +478,171 @@ def run_gpu(args):
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = shots_step * e2e_steps / e2e_s
     d2h = sum(ns * (p.info["det_words"] * 8 + p.info["obs_words"] * 8 + 1) for p, ns in zip(progs, shots))
+    del hbuf
 
-    # roofline of the dominant kernel: the persistent batched sampling kernel
+    # roofline of the dominant kernel (the batched launch's kernels)
     ops = sum(kernel_int_ops(p) * ns for p, ns in zip(progs, shots))
-    peak = int_peak_ops()
-    achieved = ops / (batch_ms / args.steps / 1e3)
+    peak, sms, clk_mhz = int_peak()
+    achieved = ops / (batch_ms / steps / 1e3)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
             "frac": achieved / peak, "traffic": None,
-            "kernel": ("k_batch (persistent kernel over all programs, graph replay)" if binfo.get("form", 0) == 0
+            "kernel": ("k_batch (persistent kernels over all programs, graph replay)" if binfo.get("form", 0) == 0
                        else "k_sample (each program's launch, graph replay)"),
             "ops_per_shot": ops / sum(shots),
-            "peak_source": "derived: 152 SMs x 4 sub-partitions x 16 INT32 lanes x 2070 MHz",
-            "measured_issue_tops": int_peaks_measured()}
-    base = oracle_baseline(args.cpu_seconds, progs) if (rank == 0 and world == 1 and args.cpu_seconds > 0) else None
+            "peak_source": f"derived: {sms} SMs (from the device) x 4 sub-partitions x 16 INT32 lanes x "
+                           f"{clk_mhz:.0f} MHz (maximum SM clock)"}
+    base = None
+    if rank == 0 and world == 1 and args.cpu_seconds > 0:
+        base = OracleBench(progs).run(args.cpu_seconds)
+    noise = [p.noise_info() for p in progs]
+    return {
+        "workload": WORKLOADS[wl.name], "value": value, "unit": "shots/s", "ms_per_step": batch_ms / steps,
+        "steps": steps, "programs": n, "shots_per_step": shots_step,
+        "term_evals_per_s": dev_terms * steps / (batch_ms / 1e3),
+        "term_evals_note": "terms the device evaluates: every table of a shot, terms with equal factor lists "
+                           "merged into one class",
+        "premerge_term_evals_per_s": pre_terms * steps / (batch_ms / 1e3),
+        "device_terms_per_shot": dev_terms / max(shots_step, 1),
+        "premerge_terms_per_shot": pre_terms / max(shots_step, 1),
+        "terms_all_programs": {"learned": sum(premerge_terms_per_shot(p) for p in progs),
+                               "heuristic": sum(premerge_terms_per_shot(p) for p in plain_progs)},
+        "identical_records": bool(identical),
+        "plain": {"value": plain, "unit": "shots/s", "ms_per_step": plain_ms / steps,
+                  "term_evals_per_s": plain_dev_terms * steps / (plain_ms / 1e3),
+                  "form": "heuristic cut order, one tsim_sample launch per program",
+                  "gpu_launches": steps * sum(1 for s in shots if s > 0)},
+        "speedup_vs_plain": value / plain,
+        "form": "learned cut order + batched launch (CUDA graph, autotuned)", "batch": binfo, "cut": wl.cut,
+        "noise_sampling": {"geometric_programs": sum(1 for z in noise if z["mode"] == 1),
+                           "words_per_shot": sum((z["words_geometric_mode"] if z["mode"] == 1 else
+                                                  z["words_per_channel_mode"]) * ns
+                                                 for z, ns in zip(noise, shots)) / sum(shots)},
+        "compile_s": wl.compile_s,
+        "e2e": {"value": e2e, "unit": "shots/s", "h2d_bytes_per_step": 0, "h2d_note": H2D_NOTE,
+                "d2h_bytes_per_step": d2h,
+                "api": "tsim_sample_host (device staging, records copied to page-locked host memory inside the "
+                       "timed region)"},
+        "gpu_launches": steps * launches_per_step(progs, shots, binfo),
+        "roofline": roof, "clocks": clk, "cpu_baseline": base,
+    }
+
+
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v.strip() for v in vis.split(",") if v.strip()]
+    clocks_index = ids[local] if local < len(ids) else str(local)
+    head = args.only or HEADLINE
+    names = [head] + ([] if args.only else [k for k in ("cfg2", "cfg3") if k != head])
+    res = {}
+    for name in names:
+        wl = Workload(name)
+        steps = args.steps if name == head else (min(args.steps, 5) if name == "cfg3" else args.steps)
+        res[name] = bench_config(wl, steps, args, dist, rank, world, flush, clocks_index)
+        del wl
+    h = res[head]
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": batch_ms / args.steps, "higher_is_better": True,
+        line = {"metric": METRIC, "value": h["value"], "unit": "shots/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (256 MiB write)",
-                           "programs": n, "shots_per_step": shots_step,
-                           "terms_per_shot": [term_evals_per_shot(p) for p in progs][:8],
-                           "plain_terms_per_shot": [term_evals_per_shot(p) for p in plain_progs][:8],
-                           "terms_all_programs": {"learned": sum(term_evals_per_shot(p) for p in progs),
-                                                  "heuristic": sum(term_evals_per_shot(p) for p in plain_progs)},
-                           "channels": [p.info["num_channels"] for p in progs][:8],
-                           "form": "learned cut order + batched persistent launch (CUDA graph)",
-                           "cut": cut, "batch": binfo},
-                "term_evals_per_s": tev,
-                "identical_records": bool(identical),
-                "plain": {"value": plain, "unit": "shots/s", "ms_per_step": plain_ms / args.steps,
-                          "term_evals_per_s": plain_terms_step * args.steps / (plain_ms / 1e3),
-                          "form": "heuristic cut order, one tsim_sample launch per program",
-                          "gpu_launches": args.steps * n},
-                "speedup_vs_plain": value / plain,
-                "e2e": {"value": e2e, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
-                        "api": "tsim_sample_host (device staging, records copied to page-locked host memory inside the timed region)"},
-                "gpu_launches": args.steps * launches_per_step(progs, shots, binfo), "roofline": roof, "clocks": clk,
-                "cpu_baseline": base}
+                "config": {"workload": h["workload"], "l2": "flushed between timed steps (256 MiB write)",
+                           "programs": h["programs"], "shots_per_step": h["shots_per_step"],
+                           "form": h["form"], "cut": h["cut"], "batch": h["batch"],
+                           "terms_all_programs": h["terms_all_programs"], "noise_sampling": h["noise_sampling"],
+                           "compile_s": h["compile_s"]},
+                "term_evals_per_s": h["term_evals_per_s"], "term_evals_note": h["term_evals_note"],
+                "premerge_term_evals_per_s": h["premerge_term_evals_per_s"],
+                "identical_records": h["identical_records"], "plain": h["plain"],
+                "speedup_vs_plain": h["speedup_vs_plain"], "e2e": h["e2e"], "gpu_launches": h["gpu_launches"],
+                "roofline": h["roofline"], "clocks": h["clocks"], "cpu_baseline": h["cpu_baseline"],
+                "measured_issue_tops": int_peaks_measured(),
+                "configs": {k: v for k, v in res.items() if k != head}}
         print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()
 
 
-def launches_per_step(progs, shots, binfo):
-    """Kernel launches one replay of the batch graph makes: one per program in
-    the one-launch-per-program form; otherwise one persistent launch per group
-    (programs without and with bit-sliced tables)."""
-    live = [p for p, n in zip(progs, shots) if n > 0]
-    if binfo.get("form", 0) == 1:
-        return len(live)
-    sliced = [any(p.device_table_layout(t)[0] == 2 for t in range(p.info["num_tables"])) for p in live]
-    return int(any(sliced)) + int(not all(sliced))
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The reference arm: the oracle (plain C, exact) on the host cores, on the
+    headline workload's programs, each step a bounded sample of it (the whole
+    run about --cpu-seconds of oracle work plus one calibration)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    head = args.only or HEADLINE
+    if head == "cfg4":
+        progs = [p for p, _, _ in config4_programs()]
+    else:
+        import paper_2604_01059_gb300 as T
+        from paper_2604_01059_gb300 import workloads as Wk
+        progs = ([T.Program(Wk.config3_circuit(p=1e-3))] if head == "cfg3"
+                 else [T.Program(Wk.config2_circuit(p=p)) for p in CFG2_P])
+    ob = OracleBench(progs)
+    per_step = max(0.05, args.cpu_seconds / max(args.steps, 1))
+    for _ in range(args.warmup):
+        ob.run(0.02)
+    vals = []
+    b = None
+    for _ in range(args.steps):
+        b = ob.run(per_step)
+        vals.append(b["value"])
+    val = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "shots/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[head]},
+            "cpu_baseline": {"kind": "oracle", "cores": b["cores"], "sample": b["sample"] + " (per step)",
+                             "value": val, "value_1thread": b["value_1thread"]},
+            "e2e": {"value": val, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
 
 
-def kernel_int_ops(prog):
-    """Integer operations one shot needs in the fused sampling kernel, counted
-    on the packed device tables it actually evaluates:
-      noise:   ceil(C/4) Philox4x32-10 calls x 10 rounds x (2 wide multiplies
-               + 2 three-input XORs) = 40 per call, plus one compare per channel;
-      outputs: 3 per deterministic output outside runs, 6 per run of
-               single-bit outputs (+4 per further 64 of its bits), 60 per
-               Bernoulli decision;
-      tables:  per distinct parity 2W+2 (AND, XOR, popcount, insert), per merged
-               term 12 (+5 per factor: two bit extracts, index, lookup, add);
-               bit-sliced tables: the lane-operations of one warp for its 32
-               shots, as the library counts them, divided by 32."""
-    i = prog.info
-    C = i["num_channels"]
-    W = next(p for p in (1, 2, 4, 8, 16, 32) if i["x_words"] <= p)
-    ops = 40 * ((C + 3) // 4) + C
-    entries, runs, run_outputs = prog.device_output_stats()
-    ops += 3 * (i["num_outputs"] - i["num_random"] - run_outputs) + 60 * i["num_random"]
-    ops += 6 * runs + 4 * (run_outputs // 64)  # a run: word extracts, shift, merge
-    for t in range(i["num_tables"]):
-        layout = prog.device_table_layout(t)
-        if layout[0] == 2:  # bit-sliced: the library counts one warp's lane-operations for 32 shots
-            ops += layout[4] / 32
-            continue
-        classes, factors, parities = prog.device_table_stats(t)
-        ops += parities * (2 * W + 2) + 12 * classes + 5 * factors
-    return ops
-
-
-def int_peaks_measured():
-    import paper_2604_01059_gb300 as T
-    names = ["lop3", "imad", "imad_wide", "popc"]
-    return {n: T.tsim_measure_int_peak(k) / 1e12 for k, n in enumerate(names)}
-
-
-def run_profile():
-    """Two launches per program of the chosen workload, nothing else."""
+def run_profile(args):
+    """For a profiler: two launches of one workload and nothing else -- each
+    program's own sampling kernel twice (configs 2 and 3), or the batched
+    workload's persistent launches twice (config 4, default launch shape,
+    no autotuning runs)."""
     import torch
 
     import paper_2604_01059_gb300 as T
-    progs = programs()
-    for k, p in enumerate(progs):
-        out = p.sample_torch(shots_of(k), SEED, 0)
-        out = p.sample_torch(shots_of(k), SEED, 0)
-    T.tsim_sync()
+    name = args.only or "cfg2"
+    if name == "cfg4":
+        pr = config4_programs()
+        progs, shots = [p for p, _, _ in pr], [s for _, s, _ in pr]
+        outs = _outputs(progs, shots)
+        batch = T.tsim_batch_create([p.h for p in progs], shots, [SEED] * len(progs), None, None,
+                                    [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs], autotune=0)
+        try:
+            for _ in range(2):
+                T.tsim_batch_launch(batch)
+            T.tsim_sync()
+        finally:
+            T.tsim_batch_free(batch)
+    else:
+        wl = Workload(name)
+        progs = wl.plain
+        for p, ns in zip(wl.plain, wl.shots):
+            p.sample_torch(ns, SEED, 0)
+            p.sample_torch(ns, SEED, 0)
+        T.tsim_sync()
     torch.cuda.synchronize()
-    print(json.dumps({"profile": WORKLOAD, "shots": SHOTS_PER_P, "programs": len(progs)}))
+    print(json.dumps({"profile": WORKLOADS[name], "programs": len(progs)}))
 
 
 def main():
-    global WORKLOAD_NAME
     args = parse()
-    WORKLOAD_NAME = args.workload
     if args.profile:
-        run_profile()
-        return
-    if args.impl == "reference":
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

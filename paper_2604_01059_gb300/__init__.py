@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import threading
 
 from .build import LIB, build as _build
 
@@ -59,13 +60,22 @@ class ProgramInfo(ctypes.Structure):
 
 
 _lib = None
+_lib_lock = threading.Lock()
 
 
 def load_library(path: str | None = None):
-    """Load the native library (building it in-tree if it is absent or stale)."""
+    """Load the native library (building it in-tree if it is absent or stale);
+    safe to call from several threads at once."""
     global _lib
     if _lib is not None:
         return _lib
+    with _lib_lock:
+        if _lib is None:
+            _lib = _load(path)
+    return _lib
+
+
+def _load(path):
     if path is None:
         path = _build() if not os.environ.get("TSIM_NO_BUILD") else LIB
     if not os.path.exists(path):
@@ -132,7 +142,6 @@ def load_library(path: str | None = None):
               "tsim_cut_dataset", "tsim_cut_forward", "tsim_cut_loss_grad", "tsim_cut_adam_step", "tsim_cut_train",
               "tsim_cut_model_set", "tsim_cut_policy_stats"):
         getattr(L, n).restype = ctypes.c_int
-    _lib = L
     return L
 
 

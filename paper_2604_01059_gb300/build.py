@@ -9,6 +9,7 @@ import concurrent.futures as cf
 import os
 import shutil
 import subprocess
+import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
@@ -65,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(max(os.cpu_count() or 1, 1), len(srcs))) as ex:
         objs = list(ex.map(one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = LIB + f".tmp{os.getpid()}.{threading.get_ident()}"
     cmd = [nvcc, "-shared", "-o", tmp, *objs, *ARCH, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -30,7 +30,6 @@ constexpr int NPARAM = OFF_WO + H + 1;
 constexpr int kThreads = 256;
 constexpr int kTile = 32;              // nodes per tile of the dense kernels
 constexpr int kMaxK = 2 * H;           // widest input of a dense layer
-constexpr int kMaxBlocks = 2 * 152;    // two blocks per SM
 constexpr int kWgradR = ((kMaxK + 1) * H + kThreads - 1) / kThreads;  // outputs per thread
 
 #define CN_CK(x)                                                                       \
@@ -312,8 +311,20 @@ struct Net {
   DevBuf<float> X, Hs[kLayers + 1], Ms[kLayers], s, ds, gl, dZa, dZb, D, Gn, y;
   DevBuf<int> rowptr, col, goff;
   cudaStream_t st = nullptr;
+  int max_blocks = 0;  // two blocks per SM of the current device
+
+  int blocks_cap() {
+    if (!max_blocks) {
+      int dev = 0, sms = 0;
+      CN_CK(cudaGetDevice(&dev));
+      CN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      max_blocks = 2 * std::max(1, sms);
+    }
+    return max_blocks;
+  }
 
   void release() {
+    max_blocks = 0;
     for (DevBuf<float>* b : {&P, &G, &Mo, &Vo, &partial, &X, &s, &ds, &gl, &dZa, &dZb, &D, &Gn, &y}) b->release();
     for (auto& b : Hs) b.release();
     for (auto& b : Ms) b.release();
@@ -359,11 +370,11 @@ struct Net {
     D.ensure(n * H);
     Gn.ensure(n * H);
     y.ensure(n);
-    partial.ensure((size_t)kMaxBlocks * (kMaxK + 1) * H);
+    partial.ensure((size_t)blocks_cap() * (kMaxK + 1) * H);
     if (n) CN_CK(cudaMemcpyAsync(y.p, b.y.data(), n * sizeof(float), cudaMemcpyHostToDevice, st));
   }
 
-  static int dense_blocks(int n) { return std::max(1, std::min(kMaxBlocks, (n + kTile - 1) / kTile)); }
+  int dense_blocks(int n) { return std::max(1, std::min(blocks_cap(), (n + kTile - 1) / kTile)); }
   static int node_blocks(long threads) { return (int)std::max(1L, (threads + 255) / 256); }
 
   const __nv_bfloat16* w(int off) const { return Wb.p + off; }
@@ -386,7 +397,7 @@ struct Net {
 
   void wgrad(int n0, int n1, const float* A1, int K1, const float* A2, int K2, const float* Gd, int J, int off) {
     const int n = n1 - n0;
-    const int nblk = std::max(1, std::min(kMaxBlocks, (n + 63) / 64));
+    const int nblk = std::max(1, std::min(blocks_cap(), (n + 63) / 64));
     const int chunk = (n + nblk - 1) / nblk;
     const int O = (K1 + K2 + 1) * J;
     k_wgrad<<<nblk, kThreads, 0, st>>>(n0, n1, chunk, A1, K1, A2, K2, Gd, J, partial.p);

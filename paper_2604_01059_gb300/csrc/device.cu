@@ -280,8 +280,8 @@ SlDec sliced_decompose(const Lut& l, bool za, bool zb, bool same) {
 // exponent d); false when some factor has no such form.
 template <class LutFn>
 bool sliced_term(const std::vector<FacKey>& f, int j, int d, LutFn& lut, SlTerm& t) {
-  static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int>, SlDec> cache;
+  // per host thread: programs compile in parallel threads without sharing it
+  thread_local std::map<std::tuple<int, int, int, int>, SlDec> cache;
   t.d = d;
   int jc = j;
   std::map<uint32_t, int> delta;
@@ -294,7 +294,6 @@ bool sliced_term(const std::vector<FacKey>& f, int j, int d, LutFn& lut, SlTerm&
     SlDec dec;
     {
       const auto key = std::make_tuple(k.kind, k.alpha & 7, k.beta & 7, flags);
-      std::lock_guard<std::mutex> g(mu);
       auto it = cache.find(key);
       if (it == cache.end()) it = cache.emplace(key, sliced_decompose(lut(k.kind, k.alpha, k.beta), za, zb, same)).first;
       dec = it->second;
