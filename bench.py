@@ -16,11 +16,13 @@ Two forms are timed on the same GPU and must write identical records:
   plain  heuristic cut order, one tsim_sample launch per program.
 
 The same line reports, each with its own timing, roofline and CPU baseline,
-the d=5 surface code with two injected logical rotations (3 x 10^6 shots)
-and the d=3 colour-code T-check (10^7 shots, the term-evaluation workload).
+the d=5 surface code with two injected logical rotations (3 x 10^6 shots),
+the same circuit sampled in measurement mode (every record, long
+autoregressive chains) and the d=3 colour-code T-check (10^7 shots, the
+term-evaluation workload).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                    [--only cfg2|cfg3|cfg4] [--profile]
+                    [--only cfg2|cfg2m|cfg3|cfg4] [--profile]
 
 Under torchrun (N > 1) every rank samples its own shot range of every
 program (weak scaling, no collective on the data path); timings take the
@@ -46,6 +48,9 @@ HEADLINE = "cfg4"
 WORKLOADS = {
     "cfg2": "d=5 rotated surface code, 49 qubits, 5 rounds, 16 T/T_DAG (two injected logical rotations, the "
             "second by gate teleportation), p in {5e-4,1e-3,2e-3}, 1e6 shots per p",
+    "cfg2m": "measurement sampling of the d=5 rotated surface code with two injected logical rotations "
+             "(147 measurement records per shot, 37 drawn by Algorithm 1 in 4 chains), p in {5e-4,1e-3,2e-3}, "
+             "1e6 shots per p",
     "cfg3": "d=3 triangular colour-code T-check, 19 qubits, 42 T/T_DAG, 3 check rounds, p=1e-3, postselected, "
             "1e7 shots",
     "cfg4": "batched launch: 256 seeded random noisy Clifford+T mirror circuits (20-60 qubits, depth 20-100, "
@@ -159,8 +164,9 @@ class Workload:
             self.texts = [(Wk.config3_circuit(p=1e-3), 10_000_000)]
         else:
             self.texts = [(Wk.config2_circuit(p=p), 1_000_000) for p in CFG2_P]
+        self.mode = T.MODE_MEASUREMENTS if name == "cfg2m" else T.MODE_DETECTORS
         if name != "cfg4":
-            self.plain = [T.Program(t) for t, _ in self.texts]
+            self.plain = [T.Program(t, mode=self.mode) for t, _ in self.texts]
             self.shots = [s for _, s in self.texts]
         self.compile_s = {"heuristic": time.perf_counter() - t0}
         t0 = time.perf_counter()
@@ -172,7 +178,7 @@ class Workload:
         if self.name == "cfg4":
             return [T.Program(t, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
                     for t, _ in self.texts]
-        return [T.Program(t, decomp=decomp) for t, _ in self.texts]
+        return [T.Program(t, decomp=decomp, mode=self.mode) for t, _ in self.texts]
 
     def _learned(self):
         import paper_2604_01059_gb300 as T
@@ -372,13 +378,16 @@ class OracleBench:
 
 # ------------------------------------------------------------------ GPU arm
 def _outputs(progs, shots):
+    """Device record buffers per program: (det, obs, accept, meas or None)."""
     import torch
     outs = []
     for p, ns in zip(progs, shots):
         i = p.info
+        meas = (torch.empty((ns, i["meas_words"]), dtype=torch.int64, device="cuda")
+                if i["mode"] == 1 and i["meas_words"] else None)
         outs.append((torch.empty((ns, max(i["det_words"], 1)), dtype=torch.int64, device="cuda"),
                      torch.empty((ns, max(i["obs_words"], 1)), dtype=torch.int64, device="cuda"),
-                     torch.empty((ns,), dtype=torch.uint8, device="cuda")))
+                     torch.empty((ns,), dtype=torch.uint8, device="cuda"), meas))
     return outs
 
 
@@ -398,10 +407,11 @@ def bench_config(wl, steps, args, dist, rank, world, flush, clocks_index):
     plain_outs = _outputs(plain_progs, shots)
 
     def plain_step():
-        for k, (p, (d, o, a)) in enumerate(zip(plain_progs, plain_outs)):
-            T.tsim_sample(p.h, shots[k], seeds[k], offsets[k], None, d, o, a, stream)
+        for k, (p, (d, o, a, m)) in enumerate(zip(plain_progs, plain_outs)):
+            T.tsim_sample(p.h, shots[k], seeds[k], offsets[k], m, d, o, a, stream)
 
-    batch = T.tsim_batch_create([p.h for p in progs], shots, seeds, offsets, None,
+    meas_list = [o[3] for o in outs] if any(o[3] is not None for o in outs) else None
+    batch = T.tsim_batch_create([p.h for p in progs], shots, seeds, offsets, meas_list,
                                 [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs], autotune=True)
     binfo = T.tsim_batch_info(batch)
 
@@ -440,8 +450,9 @@ def bench_config(wl, steps, args, dist, rank, world, flush, clocks_index):
     clk = clocks.stop()
     T.tsim_batch_free(batch)
     identical = all(torch.equal(a[:, :p.info["det_words"]], b[:, :p.info["det_words"]]) and
-                    torch.equal(x[:, :p.info["obs_words"]], y[:, :p.info["obs_words"]]) and torch.equal(u, v)
-                    for p, (a, x, u), (b, y, v) in zip(progs, outs, plain_outs))
+                    torch.equal(x[:, :p.info["obs_words"]], y[:, :p.info["obs_words"]]) and torch.equal(u, v) and
+                    (m1 is None or torch.equal(m1, m2))
+                    for p, (a, x, u, m1), (b, y, v, m2) in zip(progs, outs, plain_outs))
     del outs, plain_outs
     shots_step = sum(shots) * world
     value = shots_step * steps / (batch_ms / 1e3)
@@ -459,13 +470,15 @@ def bench_config(wl, steps, args, dist, rank, world, flush, clocks_index):
     for p, ns in zip(progs, shots):
         i = p.info
         hbuf.append((pinned((ns, max(i["det_words"], 1)), torch.int64).view(np.uint64),
-                     pinned((ns, max(i["obs_words"], 1)), torch.int64).view(np.uint64), pinned((ns,), torch.uint8)))
+                     pinned((ns, max(i["obs_words"], 1)), torch.int64).view(np.uint64), pinned((ns,), torch.uint8),
+                     pinned((ns, i["meas_words"]), torch.int64).view(np.uint64)
+                     if i["mode"] == 1 and i["meas_words"] else None))
 
     def e2e_step():
         for k, p in enumerate(progs):
             i = p.info
-            d, o, a = hbuf[k]
-            T.tsim_sample_host(p.h, shots[k], seeds[k], offsets[k], None, d if i["det_words"] else None,
+            d, o, a, m = hbuf[k]
+            T.tsim_sample_host(p.h, shots[k], seeds[k], offsets[k], m, d if i["det_words"] else None,
                                o if i["obs_words"] else None, a, stream)
 
     e2e_step()
@@ -477,7 +490,8 @@ def bench_config(wl, steps, args, dist, rank, world, flush, clocks_index):
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = shots_step * e2e_steps / e2e_s
-    d2h = sum(ns * (p.info["det_words"] * 8 + p.info["obs_words"] * 8 + 1) for p, ns in zip(progs, shots))
+    d2h = sum(ns * (p.info["det_words"] * 8 + p.info["obs_words"] * 8 + 1 +
+                    (p.info["meas_words"] * 8 if p.info["mode"] == 1 else 0)) for p, ns in zip(progs, shots))
     del hbuf
 
     # roofline of the dominant kernel (the batched launch's kernels)
@@ -541,7 +555,7 @@ def run_gpu(args):
     ids = [v.strip() for v in vis.split(",") if v.strip()]
     clocks_index = ids[local] if local < len(ids) else str(local)
     head = args.only or HEADLINE
-    names = [head] + ([] if args.only else [k for k in ("cfg2", "cfg3") if k != head])
+    names = [head] + ([] if args.only else [k for k in ("cfg2", "cfg2m", "cfg3") if k != head])
     res = {}
     for name in names:
         wl = Workload(name)
@@ -585,7 +599,7 @@ def run_reference(args):
         import paper_2604_01059_gb300 as T
         from paper_2604_01059_gb300 import workloads as Wk
         progs = ([T.Program(Wk.config3_circuit(p=1e-3))] if head == "cfg3"
-                 else [T.Program(Wk.config2_circuit(p=p)) for p in CFG2_P])
+                 else [T.Program(Wk.config2_circuit(p=p), mode=1 if head == "cfg2m" else 0) for p in CFG2_P])
     ob = OracleBench(progs)
     per_step = max(0.05, args.cpu_seconds / max(args.steps, 1))
     for _ in range(args.warmup):

@@ -118,7 +118,12 @@ typedef struct {
  * H S S_DAG SQRT_X SQRT_X_DAG T T_DAG CX CY CZ SWAP (and CX/CY/CZ with a rec[-k]
  * control), R RX M MX MR MRX (optional flip probability), X_ERROR Y_ERROR
  * Z_ERROR DEPOLARIZE1 DEPOLARIZE2 PAULI_CHANNEL_1 PAULI_CHANNEL_2, DETECTOR,
- * OBSERVABLE_INCLUDE, REPEAT, TICK, QUBIT_COORDS, SHIFT_COORDS) into a program.
+ * OBSERVABLE_INCLUDE, REPEAT, TICK, QUBIT_COORDS, SHIFT_COORDS, and the
+ * rotations R_X(t) R_Y(t) R_Z(t) U3(a, b, c) with angles in units of pi,
+ * Sec. "Methods") into a program.  Rotations by multiples of pi/4 stay in the
+ * exact ring; other angles make their chain's tables floating point: the
+ * marginals are then computed in complex double, and Algorithm 1 rounds each
+ * ratio P_1 / P_prev to the nearest FP32 value q and draws 1 iff U < q 2^32.
  * opts may be NULL (detector mode, heuristic, default budget, reduction on).
  * On success *out owns a new program. */
 tsim_status tsim_compile(const char* text, size_t len, const tsim_compile_opts* opts,
@@ -210,7 +215,9 @@ tsim_status tsim_sample_noalloc(const tsim_program* prog, uint64_t shots, uint64
  * num_random evaluations), 6 + x_words int64 values: the table index, the
  * four Z[w] coefficients c0..c3 and the sqrt2 exponent k of the kernel's
  * value (c0 + c1 w + c2 w^2 + c3 w^3) sqrt2^k, then the words of X at which
- * the kernel evaluated it.  Allocates and frees device scratch, and
+ * the kernel evaluated it.  For a floating-point table (arbitrary rotations)
+ * c0 and c1 hold the IEEE-754 bits of the real and imaginary parts of its
+ * complex value, c2 = c3 = 0, and k = INT32_MIN.  Allocates and frees device scratch, and
  * synchronises cuda_stream.  At most 2^31 shots. */
 tsim_status tsim_debug_sample(const tsim_program* prog, uint64_t shots, uint64_t seed, uint64_t shot_offset,
                               uint64_t* d_meas, uint64_t* d_det, uint64_t* d_obs, uint8_t* d_accept,
@@ -286,6 +293,13 @@ tsim_status tsim_sync(void* cuda_stream);
  * (Appendix "Validation"). */
 tsim_status tsim_eval_table(const tsim_program* prog, int t, const uint64_t* x,
                             int64_t out_zw[4], int32_t* sqrt2_exp);
+
+/* Value of marginal table t at X in complex double, for every table and in
+ * particular for those of circuits with arbitrary rotations (R_X, R_Y, R_Z,
+ * U3 at angles that are not multiples of pi/4), whose terms carry phases
+ * e^(i pi t) outside Z[w]: out[0] + i out[1].  tsim_eval_table refuses such
+ * tables with TSIM_ERR_ARG. */
+tsim_status tsim_eval_table_float(const tsim_program* prog, int t, const uint64_t* x, double out[2]);
 
 /* Map raw error bits e (num_error_bits bytes, 0/1) to X = (T e) in the
  * program's X layout (x_words words), Eq. detector_sampling. */

@@ -23,6 +23,7 @@ from fractions import Fraction
 import re
 
 ONE_Q = {"I", "X", "Y", "Z", "H", "S", "S_DAG", "SQRT_X", "SQRT_X_DAG", "T", "T_DAG"}
+ROTATIONS = {"R_X", "R_Y", "R_Z", "U3"}  # angles in units of pi (Sec. "Methods")
 ALIASES = {"CNOT": "CX", "ZCX": "CX", "ZCZ": "CZ", "ZCY": "CY", "SQRT_Z": "S",
            "SQRT_Z_DAG": "S_DAG", "H_XZ": "H", "MZ": "M", "RZ": "R", "MRZ": "MR"}
 TWO_Q = {"CX", "CY", "CZ", "SWAP"}
@@ -201,6 +202,10 @@ def parse(text: str) -> Circuit:
             c.observables.setdefault(k, []).extend(nmeas + t[1] for t in op.targets)
         elif n in ONE_Q or n in TWO_Q or n in RESETS:
             pass
+        elif n in ROTATIONS:
+            if len(op.args) != (3 if n == "U3" else 1):
+                raise ValueError(f"{n}: wrong number of angles")
+            op.args = [float(a) for a in op.args]
         else:
             raise ValueError(f"unsupported instruction {n}")
     c.ops = flat

@@ -54,10 +54,22 @@
  *     j/4; groups in program order; within a group, while channels remain, a
  *     gap word, and when it places a candidate, that candidate's word V.
  *
+ * Arbitrary rotations (R_X, R_Y, R_Z, U3 at angles that are not multiples of
+ * pi/4) leave the exact ring: their tables carry a constant phase
+ * e^(i pi phase) per term and factors e^(i pi t a) (Table "Types of
+ * parameterized phase terms" with an arbitrary angle).  A chain with such a
+ * table is evaluated in double-precision complex arithmetic: the chain's
+ * common phase is that of its normalisation z_n, so P_prev = |z_n| and a
+ * marginal z_1 gives P_1 = Re(z_1 conj(z_n)) / |z_n|.  The Bernoulli draw
+ * rounds the ratio P_1 / P_prev to the nearest FP32 value q and sets the bit
+ * iff U < q 2^32 (the decision both implementations take in the same
+ * precision, whatever the order of their sums).
+ *
  * Arithmetic: __int128 with every operation overflow-checked; an overflow or
  * a non-real marginal aborts the call with an error message rather than
  * returning a wrong bit.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -234,10 +246,11 @@ static int sign_xy(i128 X, i128 Y) {
 /* ---------------------------------------------------------- the program */
 typedef struct {
   int kind, alpha, beta;
+  double t;  /* kind 4: e^(i pi t a) */
   uint64_t* u; uint64_t* v;
 } factor;
-typedef struct { int s0, j0, nf; factor* f; } term;
-typedef struct { int nt; term* t; } table;
+typedef struct { int s0, j0, nf; double fph; factor* f; } term;
+typedef struct { int nt, flt; term* t; } table;
 typedef struct { int is_random; uint64_t* mask; int cst; int xbit, chain, table; } output;
 typedef struct { int n_out; uint32_t* thr; uint64_t* sig; } channel;
 /* geometric-gap group: members in order, Q, and T_1..T_n (T[k], T[0] unused) */
@@ -248,6 +261,7 @@ struct oracle_prog {
   int nx, W, nf, nr, nmeas, ndet, nobs;
   int n_out; output* out;
   int n_chains; int* chain_norm;
+  int* chain_float;  /* the chain has a table with arbitrary phases */
   int n_ch; channel* ch;
   int noise_mode;  /* 0 one word per channel, 1 geometric gaps */
   int n_groups; group* groups;
@@ -363,11 +377,12 @@ struct oracle_prog* oracle_load(const char* path) {
   p->tab = calloc((size_t)p->n_tab + 1, sizeof(table));
   for (int ti = 0; ti < p->n_tab; ++ti) {
     table* tb = &p->tab[ti];
-    if (expect(f, "T") || fscanf(f, "%d", &tb->nt) != 1) goto bad;
+    if (expect(f, "T") || fscanf(f, "%d %d", &tb->nt, &tb->flt) != 2 || tb->flt < 0 || tb->flt > 1) goto bad;
     tb->t = calloc((size_t)tb->nt + 1, sizeof(term));
     for (int t = 0; t < tb->nt; ++t) {
       term* tm = &tb->t[t];
       if (expect(f, "t") || fscanf(f, "%d %d %d", &tm->s0, &tm->j0, &tm->nf) != 3) goto bad;
+      if (tb->flt && fscanf(f, "%lf", &tm->fph) != 1) goto bad;
       tm->f = calloc((size_t)tm->nf + 1, sizeof(factor));
       for (int k = 0; k < tm->nf; ++k) {
         factor* fc = &tm->f[k];
@@ -375,6 +390,7 @@ struct oracle_prog* oracle_load(const char* path) {
         fc->u = calloc(W, 8);
         fc->v = calloc(W, 8);
         if (read_hex_words(f, W, fc->u) || read_hex_words(f, W, fc->v)) goto bad;
+        if (fc->kind == 4 && (!tb->flt || fscanf(f, "%lf", &fc->t) != 1)) goto bad;
       }
     }
   }
@@ -403,6 +419,18 @@ struct oracle_prog* oracle_load(const char* path) {
       if (fscanf(f, "%d", &p->obsmap[d][j]) != 1) goto bad;
   }
   if (p->mode == 1 && (nd != p->ndet || no != p->nobs)) goto bad;
+  /* a chain is evaluated in floating point when any of its tables is */
+  p->chain_float = calloc((size_t)p->n_chains + 1, sizeof(int));
+  for (int c = 0; c < p->n_chains; ++c) {
+    if (p->chain_norm[c] < 0 || p->chain_norm[c] >= p->n_tab) goto bad;
+    p->chain_float[c] = p->tab[p->chain_norm[c]].flt;
+  }
+  for (int i = 0; i < p->n_out; ++i) {
+    const output* o = &p->out[i];
+    if (!o->is_random) continue;
+    if (o->chain < 0 || o->chain >= p->n_chains || o->table < 0 || o->table >= p->n_tab) goto bad;
+    if (p->tab[o->table].flt) p->chain_float[o->chain] = 1;
+  }
   /* the raw-channel section that follows is verification data; not needed */
   fclose(f);
   return p;
@@ -418,6 +446,7 @@ void oracle_free(struct oracle_prog* p) {
   for (int i = 0; p->out && i < p->n_out; ++i) free(p->out[i].mask);
   free(p->out);
   free(p->chain_norm);
+  free(p->chain_float);
   for (int c = 0; p->ch && c < p->n_ch; ++c) { free(p->ch[c].thr); free(p->ch[c].sig); }
   free(p->ch);
   for (int g = 0; p->groups && g < p->n_groups; ++g) { free(p->groups[g].member); free(p->groups[g].T); }
@@ -545,10 +574,71 @@ static int eval_table(const struct oracle_prog* p, int ti, const uint64_t* X, zw
   return 0;
 }
 
+/* ---------------------------------------------------- floating-point tables */
+typedef struct { double re, im; } cplx;
+
+static cplx c_mul(cplx a, cplx b) { cplx r = {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; return r; }
+
+/* an exact value (c0 + c1 w + c2 w^2 + c3 w^3) sqrt2^k in complex double */
+static cplx zw_complex(const zw* z) {
+  const double h = sqrt(0.5);
+  cplx r = {(double)z->c[0] + h * ((double)z->c[1] - (double)z->c[3]),
+            (double)z->c[2] + h * ((double)z->c[1] + (double)z->c[3])};
+  const double m = pow(sqrt(2.0), z->k);
+  r.re *= m;
+  r.im *= m;
+  return r;
+}
+
+static cplx e_i_pi(double t) { cplx r = {cos(M_PI * t), sin(M_PI * t)}; return r; }
+
+/* P(X) = sum_t c^t e^(i pi phase_t) prod_k h_k, every factor from its formula
+ * (the exact kinds as elements of Z[w], then converted), in table order */
+static int eval_table_c(const struct oracle_prog* p, int ti, const uint64_t* X, cplx* out) {
+  if (ti < 0 || ti >= p->n_tab) return fail("bad table index");
+  const table* tb = &p->tab[ti];
+  cplx sum = {0, 0};
+  for (int t = 0; t < tb->nt; ++t) {
+    const term* tm = &tb->t[t];
+    zw c = zw_omega(tm->j0);
+    c.k = tm->s0;
+    cplx v = c_mul(zw_complex(&c), e_i_pi(tm->fph));
+    for (int k = 0; k < tm->nf; ++k) {
+      const factor* fc = &tm->f[k];
+      int a = parity(fc->u, X, p->W), b = parity(fc->v, X, p->W);
+      cplx h;
+      if (fc->kind == 4) {
+        h = a ? e_i_pi(fc->t) : (cplx){1.0, 0.0};
+      } else {
+        zw hz;
+        if (factor_value(fc, a, b, &hz)) return -1;
+        h = zw_complex(&hz);
+      }
+      v = c_mul(v, h);
+    }
+    sum.re += v.re;
+    sum.im += v.im;
+  }
+  *out = sum;
+  return 0;
+}
+
+/* Exported for the parity tests: the value of any table in complex double. */
+int oracle_eval_table_c(const struct oracle_prog* p, int ti, const uint64_t* X, double* re_im) {
+  g_ovf = 0;
+  cplx z;
+  if (eval_table_c(p, ti, X, &z)) return -1;
+  if (g_ovf) return fail("int128 overflow in table evaluation");
+  re_im[0] = z.re;
+  re_im[1] = z.im;
+  return 0;
+}
+
 /* Exported for the parity tests: value of one table at X, as
  * c[0..3] (each as hi,lo int64 pairs) and the sqrt2 exponent. */
 int oracle_eval_table(const struct oracle_prog* p, int ti, const uint64_t* X, int64_t* coef8, int* k) {
   g_ovf = 0;
+  if (ti >= 0 && ti < p->n_tab && p->tab[ti].flt) return fail("table has arbitrary phases");
   zw z;
   if (eval_table(p, ti, X, &z)) return -1;
   if (g_ovf) return fail("int128 overflow in table evaluation");
@@ -610,11 +700,20 @@ int oracle_noise_x(const struct oracle_prog* p, uint64_t seed, uint64_t shot, ui
 }
 
 static int sample_shot(const struct oracle_prog* p, uint64_t seed, uint64_t shot, uint64_t* X,
-                       uint8_t* bits, rv* pprev, int* rot) {
+                       uint8_t* bits, rv* pprev, int* rot, double* fprev, cplx* fnorm) {
   int W = p->W;
   sample_noise(p, seed, shot, X);
   /* Algorithm 1: P_prev <- P for every chain (phase removed) */
   for (int c = 0; c < p->n_chains; ++c) {
+    if (p->chain_float[c]) {
+      cplx z;
+      if (eval_table_c(p, p->chain_norm[c], X, &z)) return -1;
+      const double m = sqrt(z.re * z.re + z.im * z.im);
+      if (!(m > 0)) return fail("normalisation is zero");
+      fnorm[c] = z;
+      fprev[c] = m;
+      continue;
+    }
     zw z;
     if (eval_table(p, p->chain_norm[c], X, &z)) return -1;
     if (chain_phase(&z, &rot[c])) return -1;
@@ -630,6 +729,26 @@ static int sample_shot(const struct oracle_prog* p, uint64_t seed, uint64_t shot
     } else {
       int xb = o->xbit;
       X[xb >> 6] |= (uint64_t)1 << (xb & 63);
+      if (p->chain_float[o->chain]) {
+        const int c = o->chain;
+        cplx z1;
+        if (eval_table_c(p, o->table, X, &z1)) return -1;
+        const cplx zn = fnorm[c];
+        const double mn = sqrt(zn.re * zn.re + zn.im * zn.im);
+        const double p1 = (z1.re * zn.re + z1.im * zn.im) / mn;
+        if (!(fprev[c] > 0)) return fail("P_prev is not positive");
+        const float q = (float)(p1 / fprev[c]);
+        uint32_t U = philox_word(seed, shot, 1, (uint32_t)i);
+        bit = (double)U < (double)q * 4294967296.0;
+        if (bit) {
+          fprev[c] = p1;
+        } else {
+          fprev[c] = fprev[c] - p1;
+          X[xb >> 6] &= ~((uint64_t)1 << (xb & 63));
+        }
+        bits[i] = (uint8_t)bit;
+        continue;
+      }
       zw z;
       rv p1;
       if (eval_table(p, o->table, X, &z)) return -1;
@@ -670,9 +789,11 @@ int oracle_sample(const struct oracle_prog* p, uint64_t seed, uint64_t shot_begi
   uint8_t* bits = calloc((size_t)p->n_out + 1, 1);
   rv* pprev = calloc((size_t)p->n_chains + 1, sizeof(rv));
   int* rot = calloc((size_t)p->n_chains + 1, sizeof(int));
+  double* fprev = calloc((size_t)p->n_chains + 1, sizeof(double));
+  cplx* fnorm = calloc((size_t)p->n_chains + 1, sizeof(cplx));
   int rc = 0;
   for (uint64_t s = 0; s < n; ++s) {
-    if (sample_shot(p, seed, shot_begin + s, X, bits, pprev, rot)) { rc = -1; break; }
+    if (sample_shot(p, seed, shot_begin + s, X, bits, pprev, rot, fprev, fnorm)) { rc = -1; break; }
     if (g_ovf) { rc = fail("int128 overflow while sampling"); break; }
     uint8_t dbits[4096];
     int nd = p->ndet;
@@ -715,7 +836,7 @@ int oracle_sample(const struct oracle_prog* p, uint64_t seed, uint64_t shot_begi
       accept[s] = (uint8_t)ok;
     }
   }
-  free(X); free(bits); free(pprev); free(rot);
+  free(X); free(bits); free(pprev); free(rot); free(fprev); free(fnorm);
   return rc;
 }
 

@@ -26,7 +26,7 @@ def build(force=False) -> str:
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         tmp = _OUT + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-Wall",
-                               "-o", tmp, _SRC])
+                               "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _OUT)
     return _OUT
 
@@ -51,6 +51,8 @@ def lib():
                                     ctypes.c_void_p, ctypes.c_void_p]
         L.oracle_decide.argtypes = [ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
                                     ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+        L.oracle_eval_table_c.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64),
+                                          ctypes.POINTER(ctypes.c_double)]
         L.oracle_noise_x.argtypes = [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint64,
                                      ctypes.POINTER(ctypes.c_uint64)]
         L.oracle_geo_gap.argtypes = [ctypes.c_uint32, ctypes.c_int, ctypes.c_uint32]
@@ -125,6 +127,15 @@ class OracleProgram:
             c.append((hi << 64) | lo)
         # evaluator stores value * sqrt2^k ; DOmega stores / sqrt2^k
         return DOmega(c, -k.value)
+
+    def eval_table_c(self, table, xwords) -> complex:
+        """Value of any table at X in complex double (tables with arbitrary
+        phases included)."""
+        X = (ctypes.c_uint64 * self.words)(*[int(v) for v in xwords])
+        out = (ctypes.c_double * 2)()
+        if lib().oracle_eval_table_c(self._h, table, X, out) != 0:
+            raise RuntimeError(lib().oracle_last_error().decode())
+        return complex(out[0], out[1])
 
     def noise_x(self, seed, shot):
         """X = T e of one shot after its error mechanisms, before any output."""

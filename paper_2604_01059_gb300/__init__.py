@@ -22,7 +22,7 @@ __all__ = [
     "tsim_last_error", "tsim_selftest_rules", "tsim_measure_int_peak", "tsim_program_device_table_stats",
     "tsim_program_set_table_layout", "tsim_program_device_table_layout", "tsim_program_device_output_stats",
     "tsim_selftest_sliced", "tsim_debug_sample", "tsim_program_set_noise_sampling", "tsim_program_noise_info",
-    "tsim_program_device_bytes", "load_library",
+    "tsim_program_device_bytes", "tsim_eval_table_float", "load_library",
     "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T", "DECOMP_PAIRS",
     "DECOMP_CAT5",
 ]
@@ -120,6 +120,7 @@ def _load(path):
     L.tsim_program_set_noise_sampling.argtypes = [vp, i32]
     L.tsim_program_noise_info.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.tsim_program_device_bytes.argtypes = [vp, ctypes.POINTER(u64)]
+    L.tsim_eval_table_float.argtypes = [vp, i32, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_double)]
     L.tsim_cut_num_params.argtypes = []
     L.tsim_cut_init_params.argtypes = [u64, vp]
     L.tsim_cut_dataset.argtypes = [u64, i32, i32, i32, u64, i32, ctypes.c_char_p]
@@ -136,7 +137,7 @@ def _load(path):
               "tsim_program_device_table_stats", "tsim_program_set_table_layout",
               "tsim_program_device_table_layout", "tsim_program_device_output_stats", "tsim_selftest_sliced",
               "tsim_debug_sample", "tsim_program_set_noise_sampling", "tsim_program_noise_info",
-              "tsim_program_device_bytes",
+              "tsim_program_device_bytes", "tsim_eval_table_float",
               "tsim_cut_num_params",
               "tsim_cut_init_params",
               "tsim_cut_dataset", "tsim_cut_forward", "tsim_cut_loss_grad", "tsim_cut_adam_step", "tsim_cut_train",
@@ -308,6 +309,15 @@ def tsim_eval_table(h, t, xwords):
     k = ctypes.c_int32()
     _check(load_library().tsim_eval_table(h, t, x, out, ctypes.byref(k)))
     return tuple(out), k.value
+
+
+def tsim_eval_table_float(h, t, xwords):
+    """Value of any table at X in complex double (tables of arbitrary rotations included)."""
+    n = len(xwords)
+    x = (ctypes.c_uint64 * n)(*[int(v) & 0xFFFFFFFFFFFFFFFF for v in xwords])
+    out = (ctypes.c_double * 2)()
+    _check(load_library().tsim_eval_table_float(h, t, x, out))
+    return complex(out[0], out[1])
 
 
 def tsim_raw_to_x(h, e_bits, x_words):

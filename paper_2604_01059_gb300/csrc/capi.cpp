@@ -11,6 +11,8 @@
 #include "program.h"
 #include "zx.h"
 
+#include <complex>
+
 #include <cuda_runtime.h>
 
 namespace {
@@ -442,6 +444,16 @@ tsim_status tsim_eval_table(const tsim_program* prog, int t, const uint64_t* x, 
   });
 }
 
+tsim_status tsim_eval_table_float(const tsim_program* prog, int t, const uint64_t* x, double out[2]) {
+  return guard([&] {
+    const tsim::Program& p = prog_of(prog);
+    if (!x || !out) tsim::fail(TSIM_ERR_ARG, "NULL argument");
+    const std::complex<double> v = tsim::eval_table_host_c(p, t, x);
+    out[0] = v.real();
+    out[1] = v.imag();
+  });
+}
+
 tsim_status tsim_raw_to_x(const tsim_program* prog, const uint8_t* e, uint64_t* x) {
   return guard([&] {
     const tsim::Program& p = prog_of(prog);
@@ -538,6 +550,35 @@ tsim_status tsim_selftest_rules(uint64_t seed, int iterations) {
         tsim::DecompStats st;
         tsim::decompose(h, TSIM_DECOMP_LEARNED, terms, st, &scores, (int)(rng() % (uint64_t)std::max(1, h.n)));
         check(terms, "score order");
+      }
+      {
+        // the same graph with arbitrary angles on some spiders: every policy
+        // must reproduce the brute-force value in complex double
+        tsim::Graph h = g;
+        for (int v = 0; v < h.n; ++v)
+          if (rng() % 3 == 0) h.set_angle(v, (double)(rng() % 1000) / 997.0);
+        if (rng() % 2) h.fph = (double)(rng() % 1000) / 991.0;
+        if (np > 0 && rng() % 2) {
+          tsim::Bits a(np);
+          a.set(rng() % np);
+          h.add_factor_f((double)(rng() % 1000) / 983.0, a);
+        }
+        for (int policy : {0, 3, 2}) {
+          std::vector<tsim::Term> terms;
+          tsim::DecompStats st;
+          tsim::decompose(h, policy, terms, st);
+          for (uint32_t pv = 0; pv < (1u << np); ++pv) {
+            tsim::Bits b(np);
+            for (size_t q = 0; q < np; ++q)
+              if ((pv >> q) & 1) b.set(q);
+            std::complex<double> sum = 0.0;
+            for (const auto& t : terms) sum += tsim::term_value_c(t, b);
+            const std::complex<double> want = tsim::brute_value_c(h, b);
+            if (std::abs(sum - want) > 1e-9 * (1.0 + std::abs(want)))
+              tsim::fail(TSIM_ERR_INTERNAL, "rewrite self-test with arbitrary angles failed at iteration " +
+                                                std::to_string(it));
+          }
+        }
       }
       // single steps on a copy: each must preserve the brute-force value
       tsim::Graph h = g;

@@ -10,6 +10,7 @@
 #include "circuit.h"
 
 #include <cctype>
+#include <cmath>
 #include <cstdlib>
 #include <map>
 #include <sstream>
@@ -22,6 +23,7 @@ const std::map<std::string, Op>& op_table() {
       {"I", Op::I}, {"X", Op::X}, {"Y", Op::Y}, {"Z", Op::Z}, {"H", Op::H}, {"H_XZ", Op::H},
       {"S", Op::S}, {"SQRT_Z", Op::S}, {"S_DAG", Op::S_DAG}, {"SQRT_Z_DAG", Op::S_DAG},
       {"SQRT_X", Op::SQRT_X}, {"SQRT_X_DAG", Op::SQRT_X_DAG}, {"T", Op::T}, {"T_DAG", Op::T_DAG},
+      {"R_X", Op::R_X}, {"R_Y", Op::R_Y}, {"R_Z", Op::R_Z}, {"U3", Op::U3},
       {"CX", Op::CX}, {"CNOT", Op::CX}, {"ZCX", Op::CX}, {"CY", Op::CY}, {"ZCY", Op::CY},
       {"CZ", Op::CZ}, {"ZCZ", Op::CZ}, {"SWAP", Op::SWAP},
       {"R", Op::R}, {"RZ", Op::R}, {"RX", Op::RX}, {"M", Op::M}, {"MZ", Op::M}, {"MX", Op::MX},
@@ -287,6 +289,15 @@ Circuit parse_circuit(const std::string& text) {
           }
         }
         break;
+      case Op::R_X: case Op::R_Y: case Op::R_Z: case Op::U3: {
+        const size_t na = in.op == Op::U3 ? 3 : 1;
+        if (in.args.size() != na) fail(TSIM_ERR_PARSE, "rotation: wrong number of angles (units of pi)");
+        for (double a : in.args)
+          if (!std::isfinite(a)) fail(TSIM_ERR_PARSE, "rotation angle is not finite");
+        for (const Target& t : in.t)
+          if (t.rec) fail(TSIM_ERR_PARSE, "unexpected rec target");
+        break;
+      }
       default:
         for (const Target& t : in.t)
           if (t.rec) fail(TSIM_ERR_PARSE, "unexpected rec target");

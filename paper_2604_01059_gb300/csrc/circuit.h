@@ -1,5 +1,6 @@
 // Stim-subset circuit representation and parser (Sec. "Methods": Tsim reads
-// the Stim circuit format extended with T and T_DAG).
+// the Stim circuit format extended with T, T_DAG and the rotations R_X, R_Y,
+// R_Z and U3, whose angles are given in units of pi).
 #pragma once
 #include <string>
 #include <vector>
@@ -9,7 +10,7 @@
 namespace tsim {
 
 enum class Op {
-  I, X, Y, Z, H, S, S_DAG, SQRT_X, SQRT_X_DAG, T, T_DAG,
+  I, X, Y, Z, H, S, S_DAG, SQRT_X, SQRT_X_DAG, T, T_DAG, R_X, R_Y, R_Z, U3,
   CX, CY, CZ, SWAP,
   R, RX, M, MX, MR, MRX,
   X_ERROR, Y_ERROR, Z_ERROR, DEPOLARIZE1, PAULI_CHANNEL_1, DEPOLARIZE2, PAULI_CHANNEL_2,

@@ -65,6 +65,15 @@ struct Builder {
     g.add_phase(th, ket[(size_t)q]);
     g.add_phase(-th, bra[(size_t)q]);
   }
+  // R_Z(t) = diag(e^(-i pi t/2), e^(i pi t/2)) ~ diag(1, e^(i pi t)): the
+  // global phase cancels between the two copies
+  void phase_f(int q, double t) {
+    g.add_phase_f(t, ket[(size_t)q]);
+    g.add_phase_f(-t, bra[(size_t)q]);
+  }
+  void rx(int q, double t) { H(q); phase_f(q, t); H(q); }
+  // R_Y(t) = S R_X(t) S^dag (S X S^dag = Y); in time order S^dag first
+  void ry(int q, double t) { phase(q, 6); rx(q, t); phase(q, 2); }
   void Xg(int q) { ket[(size_t)q].c ^= 1; bra[(size_t)q].c ^= 1; }
   void Zg(int q) { phase(q, 4); }
   void CX(int c, int t) { form_xor(ket[(size_t)t], ket[(size_t)c]); form_xor(bra[(size_t)t], bra[(size_t)c]); }
@@ -116,6 +125,16 @@ struct Builder {
         case Op::S_DAG: for (size_t k = 0; k < in.t.size(); ++k) phase(tq(k), 6); break;
         case Op::T: for (size_t k = 0; k < in.t.size(); ++k) phase(tq(k), 1); break;
         case Op::T_DAG: for (size_t k = 0; k < in.t.size(); ++k) phase(tq(k), 7); break;
+        case Op::R_Z: for (size_t k = 0; k < in.t.size(); ++k) phase_f(tq(k), in.args[0]); break;
+        case Op::R_X: for (size_t k = 0; k < in.t.size(); ++k) rx(tq(k), in.args[0]); break;
+        case Op::R_Y: for (size_t k = 0; k < in.t.size(); ++k) ry(tq(k), in.args[0]); break;
+        case Op::U3:  // U3(theta, phi, lambda) ~ R_Z(phi) R_Y(theta) R_Z(lambda)
+          for (size_t k = 0; k < in.t.size(); ++k) {
+            phase_f(tq(k), in.args[2]);
+            ry(tq(k), in.args[0]);
+            phase_f(tq(k), in.args[1]);
+          }
+          break;
         case Op::SQRT_X: case Op::SQRT_X_DAG:  // H S H, H S_DAG H
           for (size_t k = 0; k < in.t.size(); ++k) {
             H(tq(k));
@@ -386,7 +405,7 @@ void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget,
   std::vector<int> cand;  // non-Clifford spiders by predicted term count
   int own_first = -1;     // the heuristic's own first cut: the lowest odd spider
   for (int v = 0; v < M.n; ++v)
-    if (M.alive[(size_t)v] && (M.lam[(size_t)v] & 1)) {
+    if (M.alive[(size_t)v] && M.non_clifford(v)) {
       if (own_first < 0) own_first = v;
       cand.push_back(v);
     }
@@ -490,6 +509,10 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
         if (ca) { G.ph = (G.ph + f.alpha) & 7; f.alpha = -f.alpha; }
         G.add_factor(F_PHASE, f.alpha, 0, f.a, f.b);
         break;
+      case F_PHASE_F:
+        if (ca) { G.fph = angle_mod2(G.fph + f.t); f.t = -f.t; }
+        G.add_factor_f(f.t, f.a);
+        break;
       case F_PI_PAIR:
         G.add_factor(F_PI_PAIR, 0, 0, f.a, f.b);
         if (cb) G.add_factor(F_PHASE, 4, 0, f.a, Bits());
@@ -566,6 +589,7 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
     for (int v = 0; v < G.n; ++v)
       if (G.alive[(size_t)v] && find(v) == root) {
         vmap[(size_t)v] = Gc.add_var(G.lam[(size_t)v]);
+        Gc.ang[(size_t)vmap[(size_t)v]] = G.ang[(size_t)v];
         Gc.P[(size_t)vmap[(size_t)v]] = G.P[(size_t)v];
       }
     for (int v = 0; v < G.n; ++v) {
@@ -621,6 +645,7 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
         switch (f.kind) {
           case F_NODE: { int z = M.add_var(f.alpha); M.add_sign(form_var(np, z), A); break; }
           case F_PHASE: M.add_phase(f.alpha, A); break;
+          case F_PHASE_F: M.add_phase_f(f.t, A); break;
           case F_PI_PAIR: M.add_sign(A, B); break;
           case F_PHASE_PAIR: {
             int x = M.add_var(f.alpha), y = M.add_var(f.beta);
@@ -705,12 +730,14 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
       ProgTerm pt;
       pt.s0 = tm.s2;
       pt.j0 = tm.ph & 7;
+      pt.fph = tm.fph;
       for (size_t q = 0; q < tm.fac.size(); ++q) {
         const Factor& f = tm.fac[q];
         ProgFactor pf;
         pf.kind = f.kind;
         pf.alpha = f.alpha & 7;
         pf.beta = f.beta & 7;
+        pf.t = f.t;
         pf.u = xmask_of(f.a);
         pf.v = xmask_of(f.b);
         pt.f.push_back(std::move(pf));
@@ -927,8 +954,43 @@ void set_noise_sampling(Program& p, int mode) {
   p.groups = mode ? std::move(gs) : std::vector<NoiseGroup>();
 }
 
+bool ProgTable::is_float() const {
+  for (const ProgTerm& tm : terms) {
+    if (tm.fph != 0.0) return true;
+    for (const ProgFactor& f : tm.f)
+      if (f.kind == F_PHASE_F) return true;
+  }
+  return false;
+}
+
+std::complex<double> eval_table_host_c(const Program& p, int t, const uint64_t* x) {
+  if (t < 0 || t >= (int)p.tables.size()) fail(TSIM_ERR_ARG, "table index out of range");
+  auto par = [&](const std::vector<uint64_t>& m) {
+    uint64_t acc = 0;
+    for (size_t w = 0; w < m.size(); ++w) acc ^= m[w] & x[w];
+    return __builtin_parityll(acc);
+  };
+  std::complex<double> sum = 0.0;
+  for (const ProgTerm& tm : p.tables[(size_t)t].terms) {
+    ZW c = ZW::omega(tm.j0);
+    c.k = tm.s0;
+    std::complex<double> v = zw_to_complex(c) * std::polar(1.0, M_PI * tm.fph);
+    for (const ProgFactor& f : tm.f) {
+      Factor fc;
+      fc.kind = f.kind;
+      fc.alpha = f.alpha;
+      fc.beta = f.beta;
+      fc.t = f.t;
+      v *= factor_value_c(fc, par(f.u), par(f.v));
+    }
+    sum += v;
+  }
+  return sum;
+}
+
 ZW eval_table_host(const Program& p, int t, const uint64_t* x) {
   if (t < 0 || t >= (int)p.tables.size()) fail(TSIM_ERR_ARG, "table index out of range");
+  if (p.tables[(size_t)t].is_float()) fail(TSIM_ERR_ARG, "table has arbitrary phases: use the floating-point evaluation");
   auto par = [&](const std::vector<uint64_t>& m) {
     uint64_t acc = 0;
     for (size_t w = 0; w < m.size(); ++w) acc ^= m[w] & x[w];

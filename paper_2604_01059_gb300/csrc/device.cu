@@ -8,6 +8,8 @@
 
 #include <algorithm>
 #include <array>
+#include <cmath>
+#include <complex>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -193,8 +195,9 @@ struct Lut {
 
 struct FacKey {
   int kind, alpha, beta, ia, ib;
+  double t = 0;  // arbitrary-angle factors: the angle
   bool operator<(const FacKey& o) const {
-    return std::tie(kind, alpha, beta, ia, ib) < std::tie(o.kind, o.alpha, o.beta, o.ia, o.ib);
+    return std::tie(kind, alpha, beta, ia, ib, t) < std::tie(o.kind, o.alpha, o.beta, o.ia, o.ib, o.t);
   }
 };
 
@@ -457,6 +460,19 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
   L.o_cn = s.section();
   for (int c : p.chain_norm) { int32_t v = c; s.put(&v, 4); }
   { int32_t z = 0; s.put(&z, 4); }
+  // a chain with a table of arbitrary phases is evaluated in floating point,
+  // all its tables with it (Algorithm 1 needs one arithmetic per chain)
+  std::vector<char> chain_fl(p.chain_norm.size(), 0), tab_fl(p.tables.size(), 0);
+  for (size_t c = 0; c < p.chain_norm.size(); ++c) chain_fl[c] = p.tables[(size_t)p.chain_norm[c]].is_float();
+  for (const ProgOutput& o : p.outputs)
+    if (o.random && p.tables[(size_t)o.table].is_float()) chain_fl[(size_t)o.chain] = 1;
+  for (size_t c = 0; c < p.chain_norm.size(); ++c)
+    if (chain_fl[c]) tab_fl[(size_t)p.chain_norm[c]] = 1;
+  for (const ProgOutput& o : p.outputs)
+    if (o.random && chain_fl[(size_t)o.chain]) tab_fl[(size_t)o.table] = 1;
+  L.o_cf = s.section();
+  for (char f : chain_fl) { int32_t v = f; s.put(&v, 4); }
+  { int32_t z = 0; s.put(&z, 4); }
 
   // tables: distinct parities, then terms merged into classes with equal factors
   struct Cls {
@@ -471,7 +487,10 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
   std::vector<DSBatch> sbs;
   std::vector<DSeg> segs;
   std::vector<uint32_t> rows;
-  for (const ProgTable& tb : p.tables) {
+  std::vector<uint32_t> ffidx;
+  std::vector<double> ffang;
+  for (size_t ti = 0; ti < p.tables.size(); ++ti) {
+    const ProgTable& tb = p.tables[ti];
     DTable dt{};
     dt.par_off = (uint32_t)(par.size() / (size_t)W);
     std::map<std::vector<uint64_t>, int> pidx;
@@ -487,6 +506,84 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
       return id;
     };
     parity_index(std::vector<uint64_t>((size_t)W, 0));  // index 0: the zero parity
+    if (tab_fl[ti]) {
+      // FLOAT: terms with equal factor lists merged, the complex coefficient
+      // summed in double; exact factors as per-thread increments, arbitrary
+      // ones as (parity, angle)
+      std::map<std::vector<FacKey>, size_t> fidx_of;
+      std::vector<std::pair<std::vector<FacKey>, std::complex<double>>> fcl;
+      for (const ProgTerm& tm : tb.terms) {
+        std::vector<FacKey> fk;
+        for (const ProgFactor& f : tm.f) {
+          FacKey k{f.kind, f.kind == 4 ? 0 : (f.alpha & 7), f.kind == 4 ? 0 : (f.beta & 7), parity_index(f.u),
+                   f.kind == 4 ? 0 : parity_index(f.v)};
+          k.t = f.kind == 4 ? f.t : 0.0;
+          fk.push_back(k);
+        }
+        std::sort(fk.begin(), fk.end());
+        ZW c0 = ZW::omega(tm.j0);
+        c0.k = tm.s0;
+        const std::complex<double> c = zw_to_complex(c0) * std::polar(1.0, M_PI * tm.fph);
+        auto it = fidx_of.find(fk);
+        if (it == fidx_of.end()) {
+          fidx_of[fk] = fcl.size();
+          fcl.push_back({fk, c});
+        } else {
+          fcl[it->second].second += c;
+        }
+      }
+      if (plist.size() > (size_t)kMaxParities)
+        throw PackError{TSIM_ERR_ARG, "a floating-point table has more than 256 distinct parities"};
+      dt.mode = TAB_FLOAT;
+      dt.base = 0;
+      dt.par_off = (uint32_t)(par.size() / (size_t)W);
+      for (const auto& m : plist) par.insert(par.end(), m.begin(), m.end());
+      dt.n_par = (uint32_t)plist.size();
+      dt.cls_off = (uint32_t)cls.size();
+      uint64_t nfac = 0;
+      for (const auto& [fk, coef] : fcl) {
+        DClass d{};
+        d.fac_off = (uint32_t)fidx.size();
+        d.mono = 2;
+        d.j0 = (int32_t)ffidx.size();
+        int smin_sum = 0;
+        for (const FacKey& k : fk) {
+          if (k.kind == 4) {
+            ffidx.push_back((uint32_t)k.ia);
+            ffang.push_back(k.t);
+            continue;
+          }
+          const Lut& l = lut(k.kind, k.alpha, k.beta);
+          smin_sum += l.smin;
+          fidx.push_back((uint32_t)k.ia | ((uint32_t)k.ib << 8));
+          finc.insert(finc.end(), l.inc, l.inc + 4);
+          fcoord.push_back(0);
+          fcoord.push_back(0);
+          d.n_fac++;
+        }
+        d.pad = (int32_t)(ffidx.size() - (size_t)d.j0);
+        const std::complex<double> cc = coef * std::pow(std::sqrt(2.0), smin_sum);
+        double re = cc.real(), im = cc.imag();
+        std::memcpy(&d.c[0], &re, 8);
+        std::memcpy(&d.c[1], &im, 8);
+        nfac += fk.size();
+        cls.push_back(d);
+      }
+      dt.n_cls = (uint32_t)fcl.size();
+      L.classes += fcl.size();
+      L.parities += plist.size() - 1;
+      L.table_classes.push_back(fcl.size());
+      L.table_parities.push_back(plist.size() - 1);
+      L.table_class_factors.push_back(nfac);
+      L.class_factors += nfac;
+      L.table_mode.push_back(TAB_FLOAT);
+      L.table_batches.push_back(0);
+      L.table_rows.push_back(0);
+      L.table_ops.push_back(0);
+      L.table_work32.push_back(0);
+      tabs.push_back(dt);
+      continue;
+    }
     std::map<std::vector<FacKey>, size_t> cidx;
     std::vector<Cls> cl;
     for (const ProgTerm& tm : tb.terms) {
@@ -849,6 +946,10 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
   if (!sbs.empty()) s.put(sbs.data(), sbs.size() * sizeof(DSBatch));
   L.o_row = s.section();
   if (!rows.empty()) s.put(rows.data(), rows.size() * 4);
+  L.o_ffi = s.section();
+  if (!ffidx.empty()) s.put(ffidx.data(), ffidx.size() * 4);
+  L.o_ffa = s.section();
+  if (!ffang.empty()) s.put(ffang.data(), ffang.size() * 8);
   L.sl_par = L.sl_par_max ? (int)((L.sl_par_max + 3) & ~3u) : 0;
   L.sl_rb = (int)L.sl_rows_max * 32;
   // measurement-mode detector / observable maps (CSR)
@@ -909,6 +1010,9 @@ DevView make_view(const unsigned char* base, const DeviceLayout& L, const Progra
   v.dmap_idx = (const int32_t*)(base + L.o_dmi);
   v.omap_off = (const int32_t*)(base + L.o_omo);
   v.omap_idx = (const int32_t*)(base + L.o_omi);
+  v.chain_float = (const int32_t*)(base + L.o_cf);
+  v.ffidx = (const uint32_t*)(base + L.o_ffi);
+  v.ffang = (const double*)(base + L.o_ffa);
   return v;
 }
 

@@ -25,8 +25,16 @@ struct DOut { int32_t kind, cst, a, chain, table, rec; };
 // Table layouts: SCALAR = distinct parities indexed per factor (one thread
 // per shot), BASIS = parities as coordinates in a GF(2) basis of their span,
 // SLICED = warp-cooperative bit-sliced evaluation (below).
-enum : int { TAB_SCALAR = 0, TAB_BASIS = 1, TAB_SLICED = 2 };
+// FLOAT = the tables of a chain with arbitrary rotation angles: per thread,
+// as SCALAR, with each class's coefficient a complex double and its
+// arbitrary-angle factors e^(i pi t a) summed into one phase.
+enum : int { TAB_SCALAR = 0, TAB_BASIS = 1, TAB_SLICED = 2, TAB_FLOAT = 3 };
 struct DTable { uint32_t par_off, n_par, cls_off, n_cls; int32_t base, mode, sb_off, n_sb, stage, pad[3]; };
+// A class of merged terms.  SCALAR / BASIS: coefficient w^j0 (mono) or c[4]
+// in Z[w], magnitude sqrt2^d0 over the table base.  FLOAT: fac_off / n_fac
+// its exact factors, j0 / pad the offset and count of its arbitrary-angle
+// factors, c[0] and c[1] the bits of the real and imaginary parts of its
+// complex coefficient (all magnitudes included).
 struct DClass { uint32_t fac_off, n_fac; int32_t mono, j0, d0, pad; long long c[4]; };
 
 // Bit-sliced tables.  A warp evaluates 32 shots at once: bit s of every
@@ -93,6 +101,9 @@ struct DevView {
   const int32_t* dmap_idx;
   const int32_t* omap_off;
   const int32_t* omap_idx;
+  const int32_t* chain_float;  // per chain: 1 when its tables are FLOAT
+  const uint32_t* ffidx;       // FLOAT tables: parity index of each arbitrary-angle factor
+  const double* ffang;         // FLOAT tables: its angle, in units of pi
 };
 
 // ------------------------------------------------------------------ Philox
@@ -166,8 +177,11 @@ struct BatchLaunchArgs {
 };
 
 // Words of one debug record: table, the four Z[w] coefficients, the sqrt2
-// exponent, then the W words of X at which the table was evaluated.
+// exponent, then the W words of X at which the table was evaluated.  For a
+// FLOAT table the first two coefficient words hold the bits of the real and
+// imaginary parts of its complex value and the exponent word is kDumpFloat.
 constexpr int kDumpHead = 6;
+constexpr long long kDumpFloat = -2147483648ll;
 
 // Sampling launchers, one instantiation per padded X width W (kern_w<W>.cu).
 template <int W>

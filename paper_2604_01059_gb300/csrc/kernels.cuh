@@ -291,6 +291,14 @@ struct RowsS {
   __device__ __forceinline__ void adv4(int k) { a += 512u * (uint32_t)k; }
 };
 
+// Rows per chunk of sl_loop (a multiple of 4): every row and parity load of
+// a chunk is issued before its updates.
+#ifndef TSIM_SL_CHUNK
+#define TSIM_SL_CHUNK 16
+#endif
+constexpr int kSlChunk = TSIM_SL_CHUNK;
+static_assert(kSlChunk % 4 == 0 && kSlChunk >= 4, "rows per chunk must be a multiple of 4");
+
 // The n rows (a multiple of 4) of one operation code, in chunks whose row
 // loads and parity loads are all issued before the updates; f(way, a, b)
 // spreads consecutive rows over 4 independent accumulators (way = row & 3)
@@ -298,10 +306,10 @@ struct RowsS {
 template <bool PAIR, class Rows, class F>
 __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
   int k = 0;
-  for (; k + 16 <= n; k += 16, R.adv4(4)) {
-    uint32_t r[16], a[16], b[16];
+  for (; k + kSlChunk <= n; k += kSlChunk, R.adv4(kSlChunk / 4)) {
+    uint32_t r[kSlChunk], a[kSlChunk], b[kSlChunk];
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 0; g < kSlChunk / 4; ++g) {
       const uint4 v = R.get4(g);
       r[4 * g] = v.x;
       r[4 * g + 1] = v.y;
@@ -309,12 +317,12 @@ __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
       r[4 * g + 3] = v.w;
     }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < kSlChunk; ++i) {
       a[i] = lds(par + (PAIR ? (r[i] & 0xFFFFu) : r[i]));
       b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) f(i & 3, a[i], b[i]);
+    for (int i = 0; i < kSlChunk; ++i) f(i & 3, a[i], b[i]);
   }
   for (; k < n; k += 4, R.adv4(1)) {
     const uint4 v = R.get4(0);
@@ -576,6 +584,54 @@ __device__ ZC eval_table(const DevView& V, int t, const uint64_t (&X)[W], const 
   return z;
 }
 
+// Value of a FLOAT table (complex double): per class, the exact factors give
+// w^J sqrt2^S (or vanish) as in the SCALAR layout, the arbitrary-angle
+// factors give e^(i pi phi) with phi the sum of the angles whose parity is 1,
+// and the class adds coef w^J sqrt2^S e^(i pi phi).
+struct ZF {
+  double re, im;
+};
+
+template <int W>
+__device__ ZF eval_table_f(const DevView& V, int t, const uint64_t (&X)[W]) {
+  const DTable tb = V.tab[t];
+  uint64_t P0 = 0, P1 = 0, P2 = 0, P3 = 0;
+  for (uint32_t q = 1; q < tb.n_par; ++q) {
+    const uint64_t bit = (uint64_t)parity_w<W>(V.par + (size_t)(tb.par_off + q) * V.W, X, V.W) << (q & 63);
+    if (q < 64) P0 |= bit;
+    else if (q < 128) P1 |= bit;
+    else if (q < 192) P2 |= bit;
+    else P3 |= bit;
+  }
+  auto pbit = [&](uint32_t i) -> uint32_t {
+    const uint64_t w = i < 128 ? (i < 64 ? P0 : P1) : (i < 192 ? P2 : P3);
+    return (uint32_t)((w >> (i & 63)) & 1);
+  };
+  ZF z{0.0, 0.0};
+  for (uint32_t q = 0; q < tb.n_cls; ++q) {
+    const DClass& C = V.cls[tb.cls_off + q];
+    const uint32_t fo = C.fac_off, nf = C.n_fac;
+    uint32_t acc = 0;
+    for (uint32_t k = 0; k < nf; ++k) {
+      const uint32_t ix = __ldg(V.fidx + fo + k);
+      const uint32_t a = pbit(ix & 0xFF), b = pbit((ix >> 8) & 0xFF);
+      acc += __ldg(V.finc + (size_t)(fo + k) * 4 + (a | (b << 1)));
+    }
+    if (acc >> 21) continue;  // some factor vanished
+    double phi = (double)(acc & 7) * 0.25;  // w^J = e^(i pi J / 4)
+    for (int k = 0; k < C.pad; ++k)
+      if (pbit(__ldg(V.ffidx + C.j0 + k))) phi += __ldg(V.ffang + C.j0 + k);
+    const int S = (int)((acc >> 11) & 0x3FF);
+    const double m = ldexp((S & 1) ? 1.4142135623730951 : 1.0, S >> 1);
+    double sn, cs;
+    sincospi(phi, &sn, &cs);
+    const double cr = __longlong_as_double(C.c[0]), ci = __longlong_as_double(C.c[1]);
+    z.re += m * (cr * cs - ci * sn);
+    z.im += m * (cr * sn + ci * cs);
+  }
+  return z;
+}
+
 // the power of w that makes a chain's normalisation real and positive
 __device__ __forceinline__ int chain_rotation(const ZC& z, int* st) {
   for (int rot = 0; rot < 8; ++rot) {
@@ -712,6 +768,19 @@ __device__ __forceinline__ void dump_eval(long long* rec, int t, const ZC& z, co
     if (w < ws) rec[kDumpHead + w] = (long long)X[w];
 }
 
+template <int W>
+__device__ __forceinline__ void dump_eval_f(long long* rec, int t, const ZF& z, const uint64_t (&X)[W], int ws) {
+  rec[0] = t;
+  rec[1] = __double_as_longlong(z.re);
+  rec[2] = __double_as_longlong(z.im);
+  rec[3] = 0;
+  rec[4] = 0;
+  rec[5] = kDumpFloat;
+#pragma unroll
+  for (int w = 0; w < W; ++w)
+    if (w < ws) rec[kDumpHead + w] = (long long)X[w];
+}
+
 // One shot s of a launch (global shot index shot0 + s), records at row s.
 // Every lane of a warp calls it together (sliced tables are evaluated by the
 // whole warp); lanes past the end of the launch have valid = false and
@@ -737,7 +806,21 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const Round
   // 2-3. outputs in autoregressive order (Algorithm 1 per chain)
   RV pp[kMaxChains];
   int rot[kMaxChains];
+  // chains with arbitrary rotations: P_prev and the normalisation's value
+  // (its phase is the chain's common phase, its modulus the first P_prev)
+  double fprev[kMaxChains], fnre[kMaxChains], fnim[kMaxChains], fnmag[kMaxChains];
   for (int c = 0; c < V.n_chains; ++c) {
+    if (V.chain_float[c]) {
+      const ZF z = eval_table_f<W>(V, V.chain_norm[c], X);
+      if (DBG && dump) dump_eval_f<W>(dump + (size_t)drow * nd++, V.chain_norm[c], z, X, V.W);
+      const double m = sqrt(z.re * z.re + z.im * z.im);
+      if (!(m > 0.0)) st |= ST_ZERO_PROB;
+      fnre[c] = z.re;
+      fnim[c] = z.im;
+      fnmag[c] = m;
+      fprev[c] = m;
+      continue;
+    }
     const ZC z = eval_table<W, SL>(V, V.chain_norm[c], X, sm);
     if (DBG && dump) dump_eval<W>(dump + (size_t)drow * nd++, V.chain_norm[c], z, X, V.W);
     rot[c] = chain_rotation(z, &st);
@@ -789,6 +872,27 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const Round
       bit = get_xbit<W>(X, o.a) ^ o.cst;
     } else if (o.kind == OUT_MASK) {
       bit = parity_w<W>(V.omask + o.a, X, V.W) ^ o.cst;
+    } else if (V.chain_float[o.chain]) {
+      // Algorithm 1 in double precision; the ratio is rounded to FP32 before
+      // the comparison with U / 2^32
+      const int c = o.chain;
+      set_xbit<W>(X, o.a, true);
+      const ZF z1 = eval_table_f<W>(V, o.table, X);
+      if (DBG && dump) dump_eval_f<W>(dump + (size_t)drow * nd++, o.table, z1, X, V.W);
+      const double p1 = (z1.re * fnre[c] + z1.im * fnim[c]) / fnmag[c];
+      if (!(fprev[c] > 0.0)) st |= ST_ZERO_PROB;
+      uint32_t u[4];
+      philox4x32_10(c0, c1, 1u, (uint32_t)(i >> 2), rk, u);
+      const uint32_t q4 = (uint32_t)i & 3;
+      const uint32_t U = q4 == 0 ? u[0] : q4 == 1 ? u[1] : q4 == 2 ? u[2] : u[3];
+      const float q = __double2float_rn(p1 / fprev[c]);
+      bit = (double)U < (double)q * 4294967296.0;
+      if (bit) {
+        fprev[c] = p1;
+      } else {
+        fprev[c] = fprev[c] - p1;
+        set_xbit<W>(X, o.a, false);
+      }
     } else {
       set_xbit<W>(X, o.a, true);
       const ZC z1 = eval_table<W, SL>(V, o.table, X, sm);
@@ -798,7 +902,8 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const Round
       if (sign_xy(pv.A, pv.B, &st) <= 0) st |= ST_ZERO_PROB;
       uint32_t u[4];
       philox4x32_10(c0, c1, 1u, (uint32_t)(i >> 2), rk, u);
-      const uint32_t U = u[i & 3];
+      const uint32_t q4 = (uint32_t)i & 3;
+      const uint32_t U = q4 == 0 ? u[0] : q4 == 1 ? u[1] : q4 == 2 ? u[2] : u[3];
       // bit = 1 iff U * P_prev < 2^32 * P_1
       const int e = min(pv.e, p1.e + 32);
       const __int128 LA = shl_chk(pv.A * (__int128)U, pv.e - e, &st);
@@ -874,12 +979,18 @@ extern __shared__ __align__(128) uint32_t g_warp_smem[];
 // blocks: occupancy hides the latency of the operation rows read through
 // L1), the others at 48 (10 blocks for the Philox-bound noise loop).  Wider X
 // needs 2W registers of its own, so the bounds relax with W.
+#ifndef TSIM_MINB_SL
+#define TSIM_MINB_SL 6
+#endif
+#ifndef TSIM_MINB_SL_BATCH
+#define TSIM_MINB_SL_BATCH 5
+#endif
 constexpr int min_blocks(int W, bool sl) {
-  return sl ? (W <= 4 ? 6 : W <= 8 ? 4 : 2) : (W <= 4 ? 10 : W <= 8 ? 6 : 2);
+  return sl ? (W <= 4 ? TSIM_MINB_SL : W <= 8 ? 4 : 2) : (W <= 4 ? 10 : W <= 8 ? 6 : 2);
 }
 // the batched kernel keeps its work-item state live across the whole shot
 // loop: one block less for programs with sliced tables (96 registers)
-constexpr int min_blocks_batch(int W, bool sl) { return sl && W <= 4 ? 5 : min_blocks(W, sl); }
+constexpr int min_blocks_batch(int W, bool sl) { return sl && W <= 4 ? TSIM_MINB_SL_BATCH : min_blocks(W, sl); }
 
 // One program's launch: thread s samples shot shot0 + s.  DBG: shots with
 // dump_row[s] >= 0 also write a record of every table evaluation.

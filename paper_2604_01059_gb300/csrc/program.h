@@ -8,6 +8,7 @@
 // outputs drawn by Algorithm 1.  Every parity of the program is a mask over X.
 #pragma once
 #include <atomic>
+#include <complex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -18,16 +19,20 @@ namespace tsim {
 
 struct ProgFactor {
   int kind = 0, alpha = 0, beta = 0;    // FactorKind, angles in units of pi/4
+  double t = 0;                         // F_PHASE_F: e^(i pi t a), t in units of pi
   std::vector<uint64_t> u, v;           // parities a = <u, X>, b = <v, X>
 };
 
 struct ProgTerm {
-  int s0 = 0, j0 = 0;                   // c^t = w^j0 * sqrt2^s0
+  int s0 = 0, j0 = 0;                   // c^t = w^j0 * sqrt2^s0 (* e^(i pi fph))
+  double fph = 0;                       // constant phase of arbitrary rotations, units of pi
   std::vector<ProgFactor> f;
 };
 
 struct ProgTable {
   std::vector<ProgTerm> terms;
+  // some term has an arbitrary phase: the table is evaluated in floating point
+  bool is_float() const;
 };
 
 struct ProgOutput {
@@ -84,6 +89,8 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
 void save_program(const Program& p, const std::string& path);
 Program* load_program(const std::string& path);
 ZW eval_table_host(const Program& p, int t, const uint64_t* x);
+// any table (with or without arbitrary phases) in complex double
+std::complex<double> eval_table_host_c(const Program& p, int t, const uint64_t* x);
 // Noise sampling mode: 0 one word per channel, 1 geometric gaps, -1 the
 // cheaper of the two by expected random words per shot (groups are formed
 // from the channels' outcome-0 thresholds).  Does not re-pack device tables.

@@ -14,9 +14,11 @@
 //     S <signature words>                      one line per outcome: X ^= sig
 //   noise <mode> <groups>  mode 0: one word per channel; mode 1: geometric
 //                        gaps, then per group  G <Q> <n> <channel indices>
-//   tables <n>           then per table  T <terms>, per term  t <s0> <j0> <m>
-//     (c^t = w^j0 sqrt2^s0) and per factor
-//     f <kind> <alpha> <beta> <u words> <v words>
+//   tables <n>           then per table  T <terms> <float>, per term
+//     t <s0> <j0> <m> [<phase>]   (c^t = w^j0 sqrt2^s0 e^(i pi phase); the
+//                                   phase only in tables with float = 1)
+//     and per factor  f <kind> <alpha> <beta> <u words> <v words> [<t>]
+//     (kind 4, e^(i pi t a), carries its angle t in units of pi)
 //   detmap <n> / obsmap <n>   then  M <count> <measurement indices>
 //                             (measurement mode; 0 otherwise)
 //   meta nq <qubits> E <raw bits> nft <table f bits>
@@ -119,13 +121,24 @@ void save_program(const Program& p, const std::string& path) {
   }
   os << "tables " << p.tables.size() << "\n";
   for (const ProgTable& tb : p.tables) {
-    os << "T " << tb.terms.size() << "\n";
+    const bool fl = tb.is_float();
+    os << "T " << tb.terms.size() << " " << (fl ? 1 : 0) << "\n";
+    char num[40];
     for (const ProgTerm& tm : tb.terms) {
-      os << "t " << tm.s0 << " " << tm.j0 << " " << tm.f.size() << "\n";
+      os << "t " << tm.s0 << " " << tm.j0 << " " << tm.f.size();
+      if (fl) {
+        std::snprintf(num, sizeof num, " %.17g", tm.fph);
+        os << num;
+      }
+      os << "\n";
       for (const ProgFactor& f : tm.f) {
         os << "f " << f.kind << " " << f.alpha << " " << f.beta;
         put_words(os, f.u);
         put_words(os, f.v);
+        if (f.kind == 4) {
+          std::snprintf(num, sizeof num, " %.17g", f.t);
+          os << num;
+        }
         os << "\n";
       }
     }
@@ -247,12 +260,15 @@ Program* load_program(const std::string& path) {
   for (auto& tb : p->tables) {
     R.expect("T");
     long long nt = R.integer();
+    const long long fl = R.integer();
+    if (fl != 0 && fl != 1) fail(TSIM_ERR_PARSE, "bad table float flag");
     tb.terms.resize((size_t)nt);
     for (auto& tm : tb.terms) {
       R.expect("t");
       tm.s0 = (int)R.integer();
       tm.j0 = (int)R.integer();
       long long nf = R.integer();
+      if (fl) tm.fph = R.real();
       tm.f.resize((size_t)nf);
       for (auto& f : tm.f) {
         R.expect("f");
@@ -261,6 +277,11 @@ Program* load_program(const std::string& path) {
         f.beta = (int)R.integer();
         f.u = R.words();
         f.v = R.words();
+        if (f.kind < 0 || f.kind > 4) fail(TSIM_ERR_PARSE, "bad factor kind");
+        if (f.kind == 4) {
+          if (!fl) fail(TSIM_ERR_PARSE, "arbitrary phase factor in an exact table");
+          f.t = R.real();
+        }
       }
     }
   }

@@ -19,6 +19,27 @@
 
 namespace tsim {
 
+double angle_mod2(double t) {
+  t = std::fmod(t, 2.0);
+  if (t < 0) t += 2.0;
+  if (t >= 2.0 - kAngleTol) t = 0.0;
+  return t;
+}
+
+int angle_eighths(double t) {
+  const double q = angle_mod2(t) * 4.0;
+  const double r = std::nearbyint(q);
+  if (std::fabs(q - r) > 4.0 * kAngleTol) return -1;
+  return ((int)r) & 7;
+}
+
+bool Term::is_float() const {
+  if (fph != 0.0) return true;
+  for (const Factor& f : fac)
+    if (f.kind == F_PHASE_F) return true;
+  return false;
+}
+
 Form form_const(size_t np, int c) {
   Form f;
   f.params = Bits(np);
@@ -63,6 +84,7 @@ int Graph::add_var(int l) {
     cap = nc;
   }
   lam.push_back(l & 7);
+  ang.push_back(0.0);
   P.push_back(Bits(np));
   alive.push_back(1);
   uid.push_back(-1);
@@ -116,6 +138,8 @@ void Graph::add_factor(int kind, int alpha, int beta, const Bits& a, const Bits&
     case F_PHASE:
       if (!alpha || !a.any()) return;
       break;
+    case F_PHASE_F:
+      fail(TSIM_ERR_INTERNAL, "arbitrary phase factors are added by add_factor_f");
     case F_NODE:
       if (!a.any()) {
         switch (alpha) {  // 1 + w^alpha
@@ -145,6 +169,62 @@ void Graph::add_factor(int kind, int alpha, int beta, const Bits& a, const Bits&
   f.b = (kind == F_PI_PAIR || kind == F_PHASE_PAIR) ? b : Bits(np);
   if (f.b.nwords() < f.a.nwords()) f.b.w.resize(f.a.nwords(), 0);
   fac.push_back(std::move(f));
+}
+
+void Graph::add_factor_f(double t, const Bits& a) {
+  t = angle_mod2(t);
+  const int k = angle_eighths(t);
+  if (k >= 0) {
+    add_factor(F_PHASE, k, 0, a, Bits());
+    return;
+  }
+  if (!a.any()) return;
+  Factor f;
+  f.kind = F_PHASE_F;
+  f.t = t;
+  f.a = a;
+  f.b = Bits(np);
+  if (f.b.nwords() < f.a.nwords()) f.b.w.resize(f.a.nwords(), 0);
+  fac.push_back(std::move(f));
+}
+
+void Graph::set_angle(int v, double t) {
+  t = angle_mod2(t);
+  const int k = angle_eighths(t);
+  if (k >= 0) {
+    lam[(size_t)v] = (lam[(size_t)v] + k) & 7;
+    ang[(size_t)v] = 0.0;
+  } else {
+    ang[(size_t)v] = t;
+  }
+}
+
+void Graph::add_phase_f(double t, Form L) {
+  t = angle_mod2(t);
+  const int k = angle_eighths(t);
+  if (k >= 0) {  // a multiple of pi/4: exact
+    add_phase(k, L);
+    return;
+  }
+  if (L.c) {  // e^(i pi t (1 + g)) = e^(i pi t) e^(-i pi t g)
+    fph = angle_mod2(fph + t);
+    t = angle_mod2(-t);
+    L.c = 0;
+  }
+  if (L.vars.empty()) {
+    if (L.params.any()) add_factor_f(t, L.params);
+    return;
+  }
+  if (L.vars.size() == 1 && !L.params.any()) {
+    set_angle(L.vars[0], ang[(size_t)L.vars[0]] + t);
+    return;
+  }
+  // phase gadget: new variable y = L, carrying the angle
+  int y = add_var(0);
+  Form h = L;
+  form_xor(h, form_var(np, y));
+  hub(h);
+  ang[(size_t)y] = t;
 }
 
 void Graph::add_phase(int theta, Form L) {
@@ -210,17 +290,19 @@ void Graph::hub(const Form& L) {
 
 bool Graph::can_substitute(int y, const Form& L) const {
   if (std::binary_search(L.vars.begin(), L.vars.end(), y)) return false;
-  if ((lam[(size_t)y] & 1) == 0) return true;
+  if (!non_clifford(y)) return true;
   return L.vars.empty() || (L.vars.size() == 1 && !L.params.any());
 }
 
 void Graph::substitute(int y, const Form& L) {
   if (!can_substitute(y, L)) fail(TSIM_ERR_INTERNAL, "invalid substitution");
   int th = lam[(size_t)y];
+  const double ty = ang[(size_t)y];
   Bits py = P[(size_t)y];
   std::vector<int> nb = nbrs(y);
   kill(y);
   add_phase(th, L);
+  if (ty != 0.0) add_phase_f(ty, L);
   if (py.any()) add_sign(form_params(py), L);
   for (int t : nb) add_sign(form_var(np, t), L);
 }
@@ -258,7 +340,7 @@ void Graph::simplify() {
   while (changed && !zero) {
     changed = false;
     for (int v = 0; v < n; ++v) {
-      if (!alive[(size_t)v]) continue;
+      if (!alive[(size_t)v] || ang[(size_t)v] != 0.0) continue;
       int l = lam[(size_t)v];
       if (l == 2 || l == 6) {
         lcomp(v);
@@ -274,6 +356,7 @@ void Graph::simplify() {
       }
       int best = -1, cliff = -1;
       for (int u : nb) {
+        if (ang[(size_t)u] != 0.0) continue;
         int lu = lam[(size_t)u];
         if (lu == 0 || lu == 4) { best = u; break; }
         if ((lu == 2 || lu == 6) && cliff < 0) cliff = u;
@@ -297,6 +380,7 @@ void Graph::compact() {
   for (int v = 0; v < n; ++v)
     if (alive[(size_t)v]) {
       int nv = h.add_var(lam[(size_t)v]);
+      h.ang[(size_t)nv] = ang[(size_t)v];
       h.P[(size_t)nv] = P[(size_t)v];
       h.uid[(size_t)nv] = uid[(size_t)v];
     }
@@ -307,37 +391,54 @@ void Graph::compact() {
   }
   h.s2 = s2;
   h.ph = ph;
+  h.fph = fph;
   h.zero = zero;
   h.fac = std::move(fac);
   *this = std::move(h);
 }
 
 void Graph::fold_phase_factors() {
-  // merge w^(al1 a) w^(al2 a) into one factor per parity; drop trivial ones
+  // merge w^(al1 a) w^(al2 a) into one factor per parity, and the arbitrary
+  // phases e^(i pi t1 a) e^(i pi t2 a) likewise (an arbitrary sum that
+  // reaches a multiple of pi/4 joins the exact factor); drop trivial ones
   std::vector<Factor> out;
-  for (auto& f : fac) {
-    if (f.kind == F_PHASE) {
-      bool merged = false;
-      for (auto& g : out)
-        if (g.kind == F_PHASE && g.a == f.a) {
-          g.alpha = (g.alpha + f.alpha) & 7;
-          merged = true;
-          break;
+  for (int pass = 0; pass < 2; ++pass) {
+    out.clear();
+    for (auto& f : fac) {
+      if (f.kind == F_PHASE || f.kind == F_PHASE_F) {
+        bool merged = false;
+        for (auto& g : out)
+          if (g.kind == f.kind && g.a == f.a) {
+            if (f.kind == F_PHASE) g.alpha = (g.alpha + f.alpha) & 7;
+            else g.t = angle_mod2(g.t + f.t);
+            merged = true;
+            break;
+          }
+        if (!merged) out.push_back(f);
+      } else {
+        out.push_back(f);
+      }
+    }
+    fac.clear();
+    for (auto& f : out) {
+      if (f.kind == F_PHASE_F) {
+        const int k = angle_eighths(f.t);
+        if (k >= 0) {
+          f.kind = F_PHASE;
+          f.alpha = k;
+          f.t = 0;
         }
-      if (!merged) out.push_back(f);
-    } else {
-      out.push_back(f);
+      }
+      if (!(f.kind == F_PHASE && f.alpha == 0)) fac.push_back(std::move(f));
     }
   }
-  fac.clear();
-  for (auto& f : out)
-    if (!(f.kind == F_PHASE && f.alpha == 0)) fac.push_back(std::move(f));
 }
 
 Term Graph::as_term() const {
   Term t;
   t.s2 = s2;
   t.ph = ph;
+  t.fph = fph;
   t.fac = fac;
   return t;
 }
@@ -357,6 +458,18 @@ ZW factor_value(const Factor& f, int a, int b) {
   fail(TSIM_ERR_INTERNAL, "bad factor kind");
 }
 
+std::complex<double> zw_to_complex(const ZW& z) {
+  const double r = std::sqrt(0.5);
+  std::complex<double> v((double)z.c[0] + r * ((double)z.c[1] - (double)z.c[3]),
+                         r * ((double)z.c[1] + (double)z.c[3]) + (double)z.c[2]);
+  return v * std::pow(std::sqrt(2.0), z.k);
+}
+
+std::complex<double> factor_value_c(const Factor& f, int a, int b) {
+  if (f.kind == F_PHASE_F) return a ? std::polar(1.0, M_PI * f.t) : std::complex<double>(1.0, 0.0);
+  return zw_to_complex(factor_value(f, a, b));
+}
+
 static ZW scalar_value(int s2, int ph, const std::vector<Factor>& fac, const Bits& pv) {
   ZW v = ZW::omega(ph);
   v.k = s2;
@@ -367,7 +480,44 @@ static ZW scalar_value(int s2, int ph, const std::vector<Factor>& fac, const Bit
   return v;
 }
 
-ZW term_value(const Term& t, const Bits& pv) { return scalar_value(t.s2, t.ph, t.fac, pv); }
+ZW term_value(const Term& t, const Bits& pv) {
+  if (t.is_float()) fail(TSIM_ERR_INTERNAL, "exact value of a term with an arbitrary phase");
+  return scalar_value(t.s2, t.ph, t.fac, pv);
+}
+
+static std::complex<double> scalar_value_c(int s2, int ph, double fph, const std::vector<Factor>& fac,
+                                           const Bits& pv) {
+  ZW c = ZW::omega(ph);
+  c.k = s2;
+  std::complex<double> v = zw_to_complex(c) * std::polar(1.0, M_PI * fph);
+  for (const Factor& f : fac) v *= factor_value_c(f, f.a.dot(pv), f.b.dot(pv));
+  return v;
+}
+
+std::complex<double> term_value_c(const Term& t, const Bits& pv) { return scalar_value_c(t.s2, t.ph, t.fph, t.fac, pv); }
+
+std::complex<double> brute_value_c(const Graph& g, const Bits& pv) {
+  if (g.zero) return 0.0;
+  std::vector<int> vs;
+  for (int v = 0; v < g.n; ++v)
+    if (g.alive[(size_t)v]) vs.push_back(v);
+  if (vs.size() > 20) fail(TSIM_ERR_INTERNAL, "brute force on a large graph");
+  std::complex<double> sum = 0.0;
+  for (uint64_t z = 0; z < (1ull << vs.size()); ++z) {
+    int phase = 0;
+    double fl = 0.0;
+    for (size_t i = 0; i < vs.size(); ++i) {
+      if (!((z >> i) & 1)) continue;
+      int v = vs[i];
+      phase += g.lam[(size_t)v] + 4 * g.P[(size_t)v].dot(pv);
+      fl += g.ang[(size_t)v];
+      for (size_t j = i + 1; j < vs.size(); ++j)
+        if (((z >> j) & 1) && g.edge(v, vs[j])) phase += 4;
+    }
+    sum += std::polar(1.0, M_PI * (phase / 4.0 + fl));
+  }
+  return sum * scalar_value_c(g.s2, g.ph, g.fph, g.fac, pv);
+}
 
 ZW brute_value(const Graph& g, const Bits& pv) {
   if (g.zero) return ZW();
@@ -454,7 +604,7 @@ struct Decomposer {
     if (g.zero) return;
     std::vector<int> odd;
     for (int v = 0; v < g.n; ++v)
-      if (g.alive[(size_t)v] && (g.lam[(size_t)v] & 1)) odd.push_back(v);
+      if (g.alive[(size_t)v] && g.non_clifford(v)) odd.push_back(v);
     if (odd.empty()) {
       if (g.num_alive() != 0) fail(TSIM_ERR_INTERNAL, "Clifford diagram did not reduce to a scalar");
       st->leaves++;
@@ -464,7 +614,7 @@ struct Decomposer {
     if (depth == 0 || g.num_alive() * 2 < g.n) g.compact();
     odd.clear();
     for (int v = 0; v < g.n; ++v)
-      if (g.alive[(size_t)v] && (g.lam[(size_t)v] & 1)) odd.push_back(v);
+      if (g.alive[(size_t)v] && g.non_clifford(v)) odd.push_back(v);
     auto score = [&](int v) {
       const int u = g.uid[(size_t)v];
       if (u >= 0 && u == first) return -1e300;
@@ -478,10 +628,14 @@ struct Decomposer {
     // odd spiders has phases that cancel, lam_x + lam_y = 0 mod 8: such a
     // pair -- typically a T gate's ket and bra copies in the doubled diagram
     // -- fuses away in the pair split, which then beats Cat5 by far)
-    if ((policy == 0 || policy == 1 || policy == 4) && odd.size() >= 5) {
+    // (Cat5 at theta = pi/4 only: a group with an arbitrary angle is split in pairs)
+    if ((policy == 0 || policy == 1 || policy == 4) && odd.size() >= 5 && g.ang[(size_t)odd[0]] == 0.0 &&
+        g.ang[(size_t)odd[1]] == 0.0 && g.ang[(size_t)odd[2]] == 0.0 && g.ang[(size_t)odd[3]] == 0.0 &&
+        g.ang[(size_t)odd[4]] == 0.0) {
       bool cancelling = false;
       for (size_t i = 0; policy != 4 && i + 1 < odd.size() && !cancelling; ++i)
-        cancelling = ((g.lam[(size_t)odd[i]] + g.lam[(size_t)odd[i + 1]]) & 7) == 0;
+        cancelling = ((g.lam[(size_t)odd[i]] + g.lam[(size_t)odd[i + 1]]) & 7) == 0 &&
+                     angle_eighths(g.ang[(size_t)odd[i]] + g.ang[(size_t)odd[i + 1]]) == 0;
       if (!cancelling) {
         cat5(g, odd.data(), depth);
         return;
@@ -541,10 +695,10 @@ void cut_features(const Graph& g, std::vector<float>& X, std::vector<int>& rowpt
     int odd_nb = 0;
     for (int u : nb) {
       col.push_back(idx[(size_t)u]);
-      odd_nb += g.lam[(size_t)u] & 1;
+      odd_nb += g.non_clifford(u);
     }
     rowptr[(size_t)i + 1] = (int)col.size();
-    x[0] = (float)(l & 1);                       // non-Clifford
+    x[0] = (float)g.non_clifford(v);            // non-Clifford
     x[1] = (float)(l == 0 || l == 4);            // Pauli
     x[2] = (float)(l == 2 || l == 6);            // proper Clifford
     x[3 + l] = 1.0f;                             // phase mod 2pi in units of pi/4

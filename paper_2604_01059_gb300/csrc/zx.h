@@ -17,6 +17,7 @@
 // variable at a time; stabilizer decomposition (Appendix "Stabilizer
 // decompositions") as splitting a sum into Clifford branches.
 #pragma once
+#include <complex>
 #include <vector>
 
 #include "common.h"
@@ -28,14 +29,24 @@ enum FactorKind {
   F_PHASE_PAIR = 0,  // 1 + w^(al+4a) + w^(be+4b) - w^(al+be+4a+4b)     Eq. phase_pair
   F_NODE = 1,        // 1 + w^(al+4a)                                    "Node"
   F_PHASE = 2,       // w^(al*a)  (al = +-2: "Half-pi"; al = 4: a sign)
-  F_PI_PAIR = 3      // (-1)^(a b)                                       "pi-pair"
+  F_PI_PAIR = 3,     // (-1)^(a b)                                       "pi-pair"
+  F_PHASE_F = 4      // e^(i pi t a) for an arbitrary angle t (rotation gates)
 };
 
 struct Factor {
   int kind = 0;
   int alpha = 0, beta = 0;
-  Bits a, b;  // parities over the diagram's parameters
+  double t = 0;  // F_PHASE_F: the angle, in units of pi
+  Bits a, b;     // parities over the diagram's parameters
 };
+
+// Angles of arbitrary rotations, in units of pi, reduced to [0, 2); an angle
+// within kAngleTol of a multiple of 1/4 is that multiple (it joins the exact
+// phases in units of pi/4).
+constexpr double kAngleTol = 1e-12;
+double angle_mod2(double t);
+// k in 0..7 when t is k/4 (mod 2) within kAngleTol, else -1
+int angle_eighths(double t);
 
 // Affine GF(2) form: XOR of variables, parameters and a constant bit.
 struct Form {
@@ -52,13 +63,17 @@ void form_xor(Form& a, const Form& b);
 
 struct Term {
   int s2 = 0, ph = 0;
+  double fph = 0;  // a further constant phase e^(i pi fph) from arbitrary rotations
   std::vector<Factor> fac;
+  bool is_float() const;
 };
 
 struct Graph {
   size_t np = 0;
   int n = 0, cap = 0;
   std::vector<int> lam;
+  std::vector<double> ang;  // arbitrary part of each spider's phase: e^(i pi ang z), 0 for Clifford+T
+  double fph = 0;           // constant phase e^(i pi fph)
   std::vector<Bits> P;
   std::vector<std::vector<uint64_t>> adj;
   std::vector<char> alive;
@@ -79,9 +94,17 @@ struct Graph {
 
   // multiply the diagram by w^(theta * L)
   void add_phase(int theta, Form L);
+  // multiply the diagram by e^(i pi t L) for an arbitrary angle t
+  void add_phase_f(double t, Form L);
+  // the spider is not Clifford: odd phase or an arbitrary angle
+  bool non_clifford(int v) const { return (lam[(size_t)v] & 1) || ang[(size_t)v] != 0.0; }
   // multiply by (-1)^(F * G)
   void add_sign(const Form& F, const Form& G);
   void add_factor(int kind, int alpha, int beta, const Bits& a, const Bits& b);
+  // multiply by e^(i pi t a) (a multiple of pi/4 becomes an exact factor)
+  void add_factor_f(double t, const Bits& a);
+  // set a spider's arbitrary angle (a multiple of pi/4 joins lam)
+  void set_angle(int v, double t);
   // multiply by delta(L = 0), as (1/2) sum_w (-1)^(w L)
   void hub(const Form& L);
   bool can_substitute(int y, const Form& L) const;
@@ -98,8 +121,11 @@ struct Graph {
   Term as_term() const;
 };
 
-// value of one factor for parity values a, b
+// value of one factor for parity values a, b (exact kinds only)
 ZW factor_value(const Factor& f, int a, int b);
+// value of any factor, in complex double
+std::complex<double> factor_value_c(const Factor& f, int a, int b);
+std::complex<double> zw_to_complex(const ZW& z);
 
 struct DecompStats {
   uint64_t terms = 0;
@@ -136,5 +162,8 @@ Graph random_zx_diagram(uint64_t seed, int t, int c);
 // Brute-force value of a small graph for one parameter assignment (tests).
 ZW brute_value(const Graph& g, const Bits& pv);
 ZW term_value(const Term& t, const Bits& pv);
+// the same in complex double, for graphs with arbitrary angles
+std::complex<double> brute_value_c(const Graph& g, const Bits& pv);
+std::complex<double> term_value_c(const Term& t, const Bits& pv);
 
 }  // namespace tsim

@@ -60,18 +60,26 @@ def read(path):
         groups.append((q, [int(tok()) for _ in range(m)]))
     expect("tables")
     tables = []
+    table_float = []
     for _ in range(int(tok())):
         expect("T")
         terms = []
-        for _ in range(int(tok())):
+        nt, fl = int(tok()), int(tok())
+        for _ in range(nt):
             expect("t")
             s0, j0, m = int(tok()), int(tok()), int(tok())
+            if fl:
+                tok()  # the term's arbitrary phase (floating-point tables)
             facs = []
             for _ in range(m):
                 expect("f")
-                facs.append((int(tok()), int(tok()), int(tok()), words(), words()))
+                f = (int(tok()), int(tok()), int(tok()), words(), words())
+                if f[0] == 4:
+                    tok()  # the factor's arbitrary angle
+                facs.append(f)
             terms.append((s0, j0, facs))
         tables.append(terms)
+        table_float.append(fl)
     maps = {}
     for name in ("detmap", "obsmap"):
         expect(name)
@@ -98,7 +106,7 @@ def read(path):
             cols.append(words())
         raw.append((nb, probs, cols))
     expect("end")
-    return dict(mode=mode, outputs=outs, chains=chains, channels=channels, tables=tables,
+    return dict(mode=mode, outputs=outs, chains=chains, channels=channels, tables=tables, table_float=table_float,
                 noise_mode=noise_mode, groups=groups,
                 raw=raw, meta=meta, **hdr, **maps)
 

@@ -41,7 +41,7 @@ def program_text(*, mode="detectors", nx=1, nf=0, nr=0, nmeas=0, ndet=0, nobs=0,
             L.append(f"G {Q} {len(members)} " + " ".join(str(c) for c in members))
     L.append(f"tables {len(tables)}")
     for terms in tables:
-        L.append(f"T {len(terms)}")
+        L.append(f"T {len(terms)} 0")
         for s0, j0, facs in terms:
             L.append(f"t {s0} {j0} {len(facs)}")
             for kind, a, b, u, v in facs:

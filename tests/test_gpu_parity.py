@@ -95,6 +95,31 @@ def test_config2_full_size_sampled_shots(tmp_path, p, noise):
         assert g["accept"][s] == o["accept"][0]
 
 
+@pytest.mark.parametrize("noise", [1, 0])
+def test_config2_measurement_mode_full_size(tmp_path, noise):
+    # measurement sampling of the benchmark circuit (147 records per shot, 37
+    # drawn by Algorithm 1 in 4 chains: the long autoregressive chains that
+    # detector sampling avoids): the full 10^6-shot launch, 256 shots spread
+    # over it checked against the oracle one at a time, and a ragged block
+    prog = T.Program(Wk.config2_circuit(p=2e-3), mode=T.MODE_MEASUREMENTS)
+    prog.set_noise_sampling(noise)
+    assert prog.info["num_random"] >= 30 and prog.info["num_chains"] >= 2
+    path = str(tmp_path / "c2m.prog")
+    prog.save(path)
+    shots, seed = 1_000_000, 4
+    g = _gpu(prog, shots, seed, 0)
+    orc = OracleProgram(path)
+    rng = random.Random(77 + noise)
+    idx = sorted(set([0, shots - 1] + [rng.randrange(shots) for _ in range(254)]))
+    for s in idx:
+        o = orc.sample(seed, s, 1)
+        np.testing.assert_array_equal(g["meas"][s], o["meas"][0])
+        np.testing.assert_array_equal(g["det"][s], o["det"][0])
+        np.testing.assert_array_equal(g["obs"][s], o["obs"][0])
+        assert g["accept"][s] == o["accept"][0]
+    _compare(prog, path, 1025, seed=seed + 1, offset=shots)
+
+
 def test_config3_color_code_t_check(tmp_path):
     # 19 qubits, 42 T/T_DAG, 3 check rounds (16383 stabilizer terms; the
     # oracle needs ~0.3 s per shot): a ragged two-block launch checked shot
