@@ -41,15 +41,30 @@
 
 namespace tsim {
 
+// The key schedule of Philox4x32-10: round r uses key + r (0x9E3779B9,
+// 0xBB67AE85).  RoundKeys holds all ten (a kernel parameter of one launch);
+// SeedKey derives them from the key, one add per round (no registers held
+// across a persistent loop that serves many programs).
+struct SeedKey {
+  uint32_t k0, k1;
+  __device__ __forceinline__ uint32_t key0(int r) const { return k0 + (uint32_t)r * 0x9E3779B9u; }
+  __device__ __forceinline__ uint32_t key1(int r) const { return k1 + (uint32_t)r * 0xBB67AE85u; }
+};
+__device__ __forceinline__ uint32_t key0_of(const RoundKeys& rk, int r) { return rk.k0[r]; }
+__device__ __forceinline__ uint32_t key1_of(const RoundKeys& rk, int r) { return rk.k1[r]; }
+__device__ __forceinline__ uint32_t key0_of(const SeedKey& sk, int r) { return sk.key0(r); }
+__device__ __forceinline__ uint32_t key1_of(const SeedKey& sk, int r) { return sk.key1(r); }
+
+template <class K>
 __device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                              const RoundKeys& rk, uint32_t o[4]) {
+                                              const K& rk, uint32_t o[4]) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
     const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-    c0 = hi1 ^ c1 ^ rk.k0[r];
+    c0 = hi1 ^ c1 ^ key0_of(rk, r);
     c1 = lo1;
-    c2 = hi0 ^ c3 ^ rk.k1[r];
+    c2 = hi0 ^ c3 ^ key1_of(rk, r);
     c3 = lo0;
   }
   o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
@@ -303,6 +318,12 @@ static_assert(kSlChunk % 4 == 0 && kSlChunk >= 4, "rows per chunk must be a mult
 // loads and parity loads are all issued before the updates; f(way, a, b)
 // spreads consecutive rows over 4 independent accumulators (way = row & 3)
 // so that the update chains overlap.
+#ifndef TSIM_SL_WAYS
+#define TSIM_SL_WAYS 4
+#endif
+constexpr int kSlWays = TSIM_SL_WAYS;
+static_assert(kSlWays == 2 || kSlWays == 4, "2 or 4 accumulator ways");
+
 template <bool PAIR, class Rows, class F>
 __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
   int k = 0;
@@ -322,7 +343,7 @@ __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
       b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < kSlChunk; ++i) f(i & 3, a[i], b[i]);
+    for (int i = 0; i < kSlChunk; ++i) f(i % kSlWays, a[i], b[i]);
   }
   for (; k < n; k += 4, R.adv4(1)) {
     const uint4 v = R.get4(0);
@@ -334,7 +355,7 @@ __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
       b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) f(i, a[i], b[i]);
+    for (int i = 0; i < 4; ++i) f(i % kSlWays, a[i], b[i]);
   }
 }
 
@@ -354,7 +375,7 @@ __device__ __forceinline__ void sl_batch(const DSBatch& B, Rows R, uint32_t par,
   Z = 0u - ((~B.valid >> lane) & 1u);
   // per way: J2 flips k, vanishing flags z, and a 2-bit counter (c1, c2) of
   // the rows that add 2 to J (J2 flips and vanishing flags commute with it)
-  uint32_t k[4] = {0, 0, 0, 0}, z[4] = {0, 0, 0, 0}, c1[4] = {0, 0, 0, 0}, c2[4] = {0, 0, 0, 0};
+  uint32_t k[kSlWays] = {}, z[kSlWays] = {}, c1[kSlWays] = {}, c2[kSlWays] = {};
   sl_loop<false>(B.cnt[SL_XOR4], R, par, [&](int w, uint32_t a, uint32_t) { k[w] ^= a; });
   sl_loop<false>(B.cnt[SL_ADD2], R, par, [&](int w, uint32_t a, uint32_t) {
     c2[w] ^= c1[w] & a;
@@ -370,11 +391,16 @@ __device__ __forceinline__ void sl_batch(const DSBatch& B, Rows R, uint32_t par,
   sl_loop<false>(B.cnt[SL_ZERO], R, par, [&](int w, uint32_t a, uint32_t) { z[w] |= a; });
   sl_loop<false>(B.cnt[SL_ZEROC], R, par, [&](int w, uint32_t a, uint32_t) { z[w] |= ~a; });
   add2bit(c1[0], c2[0], c1[1], c2[1]);
-  add2bit(c1[2], c2[2], c1[3], c2[3]);
-  add2bit(c1[0], c2[0], c1[2], c2[2]);
+  if constexpr (kSlWays == 4) {
+    add2bit(c1[2], c2[2], c1[3], c2[3]);
+    add2bit(c1[0], c2[0], c1[2], c2[2]);
+    J2 ^= (k[0] ^ k[1]) ^ (k[2] ^ k[3]);
+    Z |= (z[0] | z[1]) | (z[2] | z[3]);
+  } else {
+    J2 ^= k[0] ^ k[1];
+    Z |= z[0] | z[1];
+  }
   add2bit(J1, J2, c1[0], c2[0]);
-  J2 ^= (k[0] ^ k[1]) ^ (k[2] ^ k[3]);
-  Z |= (z[0] | z[1]) | (z[2] | z[3]);
   // J += a (odd phases; rare): a three-plane increment
   sl_loop<false>(B.cnt[SL_ADD1], R, par, [&](int, uint32_t a, uint32_t) {
     const uint32_t cy = J0 & a;
@@ -688,8 +714,8 @@ __device__ __forceinline__ uint64_t get_xbits(const uint64_t (&X)[W], int x, int
 //    largest k <= (channels left) with U < T_k; a candidate's own word V,
 //    mapped onto [Q, 2^32), picks its outcome by the channel's thresholds.
 //    Words come from stream 2 in the order they are used.
-template <int W>
-__device__ __forceinline__ void sample_noise(const DevView& V, uint32_t c0, uint32_t c1, const RoundKeys& rk,
+template <int W, class K>
+__device__ __forceinline__ void sample_noise(const DevView& V, uint32_t c0, uint32_t c1, const K& rk,
                                              uint64_t (&X)[W]) {
   if (V.noise_mode == 0) {
     for (int c = 0; c < V.n_ch; c += 4) {
@@ -786,8 +812,8 @@ __device__ __forceinline__ void dump_eval_f(long long* rec, int t, const ZF& z, 
 // whole warp); lanes past the end of the launch have valid = false and
 // compute a shot whose records are not written.  sm: the warp's shared words.
 // DBG: dump (may be NULL) receives one record per table evaluation.
-template <int W, bool SL, bool DBG>
-__device__ void sample_one(const DevView& V, uint64_t s, bool valid, const RoundKeys& rk, uint64_t shot0,
+template <int W, bool SL, bool DBG, class K>
+__device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk, uint64_t shot0,
                            uint64_t* __restrict__ meas, uint64_t* __restrict__ det,
                            uint64_t* __restrict__ obs, uint8_t* __restrict__ accept, const SlSmem& sm,
                            long long* dump = nullptr) {
@@ -801,7 +827,7 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const Round
   uint64_t X[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) X[w] = 0;
-  sample_noise<W>(V, c0, c1, rk, X);
+  sample_noise<W, K>(V, c0, c1, rk, X);
 
   // 2-3. outputs in autoregressive order (Algorithm 1 per chain)
   RV pp[kMaxChains];
@@ -982,6 +1008,9 @@ extern __shared__ __align__(128) uint32_t g_warp_smem[];
 #ifndef TSIM_MINB_SL
 #define TSIM_MINB_SL 6
 #endif
+#ifndef TSIM_BATCH_SEEDKEY
+#define TSIM_BATCH_SEEDKEY 1
+#endif
 #ifndef TSIM_MINB_SL_BATCH
 #define TSIM_MINB_SL_BATCH 5
 #endif
@@ -1012,7 +1041,7 @@ __global__ void __launch_bounds__(kThreads, min_blocks(W, SL)) k_sample(DevView 
     const int r = s < nshots ? dump_row[s] : -1;
     if (r >= 0) rec = dump + (size_t)r * (size_t)dump_stride;
   }
-  sample_one<W, SL, DBG>(V, s, s < nshots, rk, shot0, meas, det, obs, accept, sm, rec);
+  sample_one<W, SL, DBG, RoundKeys>(V, s, s < nshots, rk, shot0, meas, det, obs, accept, sm, rec);
 }
 
 // ------------------------------------------------------- batched launch
@@ -1046,11 +1075,19 @@ __global__ void __launch_bounds__(kThreads, min_blocks_batch(W, SL)) k_batch(con
     const BatchProg& P = progs[lo];
     const uint64_t first = (it - item_start[lo]) * sb;
     const uint64_t last = min(first + sb, P.shots);
+#if TSIM_BATCH_SEEDKEY
+    const SeedKey rk{(uint32_t)P.seed, (uint32_t)(P.seed >> 32)};
+    for (uint64_t s0 = first; s0 < last; s0 += 32) {
+      const uint64_t s = s0 + lane;
+      sample_one<W, SL, false, SeedKey>(P.v, s, s < last, rk, P.shot_offset, P.meas, P.det, P.obs, P.accept, sm);
+    }
+#else
     const RoundKeys rk = round_keys(P.seed);
     for (uint64_t s0 = first; s0 < last; s0 += 32) {
       const uint64_t s = s0 + lane;
-      sample_one<W, SL, false>(P.v, s, s < last, rk, P.shot_offset, P.meas, P.det, P.obs, P.accept, sm);
+      sample_one<W, SL, false, RoundKeys>(P.v, s, s < last, rk, P.shot_offset, P.meas, P.det, P.obs, P.accept, sm);
     }
+#endif
   }
 }
 
