@@ -80,9 +80,10 @@ typedef struct {
                             phases that cancel (a T gate's ket and bra copies, which
                             the pair split removes together); PAIRS = BSS pairs only;
                             SINGLE_T = one T-state cut at a time; LEARNED = the three
-                            first cuts the cut-order network ranks best, each followed
-                            by the heuristic order, against the heuristic itself
-                            (kept only with strictly fewer terms). */
+                            cut units the cut-order network ranks best split first,
+                            each followed by the heuristic order, and every unit in the
+                            network's order, against the heuristic itself (kept only
+                            with strictly fewer terms). */
   uint64_t chi_budget;   /* maximum stabilizer terms per marginal; 0 = 1<<20 */
   int channel_reduction; /* 1 = apply the four steps of Appendix "Channel reduction" */
   uint64_t total_budget; /* maximum stabilizer terms summed over all marginals; 0 = none.
@@ -408,12 +409,14 @@ int tsim_cut_num_params(void);
 /* He-uniform weights, zero biases, from a splitmix64 stream of seed (host). */
 tsim_status tsim_cut_init_params(uint64_t seed, float* params);
 
-/* Training graphs: n_graphs seeded random Clifford+T ZX diagrams with
- * t_min..t_max non-Clifford spiders, reduced by the Clifford rewrites; up to
- * max_candidates non-Clifford spiders per graph are labelled with log2 of the
- * exact number of stabilizer terms the decomposition produces when that
- * spider is cut first (log2(2 budget) when it exceeds budget).  Written to
- * path in a binary format read by tsim_cut_train (host only, multithreaded). */
+/* Training graphs: n_graphs marginal diagrams of seeded random Clifford+T
+ * circuits with t_min..t_max T/T_DAG gates, reduced by the Clifford rewrites;
+ * up to max_candidates cut units per graph (a cancelling ket/bra pair of one
+ * T gate, or a single non-Clifford spider) are labelled, on their members,
+ * with log2 of the exact number of stabilizer terms the decomposition
+ * produces when that unit is split first and the rest follow the heuristic
+ * (log2(2 budget) when it exceeds budget).  Written to path in a binary
+ * format read by tsim_cut_train (host only, multithreaded). */
 tsim_status tsim_cut_dataset(uint64_t seed, int n_graphs, int t_min, int t_max, uint64_t budget,
                              int max_candidates, const char* path);
 
@@ -442,11 +445,25 @@ tsim_status tsim_cut_train(const char* dataset_path, int epochs, int batch_graph
 /* Register (params != NULL) the network used by TSIM_DECOMP_LEARNED on the
  * current device, or remove it (NULL).  Without a model, or when scoring
  * fails, LEARNED compiles with the heuristic order.  With a model the
- * compiler decomposes each marginal in the heuristic order and with each of
- * the three first cuts the network ranks best (the rest in the heuristic
- * order, each bounded by the fewest terms so far), and keeps a learned first
- * cut only when it has strictly fewer terms. */
+ * compiler decomposes each marginal in the heuristic order, with each of the
+ * three cut units the network ranks best split first (a unit is a
+ * cancelling ket/bra pair of one T gate, or a single spider; the rest in the
+ * heuristic order), and with every unit in the network's order (each bounded
+ * by the fewest terms so far), and keeps a learned order only when it has
+ * strictly fewer terms. */
 tsim_status tsim_cut_model_set(const float* params);
+
+/* Held-out comparison of cut orders, against the heuristic that judges them:
+ * n_graphs graphs drawn as tsim_cut_dataset draws them (seed, t_min..t_max),
+ * and per graph g, out[5 g + 0..4] = non-Clifford spiders, terms in the
+ * heuristic order, terms with TSIM_DECOMP_LEARNED (the registered network;
+ * the heuristic when none is registered), the geometric mean of the terms
+ * when one cut unit (a cancelling ket/bra pair, or a single non-Clifford
+ * spider) is split first and the rest follow the heuristic (up to 16 units:
+ * a random first unit), and the fewest of those and the heuristic's.
+ * Counts above budget read 2 budget.  Host and the current device (for
+ * scoring). */
+tsim_status tsim_cut_evaluate(uint64_t seed, int n_graphs, int t_min, int t_max, uint64_t budget, double* out);
 
 /* out[0] = scorer calls, out[1] = calls that produced scores, out[2] =
  * marginals where a learned first cut had strictly fewer terms, out[3] =

@@ -21,7 +21,7 @@ __all__ = [
     "tsim_raw_to_x", "tsim_program_save", "tsim_program_load", "tsim_program_free",
     "tsim_last_error", "tsim_selftest_rules", "tsim_measure_int_peak", "tsim_program_device_table_stats",
     "tsim_program_set_table_layout", "tsim_program_device_table_layout", "tsim_program_device_output_stats",
-    "tsim_selftest_sliced", "tsim_debug_sample", "tsim_program_set_noise_sampling", "tsim_program_noise_info",
+    "tsim_selftest_sliced", "tsim_cut_evaluate", "tsim_debug_sample", "tsim_program_set_noise_sampling", "tsim_program_noise_info",
     "tsim_program_device_bytes", "tsim_eval_table_float", "load_library",
     "MODE_DETECTORS", "MODE_MEASUREMENTS", "DECOMP_HEURISTIC", "DECOMP_LEARNED", "DECOMP_SINGLE_T", "DECOMP_PAIRS",
     "DECOMP_CAT5",
@@ -130,6 +130,7 @@ def _load(path):
     L.tsim_cut_train.argtypes = [ctypes.c_char_p, i32, i32, ctypes.c_float, u64, vp, vp]
     L.tsim_cut_model_set.argtypes = [vp]
     L.tsim_cut_policy_stats.argtypes = [vp]
+    L.tsim_cut_evaluate.argtypes = [u64, i32, i32, i32, u64, vp]
     for n in ("tsim_compile", "tsim_program_info", "tsim_program_table_terms", "tsim_program_table_stats", "tsim_sample",
               "tsim_sample_host", "tsim_sample_noalloc", "tsim_sample_batch", "tsim_batch_create",
               "tsim_batch_launch", "tsim_batch_info", "tsim_sync", "tsim_eval_table", "tsim_raw_to_x",
@@ -141,7 +142,7 @@ def _load(path):
               "tsim_cut_num_params",
               "tsim_cut_init_params",
               "tsim_cut_dataset", "tsim_cut_forward", "tsim_cut_loss_grad", "tsim_cut_adam_step", "tsim_cut_train",
-              "tsim_cut_model_set", "tsim_cut_policy_stats"):
+              "tsim_cut_model_set", "tsim_cut_policy_stats", "tsim_cut_evaluate"):
         getattr(L, n).restype = ctypes.c_int
     return L
 
@@ -484,6 +485,16 @@ def tsim_cut_policy_stats():
     out = (ctypes.c_uint64 * 4)()
     _check(load_library().tsim_cut_policy_stats(out))
     return tuple(out)
+
+
+def tsim_cut_evaluate(seed, n_graphs, t_min, t_max, budget):
+    """Held-out cut-order comparison: [graphs][5] = non-Clifford spiders,
+    heuristic terms, learned-policy terms, random-first-cut terms (geometric
+    mean), best-first-cut terms."""
+    import numpy as np
+    out = np.zeros((n_graphs, 5), dtype=np.float64)
+    _check(load_library().tsim_cut_evaluate(seed, n_graphs, t_min, t_max, budget, out.ctypes.data))
+    return out
 
 
 def read_cut_dataset(path):

@@ -715,6 +715,10 @@ tsim_status tsim_cut_model_set(const float* params) {
   return guard([&] { tsim::cutnet::set_model(params); });
 }
 
+tsim_status tsim_cut_evaluate(uint64_t seed, int n_graphs, int t_min, int t_max, uint64_t budget, double* out) {
+  return guard([&] { tsim::cutnet::evaluate_policy(seed, n_graphs, t_min, t_max, budget, out); });
+}
+
 tsim_status tsim_cut_policy_stats(uint64_t out[4]) {
   return guard([&] {
     if (!out) tsim::fail(TSIM_ERR_ARG, "NULL out");

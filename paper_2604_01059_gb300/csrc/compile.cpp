@@ -387,11 +387,13 @@ void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget,
     decompose(M, TSIM_DECOMP_HEURISTIC, out, st);
     return;
   }
-  // The network was trained to rank spiders as the FIRST cut (the rest in
-  // the heuristic order): decompose the heuristic order, then the three
-  // best-ranked first cuts, each with the fewest terms so far as its budget
-  // (a worse order stops as soon as it exceeds it).  The heuristic is the
-  // fallback and the judge: a learned first cut is kept only when it has
+  // The network was trained to rank cut units (a cancelling ket/bra pair of
+  // one T gate, or a single spider) by the terms when that unit is split
+  // first and the rest follow the heuristic: decompose the heuristic order,
+  // then the three best-ranked units first, then every unit in the
+  // network's order, each with the fewest terms so far as its budget (a
+  // worse order stops as soon as it exceeds it).  The heuristic is the
+  // fallback and the judge: a learned order is kept only when it has
   // strictly fewer terms.
   std::vector<Term> heuristic;
   DecompStats s2 = st;
@@ -402,41 +404,50 @@ void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget,
     if (e.code != TSIM_ERR_CHI_BUDGET) throw;
     ok2 = false;
   }
-  std::vector<int> cand;  // non-Clifford spiders by predicted term count
-  int own_first = -1;     // the heuristic's own first cut: the lowest odd spider
-  for (int v = 0; v < M.n; ++v)
-    if (M.alive[(size_t)v] && M.non_clifford(v)) {
-      if (own_first < 0) own_first = v;
-      cand.push_back(v);
-    }
-  std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
-    return scores[(size_t)a] < scores[(size_t)b];
-  });
+  // cut units (cancelling ket/bra pairs and single spiders), each scored by
+  // its best member; the heuristic splits them in id order (unit 0 first)
+  const std::vector<std::vector<int>> units = cut_units(M);
+  std::vector<double> us(units.size(), 1e300);
+  for (size_t u = 0; u < units.size(); ++u)
+    for (int v : units[u]) us[u] = std::min(us[u], scores[(size_t)v]);
+  std::vector<int> rank(units.size());
+  for (size_t u = 0; u < rank.size(); ++u) rank[u] = (int)u;
+  std::stable_sort(rank.begin(), rank.end(), [&](int a, int b) { return us[(size_t)a] < us[(size_t)b]; });
   std::vector<Term> learned;
   uint64_t t1 = t2;
   bool ok1 = false;
-  int tried = 0;
-  for (size_t k = 0; k < cand.size() && tried < 3; ++k) {
-    if (cand[k] == own_first) continue;
-    ++tried;
+  auto trial_order = [&](const std::vector<int>& order) {
     std::vector<Term> trial;
     DecompStats s1 = st;
     uint64_t tt = total ? *total : 0;
     s1.total = &tt;
     const uint64_t best = ok1 ? learned.size() : (ok2 ? heuristic.size() : 0);
     if (best) s1.budget = std::min<uint64_t>(s1.budget ? s1.budget : best, best > 1 ? best - 1 : 1);
+    const std::vector<double> sc = unit_order_scores(M, units, order);
     try {
-      decompose(M, TSIM_DECOMP_HEURISTIC, trial, s1, nullptr, cand[k]);
+      decompose(M, TSIM_DECOMP_LEARNED, trial, s1, &sc);
     } catch (const Error& e) {
       if (e.code != TSIM_ERR_CHI_BUDGET) throw;
-      continue;
+      return;
     }
     if (!ok1 || trial.size() < learned.size()) {
       learned.swap(trial);
       t1 = tt;
       ok1 = true;
     }
+  };
+  // the three best-ranked units split first (the rest in the heuristic
+  // order), then every unit in the network's order
+  int tried = 0;
+  for (size_t k = 0; k < rank.size() && tried < 3; ++k) {
+    if (rank[k] == 0) continue;  // the heuristic's own first unit
+    ++tried;
+    std::vector<int> order{rank[k]};
+    for (size_t u = 0; u < units.size(); ++u)
+      if ((int)u != rank[k]) order.push_back((int)u);
+    trial_order(order);
   }
+  if (units.size() > 2) trial_order(rank);
   if (!ok1 && !ok2) fail(TSIM_ERR_CHI_BUDGET, "stabilizer terms exceed the budget");
   g_cut_stats[1]++;
   const bool use_learned = ok1 && (!ok2 || learned.size() < heuristic.size());

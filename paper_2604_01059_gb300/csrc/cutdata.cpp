@@ -1,15 +1,18 @@
 // Training data for the learned cut order: ZX diagrams of the marginals of
 // seeded random Clifford+T circuits, each reduced by the Clifford rewrites
-// exactly as the compiler reduces it, with every candidate
-// non-Clifford spider labelled by the exact number of stabilizer terms the
-// compiler produces when that spider is in the first cut (the rest in the
-// heuristic order).  The labels are measured, not estimated: they are the
-// term counts of real decompositions, capped by a budget.
+// exactly as the compiler reduces it, with every candidate cut unit (a
+// cancelling ket/bra pair of one T gate, or a single non-Clifford spider)
+// labelled, on its members, by the exact number of stabilizer terms the
+// compiler produces when that unit is split first (the rest in the heuristic
+// order).  The labels are measured, not estimated: they are the term counts
+// of real decompositions, capped by a budget.
 #include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <thread>
+
+#include <cuda_runtime.h>
 
 #include "cutnet.h"
 #include "program.h"
@@ -71,15 +74,17 @@ std::string random_circuit(uint64_t r, int q, int t) {
 
 int odd_count(const Graph& g) {
   int k = 0;
-  for (int v = 0; v < g.n; ++v) k += g.alive[(size_t)v] && (g.lam[(size_t)v] & 1);
+  for (int v = 0; v < g.n; ++v) k += g.alive[(size_t)v] && g.non_clifford(v);
   return k;
 }
 
 // Training graph gi: one marginal diagram (chosen at random among those with
 // two or more non-Clifford spiders) of a random circuit with t_min..t_max
 // T/T_DAG gates on 3..10 qubits.
-void make_graph(uint64_t seed, int gi, int t_min, int t_max, uint64_t budget, int max_cand, CutGraph& out) {
-  uint64_t r = mix(seed * 1000003ull + (uint64_t)gi);
+// The marginal diagram of training graph gi (see make_graph), compacted,
+// with uid = vertex index; r receives the generator state after it.
+Graph pick_graph(uint64_t seed, int gi, int t_min, int t_max, uint64_t& r) {
+  r = mix(seed * 1000003ull + (uint64_t)gi);
   Graph g;
   for (int attempt = 0; attempt < 8; ++attempt) {
     r = mix(r);
@@ -97,41 +102,142 @@ void make_graph(uint64_t seed, int gi, int t_min, int t_max, uint64_t budget, in
   }
   g.compact();
   for (int v = 0; v < g.n; ++v) g.uid[(size_t)v] = v;
+  return g;
+}
+
+// terms when unit u is split first and the rest follow the heuristic order
+// (2 budget when they exceed the budget)
+double unit_first_terms(const Graph& g, const std::vector<std::vector<int>>& units, int u, uint64_t budget) {
+  std::vector<int> order{u};
+  for (size_t k = 0; k < units.size(); ++k)
+    if ((int)k != u) order.push_back((int)k);
+  const std::vector<double> sc = unit_order_scores(g, units, order);
+  std::vector<Term> terms;
+  DecompStats st;
+  st.budget = budget;
+  try {
+    decompose(g, TSIM_DECOMP_LEARNED, terms, st, &sc);
+  } catch (const Error& e) {
+    if (e.code != TSIM_ERR_CHI_BUDGET) throw;
+    return 2.0 * (double)budget;
+  }
+  return (double)std::max<size_t>(1, terms.size());
+}
+
+// terms of one decomposition, 2 budget when it exceeds the budget
+double count_terms(const Graph& g, int policy, uint64_t budget, int first) {
+  std::vector<Term> terms;
+  DecompStats st;
+  st.budget = budget;
+  try {
+    decompose(g, policy, terms, st, nullptr, first);
+  } catch (const Error& e) {
+    if (e.code != TSIM_ERR_CHI_BUDGET) throw;
+    return 2.0 * (double)budget;
+  }
+  return (double)std::max<size_t>(1, terms.size());
+}
+
+void make_graph(uint64_t seed, int gi, int t_min, int t_max, uint64_t budget, int max_cand, CutGraph& out) {
+  uint64_t r = 0;
+  Graph g = pick_graph(seed, gi, t_min, t_max, r);
   std::vector<int> uids;
   cut_features(g, out.X, out.rowptr, out.col, uids);
   out.y.assign(uids.size(), NAN);
-  std::vector<int> odd;
-  for (int v = 0; v < g.n; ++v)
-    if (g.alive[(size_t)v] && (g.lam[(size_t)v] & 1)) odd.push_back(v);
-  if (odd.size() < 2) return;
-  // candidates: a seeded shuffle of the odd spiders, at most max_cand
-  for (size_t i = odd.size(); i > 1; --i) {
+  // candidates: a seeded shuffle of the cut units (cancelling pairs and
+  // single spiders), at most max_cand; each is labelled, on every member,
+  // with the terms when it is split first and the rest follow the heuristic
+  const std::vector<std::vector<int>> units = cut_units(g);
+  size_t n_odd = 0;
+  for (const auto& u : units) n_odd += u.size();
+  if (n_odd < 2) return;
+  std::vector<int> order(units.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  for (size_t i = order.size(); i > 1; --i) {
     r = mix(r);
-    std::swap(odd[i - 1], odd[(size_t)(r % i)]);
+    std::swap(order[i - 1], order[(size_t)(r % i)]);
   }
-  if ((int)odd.size() > max_cand) odd.resize((size_t)max_cand);
-  for (int v : odd) {
-    std::vector<Term> terms;
-    DecompStats st;
-    st.budget = budget;
-    double count;
-    try {
-      decompose(g, TSIM_DECOMP_HEURISTIC, terms, st, nullptr, v);
-      count = (double)std::max<size_t>(1, terms.size());
-    } catch (const Error& e) {
-      if (e.code != TSIM_ERR_CHI_BUDGET) throw;
-      count = 2.0 * (double)budget;
-    }
+  if ((int)order.size() > max_cand) order.resize((size_t)max_cand);
+  for (int u : order) {
+    const double count = unit_first_terms(g, units, u, budget);
     // after compact() every vertex is alive, so node index = vertex index
-    out.y[(size_t)v] = (float)std::log2(count);
+    for (int v : units[(size_t)u]) out.y[(size_t)v] = (float)std::log2(count);
   }
 }
 
 }  // namespace
+
+// compile.cpp: one marginal decomposed by the policy of opts (LEARNED: the
+// heuristic against the network's orders)
+void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget, uint64_t* total,
+                        std::vector<Term>& out);
+
 }  // namespace tsim
 
 namespace tsim {
 namespace cutnet {
+
+void evaluate_one(uint64_t seed, int gi, int t_min, int t_max, uint64_t budget, double* row);
+
+void evaluate_policy(uint64_t seed, int n_graphs, int t_min, int t_max, uint64_t budget, double* out) {
+  if (n_graphs < 0 || t_min < 1 || t_max < t_min || !budget || !out) fail(TSIM_ERR_ARG, "bad evaluation parameters");
+  // graphs in parallel host threads; the network's scorer serialises itself
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::atomic<int> next{0}, failed{0};
+  const unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+  std::vector<std::thread> pool;
+  for (unsigned k = 0; k < nt; ++k)
+    pool.emplace_back([&] {
+      cudaSetDevice(dev);
+      for (;;) {
+        const int gi = next++;
+        if (gi >= n_graphs) return;
+        try {
+          evaluate_one(seed, gi, t_min, t_max, budget, out + 5 * (size_t)gi);
+        } catch (...) {
+          failed++;
+        }
+      }
+    });
+  for (auto& th : pool) th.join();
+  if (failed) fail(TSIM_ERR_INTERNAL, "a held-out graph could not be decomposed");
+}
+
+void evaluate_one(uint64_t seed, int gi, int t_min, int t_max, uint64_t budget, double* row) {
+  {
+    uint64_t r = 0;
+    const Graph g = pick_graph(seed, gi, t_min, t_max, r);
+    std::vector<int> odd;
+    for (int v = 0; v < g.n; ++v)
+      if (g.alive[(size_t)v] && g.non_clifford(v)) odd.push_back(v);
+    row[0] = (double)odd.size();
+    row[1] = count_terms(g, TSIM_DECOMP_HEURISTIC, budget, -1);
+    {
+      tsim_compile_opts o{};
+      o.decomp = TSIM_DECOMP_LEARNED;
+      std::vector<Term> terms;
+      try {
+        decompose_marginal(g, o, budget, nullptr, terms);
+        row[2] = (double)std::max<size_t>(1, terms.size());
+      } catch (const Error& e) {
+        if (e.code != TSIM_ERR_CHI_BUDGET) throw;
+        row[2] = 2.0 * (double)budget;
+      }
+    }
+    const std::vector<std::vector<int>> units = cut_units(g);
+    double sum = 0, best = row[1];
+    int n = 0;
+    for (size_t k = 0; k < units.size() && k < 16; ++k) {
+      const double c = unit_first_terms(g, units, (int)k, budget);
+      sum += std::log2(c);
+      best = std::min(best, c);
+      ++n;
+    }
+    row[3] = n ? std::exp2(sum / n) : row[1];  // geometric mean over first units: a random first unit
+    row[4] = best;
+  }
+}
 
 void write_dataset(uint64_t seed, int n_graphs, int t_min, int t_max, uint64_t budget, int max_candidates,
                    const std::string& path) {

@@ -57,6 +57,14 @@ void adam_step(float* params, const float* grad, float* m, float* v, int n, int 
 // registers (params != nullptr) or removes the GPU scorer used by the compiler
 void set_model(const float* params);
 
+// Held-out comparison of cut orders on graphs drawn like the training ones
+// (seed, n_graphs, t_min..t_max): per graph, out[5 g ..] = non-Clifford
+// spiders, terms in the heuristic order, terms with the LEARNED policy (the
+// registered network; the heuristic without one), the geometric mean of the
+// terms over the cut units split first (at most 16 units, the rest
+// heuristic: a random first unit), and the fewest over those and the heuristic.
+void evaluate_policy(uint64_t seed, int n_graphs, int t_min, int t_max, uint64_t budget, double* out);
+
 Batch read_dataset(const std::string& path);
 void write_dataset(uint64_t seed, int n_graphs, int t_min, int t_max, uint64_t budget, int max_candidates,
                    const std::string& path);

@@ -316,10 +316,10 @@ static_assert(kSlChunk % 4 == 0 && kSlChunk >= 4, "rows per chunk must be a mult
 
 // The n rows (a multiple of 4) of one operation code, in chunks whose row
 // loads and parity loads are all issued before the updates; f(way, a, b)
-// spreads consecutive rows over 4 independent accumulators (way = row & 3)
-// so that the update chains overlap.
+// spreads consecutive rows over kSlWays independent accumulators so that
+// the update chains overlap (2 ways: fewer registers, measured as fast as 4).
 #ifndef TSIM_SL_WAYS
-#define TSIM_SL_WAYS 4
+#define TSIM_SL_WAYS 2
 #endif
 constexpr int kSlWays = TSIM_SL_WAYS;
 static_assert(kSlWays == 2 || kSlWays == 4, "2 or 4 accumulator ways");

@@ -676,6 +676,41 @@ void decompose(Graph g, int policy, std::vector<Term>& out, DecompStats& st,
 
 namespace tsim {
 
+std::vector<std::vector<int>> cut_units(const Graph& g) {
+  std::vector<int> odd;
+  for (int v = 0; v < g.n; ++v)
+    if (g.alive[(size_t)v] && g.non_clifford(v)) odd.push_back(v);
+  std::vector<std::vector<int>> units;
+  for (size_t i = 0; i < odd.size();) {
+    const int a = odd[i];
+    if (i + 1 < odd.size()) {
+      const int b = odd[i + 1];
+      if (((g.lam[(size_t)a] + g.lam[(size_t)b]) & 7) == 0 && angle_eighths(g.ang[(size_t)a] + g.ang[(size_t)b]) == 0) {
+        units.push_back({a, b});
+        i += 2;
+        continue;
+      }
+    }
+    units.push_back({a});
+    i += 1;
+  }
+  return units;
+}
+
+std::vector<double> unit_order_scores(const Graph& g, const std::vector<std::vector<int>>& units,
+                                      const std::vector<int>& order) {
+  std::vector<double> sc((size_t)g.n, 1e300);
+  double r = 0;
+  for (int u : order)
+    for (int v : units[(size_t)u]) {
+      const int id = g.uid[(size_t)v] >= 0 ? g.uid[(size_t)v] : v;
+      if ((size_t)id >= sc.size()) sc.resize((size_t)id + 1, 1e300);
+      sc[(size_t)id] = r;
+      r += 1;
+    }
+  return sc;
+}
+
 void cut_features(const Graph& g, std::vector<float>& X, std::vector<int>& rowptr, std::vector<int>& col,
                   std::vector<int>& uids) {
   std::vector<int> idx((size_t)g.n, -1);

@@ -149,6 +149,17 @@ struct DecompStats {
 void decompose(Graph g, int policy, std::vector<Term>& out, DecompStats& st,
                const std::vector<double>* scores = nullptr, int first = -1);
 
+// Units of a cut order: the non-Clifford spiders in ascending id, two
+// consecutive ones whose phases cancel (a T gate's ket and bra copies) forming
+// one pair unit, every other spider a unit of its own.  The heuristic splits
+// the pair units in id order; a cut order that keeps them together only
+// reorders units.
+std::vector<std::vector<int>> cut_units(const Graph& g);
+// Scores for decompose(policy 1) that put the units in the given order
+// (members of one unit in ascending id); spiders in no listed unit go last.
+std::vector<double> unit_order_scores(const Graph& g, const std::vector<std::vector<int>>& units,
+                                      const std::vector<int>& order);
+
 // Node features of the alive spiders for the cut-order network, row-major
 // [nodes][kCutFeatures], with the adjacency in CSR form and each node's uid.
 constexpr int kCutFeatures = 14;

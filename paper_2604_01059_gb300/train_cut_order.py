@@ -10,7 +10,10 @@ library's CUDA kernels (BF16 weights, FP32 accumulation, Adam).  Output:
 ``cut_order.f32`` (the parameter vector, little-endian float32, in the layout
 ``tsim_cut_num_params`` documents) and ``cut_order.json`` (how it was made).
 ``--evaluate PATH`` reports the ranking quality of the weights on a held-out
-dataset.
+dataset; ``--policy N`` compares, on N held-out graphs drawn like the
+training ones (data seed + 1), the term counts of the compiler's LEARNED
+policy with the weights against the heuristic order that judges it, a
+random first cut and the best first cut.
 """
 import argparse
 import json
@@ -63,6 +66,25 @@ def evaluate(params, dataset_path):
             "terms_ratio_top_over_best": float(np.mean(2.0 ** (top - best)))}
 
 
+def policy_report(params, n_graphs, seed, t_min, t_max, budget):
+    """LEARNED against the heuristic on held-out graphs (tsim_cut_evaluate)."""
+    from . import tsim_cut_evaluate, tsim_cut_model_set
+    tsim_cut_model_set(params)
+    try:
+        r = tsim_cut_evaluate(seed, n_graphs, t_min, t_max, budget)
+    finally:
+        tsim_cut_model_set(None)
+    heur, learned, rnd, best = (np.log2(np.maximum(r[:, k], 1.0)) for k in (1, 2, 3, 4))
+    return {"graphs": int(n_graphs), "seed": int(seed), "budget": int(budget),
+            "mean_log2_terms": {"heuristic": float(heur.mean()), "learned": float(learned.mean()),
+                                "random_first_cut": float(rnd.mean()), "best_first_cut": float(best.mean())},
+            "total_terms": {"heuristic": float(r[:, 1].sum()), "learned": float(r[:, 2].sum()),
+                            "best_first_cut": float(r[:, 4].sum())},
+            "learned_fewer": int((r[:, 2] < r[:, 1]).sum()), "learned_equal": int((r[:, 2] == r[:, 1]).sum()),
+            "learned_more": int((r[:, 2] > r[:, 1]).sum()),
+            "best_first_cut_fewer_than_heuristic": int((r[:, 4] < r[:, 1]).sum())}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--dataset", default=None, help="dataset file (generated when missing)")
@@ -78,9 +100,16 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--evaluate", default=None, help="held-out dataset: report the ranking quality of --out")
+    ap.add_argument("--policy", type=int, default=0, help="held-out graphs for the LEARNED-vs-heuristic report")
     a = ap.parse_args(argv)
-    if a.evaluate:
-        print(json.dumps(evaluate(load_weights(a.out), a.evaluate)))
+    if a.evaluate or a.policy:
+        rep = {}
+        if a.evaluate:
+            rep["ranking"] = evaluate(load_weights(a.out), a.evaluate)
+        if a.policy:
+            rep["policy"] = policy_report(load_weights(a.out), a.policy, a.data_seed + 1, a.t_min, a.t_max,
+                                          a.budget)
+        print(json.dumps(rep))
         return
     ds = a.dataset or os.path.join(os.path.dirname(os.path.abspath(a.out)), "cut_order_dataset.bin")
     t0 = time.time()
