@@ -174,11 +174,23 @@ class Workload:
         self.compile_s["learned"] = time.perf_counter() - t0
 
     def _compile(self, decomp):
+        """Compile the workload's circuits in parallel host threads, each with
+        this rank's GPU current (the cut-order network scores on it)."""
+        from concurrent.futures import ThreadPoolExecutor
+
+        import torch
+
         import paper_2604_01059_gb300 as T
-        if self.name == "cfg4":
-            return [T.Program(t, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
-                    for t, _ in self.texts]
-        return [T.Program(t, decomp=decomp, mode=self.mode) for t, _ in self.texts]
+        dev = torch.cuda.current_device() if torch.cuda.is_available() else None
+
+        def one(t):
+            if self.name == "cfg4":
+                return T.Program(t, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
+            return T.Program(t, decomp=decomp, mode=self.mode)
+
+        init = (lambda: torch.cuda.set_device(dev)) if dev is not None else None
+        with ThreadPoolExecutor(max_workers=os.cpu_count() or 1, initializer=init) as ex:
+            return list(ex.map(one, [t for t, _ in self.texts]))
 
     def _learned(self):
         import paper_2604_01059_gb300 as T

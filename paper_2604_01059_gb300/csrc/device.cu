@@ -346,8 +346,6 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
   const int W = padded_words_or_zero(p.W);
   if (!W) throw PackError{TSIM_ERR_ARG, "per-shot vector wider than 2048 bits is not supported"};
   if ((int)p.chain_norm.size() > kMaxChains) throw PackError{TSIM_ERR_ARG, "too many autoregressive chains for the kernel"};
-  if (p.mode == TSIM_MODE_MEASUREMENTS && (int)p.outputs.size() > kMaxOutWords * 64)
-    throw PackError{TSIM_ERR_ARG, "too many measurement outputs for the kernel"};
   Packer s;
   DeviceLayout& L = out.layout;
   L = DeviceLayout();
@@ -928,6 +926,50 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
     L.table_work32.push_back(sliced_work);
     tabs.push_back(dt);
   }
+  // tables whose value does not depend on the shot (only the zero parity):
+  // the value at the table base, and for a chain normalisation the power of
+  // w that makes it real and positive
+  std::vector<DConst> tconst(tabs.size(), DConst{});
+  {
+    std::vector<char> is_norm(tabs.size(), 0);
+    for (int c : p.chain_norm) is_norm[(size_t)c] = 1;
+    const std::vector<uint64_t> zeros((size_t)W, 0);
+    for (size_t t = 0; t < tabs.size(); ++t) {
+      DTable& dt = tabs[t];
+      dt.cst = 0;
+      dt.rot = -1;
+      if (dt.mode != TAB_SCALAR || dt.n_par != 1) continue;
+      ZW v = eval_table_host(p, (int)t, zeros.data());
+      if (v.zero()) v.k = dt.base;
+      if (v.k < dt.base) continue;
+      while (v.k > dt.base) v = zw_lower_k(v);
+      bool fits = true;
+      for (int i = 0; i < 4; ++i) fits = fits && v.c[i] < ((__int128)1 << 62) && v.c[i] > -((__int128)1 << 62);
+      if (!fits) continue;
+      for (int i = 0; i < 4; ++i) tconst[t].c[i] = (long long)v.c[i];
+      dt.cst = 1;
+      if (!is_norm[t]) continue;
+      for (int rot = 0; rot < 8 && dt.rot < 0; ++rot) {
+        ZW r = zw_mul(v, ZW::omega(-rot));
+        if (r.c[2] != 0 || r.c[1] + r.c[3] != 0) continue;
+        // Re = (2 c0 + (c1 - c3) sqrt2) / 2 > 0
+        const __int128 X = 2 * r.c[0], Y = r.c[1] - r.c[3];
+        bool pos;
+        if (X >= 0 && Y >= 0) pos = X > 0 || Y > 0;
+        else if (X <= 0 && Y <= 0) pos = false;
+        else {
+          // compare X^2 with 2 Y^2 exactly (both below 2^126 under the bound)
+          const unsigned __int128 ax = (unsigned __int128)(X < 0 ? -X : X), ay = (unsigned __int128)(Y < 0 ? -Y : Y);
+          if ((ax >> 62) || (ay >> 62)) continue;  // left to the device
+          const unsigned __int128 x2 = ax * ax, y2 = 2 * ay * ay;
+          pos = X > 0 ? x2 > y2 : y2 > x2;
+        }
+        if (pos) dt.rot = rot;
+      }
+    }
+  }
+  L.o_tc = s.section();
+  if (!tconst.empty()) s.put(tconst.data(), tconst.size() * sizeof(DConst));
   L.o_tab = s.section();
   if (!tabs.empty()) s.put(tabs.data(), tabs.size() * sizeof(DTable));
   L.o_par = s.section();
@@ -966,6 +1008,39 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
   };
   csr(p.detmap, &L.o_dmo, &L.o_dmi);
   csr(p.obsmap, &L.o_omo, &L.o_omi);
+  // measurement mode: every detector / observable (Eq. xor) as one parity of
+  // X: the XOR of its measurements' vectors (a deterministic output's mask, a
+  // random output's own X bit) and of their constants; X keeps every drawn
+  // bit until the shot ends, so the parity at the end equals the XOR
+  auto xor_masks = [&](const std::vector<std::vector<int>>& m, size_t* o_mask, size_t* o_cst) {
+    std::vector<uint64_t> masks;
+    std::vector<int32_t> csts;
+    for (const auto& d : m) {
+      std::vector<uint64_t> mk((size_t)W, 0);
+      int c = 0;
+      for (int j : d) {
+        const ProgOutput& o = p.outputs[(size_t)j];
+        if (o.random) {
+          mk[(size_t)o.xbit >> 6] ^= 1ull << (o.xbit & 63);
+        } else {
+          for (size_t w = 0; w < o.mask.size() && w < (size_t)W; ++w) mk[w] ^= o.mask[w];
+          c ^= o.cst;
+        }
+      }
+      masks.insert(masks.end(), mk.begin(), mk.end());
+      csts.push_back(c);
+    }
+    *o_mask = s.section();
+    if (!masks.empty()) s.put(masks.data(), masks.size() * 8);
+    *o_cst = s.section();
+    if (!csts.empty()) s.put(csts.data(), csts.size() * 4);
+    int32_t z = 0;
+    s.put(&z, 4);
+  };
+  if (p.mode == TSIM_MODE_MEASUREMENTS) {
+    xor_masks(p.detmap, &L.o_dmk, &L.o_dcs);
+    xor_masks(p.obsmap, &L.o_omk, &L.o_ocs);
+  }
   L.total = s.section();
   out.blob.swap(s.b);
 }
@@ -1011,6 +1086,11 @@ DevView make_view(const unsigned char* base, const DeviceLayout& L, const Progra
   v.omap_off = (const int32_t*)(base + L.o_omo);
   v.omap_idx = (const int32_t*)(base + L.o_omi);
   v.chain_float = (const int32_t*)(base + L.o_cf);
+  v.tconst = (const DConst*)(base + L.o_tc);
+  v.dmask = (const uint64_t*)(base + L.o_dmk);
+  v.omask2 = (const uint64_t*)(base + L.o_omk);
+  v.dcst = (const int32_t*)(base + L.o_dcs);
+  v.ocst = (const int32_t*)(base + L.o_ocs);
   v.ffidx = (const uint32_t*)(base + L.o_ffi);
   v.ffang = (const double*)(base + L.o_ffa);
   return v;

@@ -11,7 +11,6 @@ namespace tsim {
 enum : int { ST_NOT_REAL = 1, ST_OVERFLOW = 2, ST_ZERO_PROB = 4, ST_TIMEOUT = 8 };
 
 constexpr int kMaxChains = 16;
-constexpr int kMaxOutWords = 64;  // measurement mode: 4096 outputs
 constexpr int kMaxParities = 256;
 constexpr int kThreads = 128;
 
@@ -29,7 +28,12 @@ struct DOut { int32_t kind, cst, a, chain, table, rec; };
 // as SCALAR, with each class's coefficient a complex double and its
 // arbitrary-angle factors e^(i pi t a) summed into one phase.
 enum : int { TAB_SCALAR = 0, TAB_BASIS = 1, TAB_SLICED = 2, TAB_FLOAT = 3 };
-struct DTable { uint32_t par_off, n_par, cls_off, n_cls; int32_t base, mode, sb_off, n_sb, stage, pad[3]; };
+// A marginal table.  cst = 1: its value does not depend on the shot (no
+// factor has a nonzero parity) and is precomputed in DevView::tconst, with
+// the chain rotation of a normalisation in rot (-1 when not precomputed).
+struct DTable { uint32_t par_off, n_par, cls_off, n_cls; int32_t base, mode, sb_off, n_sb, stage, cst, rot, pad; };
+// the precomputed value (c0 + c1 w + c2 w^2 + c3 w^3) sqrt2^base of a constant table
+struct DConst { long long c[4]; };
 // A class of merged terms.  SCALAR / BASIS: coefficient w^j0 (mono) or c[4]
 // in Z[w], magnitude sqrt2^d0 over the table base.  FLOAT: fac_off / n_fac
 // its exact factors, j0 / pad the offset and count of its arbitrary-angle
@@ -101,6 +105,11 @@ struct DevView {
   const int32_t* dmap_idx;
   const int32_t* omap_off;
   const int32_t* omap_idx;
+  const DConst* tconst;        // per table: its value when constant
+  const uint64_t* dmask;       // measurement mode: per detector a mask over X (W words) ...
+  const uint64_t* omask2;      // ... and per observable; the constants in dcst / ocst
+  const int32_t* dcst;
+  const int32_t* ocst;
   const int32_t* chain_float;  // per chain: 1 when its tables are FLOAT
   const uint32_t* ffidx;       // FLOAT tables: parity index of each arbitrary-angle factor
   const double* ffang;         // FLOAT tables: its angle, in units of pi

@@ -555,6 +555,10 @@ __device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64
 template <int W, bool SL>
 __device__ ZC eval_table(const DevView& V, int t, const uint64_t (&X)[W], const SlSmem& sm) {
   const DTable tb = V.tab[t];
+  if (tb.cst) {  // precomputed: the value does not depend on the shot
+    const DConst k = V.tconst[t];
+    return ZC{{k.c[0], k.c[1], k.c[2], k.c[3]}, tb.base};
+  }
   if constexpr (SL) {
     if (tb.mode == TAB_SLICED) return eval_table_sliced<W>(V, tb, X, sm);
   }
@@ -742,13 +746,29 @@ __device__ __forceinline__ void sample_noise(const DevView& V, uint32_t c0, uint
     }
     return;
   }
+  // The first eight words of stream 2 come from two Philox calls that every
+  // lane makes up front, together (a shot draws one word per group plus two
+  // per candidate, rarely more than eight); they are consumed in order from
+  // a register queue, and only a lane that needs more generates further
+  // blocks on its own.
   uint32_t j = 0;  // next word of stream 2
+  uint32_t q0[4], q1[4];
+  philox4x32_10(c0, c1, 2u, 0u, rk, q0);
+  philox4x32_10(c0, c1, 2u, 1u, rk, q1);
   uint32_t blk[4] = {0, 0, 0, 0};
   auto word = [&]() {
-    if ((j & 3) == 0) philox4x32_10(c0, c1, 2u, j >> 2, rk, blk);
-    const uint32_t q = j & 3;
+    uint32_t v;
+    if (j < 8) {
+      v = q0[0];
+      q0[0] = q0[1]; q0[1] = q0[2]; q0[2] = q0[3]; q0[3] = q1[0];
+      q1[0] = q1[1]; q1[1] = q1[2]; q1[2] = q1[3];
+    } else {
+      if ((j & 3) == 0) philox4x32_10(c0, c1, 2u, j >> 2, rk, blk);
+      const uint32_t q = j & 3;
+      v = q == 0 ? blk[0] : q == 1 ? blk[1] : q == 2 ? blk[2] : blk[3];
+    }
     ++j;
-    return q == 0 ? blk[0] : q == 1 ? blk[1] : q == 2 ? blk[2] : blk[3];
+    return v;
   };
   for (int g = 0; g < V.n_grp; ++g) {
     const DGroup G = V.grp[g];
@@ -849,11 +869,13 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk
     }
     const ZC z = eval_table<W, SL>(V, V.chain_norm[c], X, sm);
     if (DBG && dump) dump_eval<W>(dump + (size_t)drow * nd++, V.chain_norm[c], z, X, V.W);
-    rot[c] = chain_rotation(z, &st);
+    const int pre = V.tab[V.chain_norm[c]].rot;  // precomputed for a constant normalisation
+    rot[c] = pre >= 0 ? pre : chain_rotation(z, &st);
     pp[c] = to_real_rot(z, rot[c], &st);
   }
-  const int dw = (V.ndet + 63) >> 6, mw = (V.nmeas + 63) >> 6, ow = (V.nobs + 63) >> 6;
-  uint64_t ob[kMaxOutWords];  // measurement mode only
+  const int dw = (V.ndet + 63) >> 6, ow = (V.nobs + 63) >> 6;
+  const int mw = (V.nmeas + 63) >> 6;
+  uint64_t mcur = 0;  // measurement mode: the record word being filled
   uint64_t cur = 0;  // detector mode: record word cw (detector words, then observable words)
   int cw = -1;
   bool any_det = false;
@@ -952,26 +974,25 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk
     if (V.mode == 0) {
       put(i, (uint64_t)bit);  // detectors are outputs [0, ndet), observables [ndet, ndet + nobs)
     } else {
-      if ((i & 63) == 0) ob[i >> 6] = 0;
-      ob[i >> 6] |= (uint64_t)bit << (i & 63);
+      // measurement records in output order, one word at a time
+      mcur |= (uint64_t)bit << (i & 63);
+      if ((i & 63) == 63 || i == V.n_out - 1) {
+        if (meas && valid) meas[s * mw + (i >> 6)] = mcur;
+        mcur = 0;
+      }
     }
   }
   if (V.mode == 0) flush();
 
-  // 4. measurement-mode records
+  // 4. measurement mode: every detector and observable (Eq. xor) is one
+  // parity of the final X (its measurements' masks and drawn bits, XORed
+  // ahead of time) plus a constant
   if (V.mode != 0) {
-    if (meas && valid)
-      for (int w = 0; w < mw; ++w) meas[s * mw + w] = ob[w];
     for (int w = 0; w < dw; ++w) {
       uint64_t v = 0;
       for (int b = 0; b < 64 && 64 * w + b < V.ndet; ++b) {
         const int d = 64 * w + b;
-        int x = 0;
-        for (int q = V.dmap_off[d]; q < V.dmap_off[d + 1]; ++q) {
-          const int j = V.dmap_idx[q];
-          x ^= (int)((ob[j >> 6] >> (j & 63)) & 1);
-        }
-        v |= (uint64_t)x << b;
+        v |= (uint64_t)(parity_w<W>(V.dmask + (size_t)d * V.W, X, V.W) ^ V.dcst[d]) << b;
       }
       any_det |= v != 0;
       if (det && valid) det[s * dw + w] = v;
@@ -981,12 +1002,7 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk
         uint64_t v = 0;
         for (int b = 0; b < 64 && 64 * w + b < V.nobs; ++b) {
           const int d = 64 * w + b;
-          int x = 0;
-          for (int q = V.omap_off[d]; q < V.omap_off[d + 1]; ++q) {
-            const int j = V.omap_idx[q];
-            x ^= (int)((ob[j >> 6] >> (j & 63)) & 1);
-          }
-          v |= (uint64_t)x << b;
+          v |= (uint64_t)(parity_w<W>(V.omask2 + (size_t)d * V.W, X, V.W) ^ V.ocst[d]) << b;
         }
         obs[s * ow + w] = v;
       }
