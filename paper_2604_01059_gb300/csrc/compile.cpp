@@ -351,11 +351,11 @@ std::atomic<CutScorer> g_cut_scorer{nullptr};
 std::atomic<uint64_t> g_cut_stats[4];
 
 // Decompose one marginal diagram.  LEARNED: the spiders of the simplified
-// diagram are scored by the cut-order network (trained on the term count of
-// each spider as the first cut), and the best-ranked first cuts are tried
-// against the heuristic order, which judges (a learned first cut is kept only
-// with strictly fewer terms; every order gives the same exact sum).  Without
-// a scorer LEARNED falls back to the heuristic.
+// diagram are scored by the cut-order network, cut units are ranked by their
+// best member, and learned unit orders are tried against the heuristic order,
+// which judges (a learned order is kept only with strictly fewer terms; every
+// order gives the same exact sum).  Without a scorer LEARNED falls back to
+// the heuristic.
 // When set, compile_program records each marginal's diagram after the
 // Clifford rewrites and stops before decomposing anything.
 thread_local std::vector<Graph>* g_marginal_capture = nullptr;

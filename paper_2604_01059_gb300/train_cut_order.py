@@ -113,9 +113,10 @@ def main(argv=None):
         return
     ds = a.dataset or os.path.join(os.path.dirname(os.path.abspath(a.out)), "cut_order_dataset.bin")
     t0 = time.time()
-    if not os.path.exists(ds):
+    reused = os.path.exists(ds)
+    if not reused:
         tsim_cut_dataset(a.data_seed, a.graphs, a.t_min, a.t_max, a.budget, a.candidates, ds)
-    t_data = time.time() - t0
+    t_data = None if reused else round(time.time() - t0, 1)
     x, rp, col, y, go = read_cut_dataset(ds)
     lab = ~np.isnan(y)
     p0 = tsim_cut_init_params(a.seed)
@@ -128,7 +129,7 @@ def main(argv=None):
     rec = {
         "dataset": {"graphs": int(len(go) - 1), "nodes": int(len(rp) - 1), "labelled": int(lab.sum()),
                     "t_min": a.t_min, "t_max": a.t_max, "budget": a.budget, "candidates": a.candidates,
-                    "seed": a.data_seed, "seconds": round(t_data, 1)},
+                    "seed": a.data_seed, "seconds": t_data, "reused_file": reused},
         "training": {"epochs": a.epochs, "batch_graphs": a.batch, "lr": a.lr, "seed": a.seed,
                      "seconds": round(t_train, 2), "loss_init": L0, "loss_final": L1,
                      "loss_per_epoch": [round(float(v), 5) for v in hist]},
