@@ -18,11 +18,13 @@ Two forms are timed on the same GPU and must write identical records:
 The same line reports, each with its own timing, roofline and CPU baseline,
 the d=5 surface code with two injected logical rotations (3 x 10^6 shots),
 the same circuit sampled in measurement mode (every record, long
-autoregressive chains) and the d=3 colour-code T-check (10^7 shots, the
-term-evaluation workload).
+autoregressive chains), the d=3 colour-code T-check (10^7 shots, the
+term-evaluation workload) and the learned-cut-order workload (32 held-out
+circuits of the network's training family, 34-46 T/T_DAG, where the learned
+order and the heuristic give different programs).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
-                    [--only cfg2|cfg2m|cfg3|cfg4] [--profile]
+                    [--only cfg2|cfg2m|cfg3|cfg4|cfg5] [--profile]
 
 Under torchrun (N > 1) every rank samples its own shot range of every
 program (weak scaling, no collective on the data path); timings take the
@@ -56,10 +58,18 @@ WORKLOADS = {
     "cfg4": "batched launch: 256 seeded random noisy Clifford+T mirror circuits (20-60 qubits, depth 20-100, "
             "8-40 T/T_DAG, 2-qubit density 0.3, p in U[1e-4,3e-3]), shots log-uniform in [1e3,1e6], "
             "persistent launches replayed from a CUDA graph, autotuned shot block and residency",
+    "cfg5": "learned cut order against the heuristic: 32 seeded random Clifford+T circuits of the network's "
+            "training family held out from training (3-10 qubits, 34-46 T/T_DAG, CX density 0.4, DEPOLARIZE1 "
+            "1e-3 per layer), the first that compile within 8192 terms per marginal and 32768 per program, "
+            "measurement sampling, 1e5 shots each",
 }
 CFG2_P = (5e-4, 1e-3, 2e-3)
 CFG4_TABLE_BUDGET = 2048     # terms per marginal table
 CFG4_PROGRAM_BUDGET = 8192   # terms per program
+CFG5_PROGRAMS = 32
+CFG5_T_RANGE = (34, 46)
+CFG5_TABLE_BUDGET = 8192     # terms per marginal table
+CFG5_PROGRAM_BUDGET = 32768  # terms per program
 H2D_NOTE = ("0: a sampling step has no per-step input beyond scalars (seed, shot offset); each program's "
             "tables are uploaded once, before the timed region")
 
@@ -111,21 +121,38 @@ def config4_programs(n=256, decomp=0, texts=None):
     """The batched workload, compiled in parallel host threads.  Circuits over
     the term budgets are skipped and the next seeds drawn (deterministic
     order); `texts` recompiles a chosen list.  Returns (program, shots, text)."""
+    from paper_2604_01059_gb300 import workloads as Wk
+    pool = Wk.config4_batch(n=4 * n, seed=0) if texts is None else texts
+    return select_programs(pool, n, CFG4_TABLE_BUDGET, CFG4_PROGRAM_BUDGET, 0, decomp)
+
+
+def config5_programs(n=CFG5_PROGRAMS):
+    """The learned-cut-order workload: the first n circuits of the seeded pool
+    (training-family circuits, 34-46 T/T_DAG) that compile within the term
+    budgets in the heuristic order, measurement mode."""
+    import paper_2604_01059_gb300 as T
+    from paper_2604_01059_gb300 import workloads as Wk
+    pool = Wk.config5_pool(8 * n, t_range=CFG5_T_RANGE)
+    return select_programs(pool, n, CFG5_TABLE_BUDGET, CFG5_PROGRAM_BUDGET, T.MODE_MEASUREMENTS, 0)
+
+
+def select_programs(pool, n, chi_budget, total_budget, mode, decomp):
+    """The first n (circuit, shots) items of the pool whose programs fit the
+    term budgets, compiled in parallel host threads.  Returns (program, shots,
+    text) triples in pool order."""
     from concurrent.futures import ThreadPoolExecutor
 
     import paper_2604_01059_gb300 as T
-    from paper_2604_01059_gb300 import workloads as Wk
-    pool = Wk.config4_batch(n=4 * n, seed=0) if texts is None else texts
 
     def build(item):
         txt, shots = item
         try:
-            p = T.Program(txt, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
+            p = T.Program(txt, chi_budget=chi_budget, total_budget=total_budget, decomp=decomp, mode=mode)
         except T.TsimError as e:
             if e.code == 3:
                 return None
             raise
-        return (p, shots, txt) if p.info["total_terms"] <= CFG4_PROGRAM_BUDGET else None
+        return (p, shots, txt) if p.info["total_terms"] <= total_budget else None
 
     # a sliding window of compilations in pool order: results are taken in
     # order (the first n that fit the budgets), while a slow circuit does not
@@ -155,8 +182,8 @@ class Workload:
         from paper_2604_01059_gb300 import workloads as Wk
         self.name = name
         t0 = time.perf_counter()
-        if name == "cfg4":
-            pr = config4_programs()
+        if name in ("cfg4", "cfg5"):
+            pr = config4_programs() if name == "cfg4" else config5_programs()
             self.plain = [p for p, _, _ in pr]
             self.shots = [s for _, s, _ in pr]
             self.texts = [(t, s) for _, s, t in pr]
@@ -164,8 +191,8 @@ class Workload:
             self.texts = [(Wk.config3_circuit(p=1e-3), 10_000_000)]
         else:
             self.texts = [(Wk.config2_circuit(p=p), 1_000_000) for p in CFG2_P]
-        self.mode = T.MODE_MEASUREMENTS if name == "cfg2m" else T.MODE_DETECTORS
-        if name != "cfg4":
+        self.mode = T.MODE_MEASUREMENTS if name in ("cfg2m", "cfg5") else T.MODE_DETECTORS
+        if name not in ("cfg4", "cfg5"):
             self.plain = [T.Program(t, mode=self.mode) for t, _ in self.texts]
             self.shots = [s for _, s in self.texts]
         self.compile_s = {"heuristic": time.perf_counter() - t0}
@@ -186,6 +213,9 @@ class Workload:
         def one(t):
             if self.name == "cfg4":
                 return T.Program(t, chi_budget=CFG4_TABLE_BUDGET, total_budget=CFG4_PROGRAM_BUDGET, decomp=decomp)
+            if self.name == "cfg5":
+                return T.Program(t, chi_budget=CFG5_TABLE_BUDGET, total_budget=CFG5_PROGRAM_BUDGET, decomp=decomp,
+                                 mode=self.mode)
             return T.Program(t, decomp=decomp, mode=self.mode)
 
         init = (lambda: torch.cuda.set_device(dev)) if dev is not None else None
@@ -222,7 +252,7 @@ def premerge_terms_per_shot(prog):
     return sum(prog.table_terms())
 
 
-def kernel_int_ops(prog):
+def kernel_int_ops(prog, padded=False):
     """Integer operations one shot needs in the fused sampling kernel, counted
     on the packed device tables it evaluates:
       noise, one word per channel: ceil(C/4) Philox4x32-10 calls x 10 rounds x
@@ -237,7 +267,9 @@ def kernel_int_ops(prog):
       tables:  per distinct parity 2W+2 (AND, XOR, popcount, insert), per merged
                term 12 (+5 per factor: two bit extracts, index, lookup, add);
                bit-sliced tables: the lane-operations of one warp for its 32
-               shots, as the library counts them, divided by 32."""
+               shots, as the library counts them, divided by 32: without
+               padding (each term's own rows, one batch epilogue per term),
+               or with it (padded=True: every row and lane the kernel runs)."""
     i = prog.info
     C = i["num_channels"]
     W = next(p for p in (1, 2, 4, 8, 16, 32) if i["x_words"] <= p)
@@ -254,7 +286,7 @@ def kernel_int_ops(prog):
     for t in range(i["num_tables"]):
         layout = prog.device_table_layout(t)
         if layout[0] == 2:
-            ops += layout[4] / 32
+            ops += (layout[4] if padded else layout[5]) / 32
             continue
         classes, factors, parities = prog.device_table_stats(t)
         ops += parities * (2 * W + 2) + 12 * classes + 5 * factors
@@ -508,6 +540,7 @@ def bench_config(wl, steps, args, dist, rank, world, flush, clocks_index):
 
     # roofline of the dominant kernel (the batched launch's kernels)
     ops = sum(kernel_int_ops(p) * ns for p, ns in zip(progs, shots))
+    ops_padded = sum(kernel_int_ops(p, padded=True) * ns for p, ns in zip(progs, shots))
     peak, sms, clk_mhz = int_peak()
     achieved = ops / (batch_ms / steps / 1e3)
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
@@ -515,6 +548,10 @@ def bench_config(wl, steps, args, dist, rank, world, flush, clocks_index):
             "kernel": ("k_batch (persistent kernels over all programs, graph replay)" if binfo.get("form", 0) == 0
                        else "k_sample (each program's launch, graph replay)"),
             "ops_per_shot": ops / sum(shots),
+            "ops_note": "algorithmic integer operations without padding (bit-sliced rows of each term's own "
+                        "factors, one batch epilogue per term)",
+            "ops_per_shot_padded": ops_padded / sum(shots),
+            "frac_padded": ops_padded / (batch_ms / steps / 1e3) / peak,
             "peak_source": f"derived: {sms} SMs (from the device) x 4 sub-partitions x 16 INT32 lanes x "
                            f"{clk_mhz:.0f} MHz (maximum SM clock)"}
     base = None
@@ -567,7 +604,7 @@ def run_gpu(args):
     ids = [v.strip() for v in vis.split(",") if v.strip()]
     clocks_index = ids[local] if local < len(ids) else str(local)
     head = args.only or HEADLINE
-    names = [head] + ([] if args.only else [k for k in ("cfg2", "cfg2m", "cfg3") if k != head])
+    names = [head] + ([] if args.only else [k for k in ("cfg2", "cfg2m", "cfg3", "cfg5") if k != head])
     res = {}
     for name in names:
         wl = Workload(name)

@@ -358,12 +358,13 @@ tsim_status tsim_program_device_table_stats(const tsim_program* prog, int t, uin
  *
  * tsim_program_device_table_layout: out[0] = layout of table t, out[1] =
  * batches of 32 terms (over all segments), out[2] = padded operation rows,
- * out[3] = operations before padding, out[4] = integer lane-operations one
- * warp executes on the table for its 32 shots (out[1..4] are 0 unless
- * SLICED). */
+ * out[3] = operations before padding (lane-rows of real factors), out[4] =
+ * integer lane-operations one warp executes on the table for its 32 shots,
+ * out[5] = the same count without padding (each term's own rows, one batch
+ * epilogue per term) (out[1..5] are 0 unless SLICED). */
 tsim_status tsim_program_set_table_layout(tsim_program* prog, int64_t sliced_min_terms, int32_t stage_rows,
                                           int32_t segment_parities);
-tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[5]);
+tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[6]);
 
 /* Output entries of the packed program: out[0] = entries the kernel walks
  * per shot, out[1] = runs (in detector mode, consecutive single-bit

@@ -371,8 +371,9 @@ def tsim_program_set_table_layout(h, sliced_min_terms, stage_rows=-1, segment_pa
 
 def tsim_program_device_table_layout(h, t):
     """(layout, batches of 32 terms, padded operation rows, operations,
-    integer lane-operations per 32 shots) of table t."""
-    out = (ctypes.c_uint64 * 5)()
+    integer lane-operations per 32 shots, the same without padding) of
+    table t."""
+    out = (ctypes.c_uint64 * 6)()
     _check(load_library().tsim_program_device_table_layout(h, t, out))
     return tuple(out)
 

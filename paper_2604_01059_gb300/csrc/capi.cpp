@@ -146,7 +146,7 @@ tsim_status tsim_program_set_table_layout(tsim_program* prog, int64_t sliced_min
   });
 }
 
-tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[5]) {
+tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, uint64_t out[6]) {
   return guard([&] {
     const tsim::Program& p = prog_of(prog);
     if (!out || t < 0 || t >= (int)p.tables.size()) tsim::fail(TSIM_ERR_ARG, "bad table index");
@@ -157,6 +157,7 @@ tsim_status tsim_program_device_table_layout(const tsim_program* prog, int t, ui
     out[2] = L.table_rows[(size_t)t];
     out[3] = L.table_ops[(size_t)t];
     out[4] = L.table_work32[(size_t)t];
+    out[5] = L.table_work32_real[(size_t)t];
   });
 }
 

@@ -373,7 +373,9 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
   {
     uint32_t moff = 0;
     for (const NoiseGroup& g : p.groups) {
-      DGroup d{g.Q, (uint32_t)g.member.size(), moff, moff};
+      uint64_t tn = 1ull << 32;
+      for (size_t k = 0; k < g.member.size(); ++k) tn = (tn * (uint64_t)g.Q) >> 32;
+      DGroup d{g.Q, (uint32_t)g.member.size(), moff, (uint32_t)tn};
       moff += (uint32_t)g.member.size();
       s.put(&d, sizeof d);
     }
@@ -579,6 +581,7 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
       L.table_rows.push_back(0);
       L.table_ops.push_back(0);
       L.table_work32.push_back(0);
+      L.table_work32_real.push_back(0);
       tabs.push_back(dt);
       continue;
     }
@@ -659,18 +662,23 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
       if (!sliced_term(cl[pr.i].f, pr.j, pr.raw - base, lut, t)) { sliced = false; break; }
       if (!t.dead) sterms.push_back(std::move(t));
     }
-    uint64_t real_ops = 0, padded_rows = 0, sliced_work = 0, nbatches = 0;
+    uint64_t real_ops = 0, padded_rows = 0, sliced_work = 0, nbatches = 0, real_work = 0;
     if (sliced) {
       dt.mode = TAB_SLICED;
       dt.sb_off = (int32_t)segs.size();  // sliced: the table's segments
       // integer lane-operations of one warp (32 shots) on this table: the
-      // bit transpose of X (2W transposes of 5 stages of 4 ops, 32 lanes), per
-      // segment each parity (load, store, and per mask bit: find, load, XOR),
-      // each padded row on 32 lanes (index load, parity load and the word
-      // operations of its code), and per batch 4 transposes, the signed
-      // counts and their accumulation (about 110 per lane)
-      static const int kRowOps[kSlCodes] = {3, 4, 5, 6, 3, 3, 6};
-      uint64_t w32 = 2ull * (uint64_t)W * 5 * 4 * 32;
+      // bit transpose of X (W paired transposes of 5 stages of 6 ops, and 2W
+      // stores, 32 lanes), per segment each parity (load, store, and per mask
+      // bit: find, load, XOR), each padded row on 32 lanes (its share of the
+      // 16-byte row load and of the code dispatch, its parity load(s) and the
+      // word operations of its code), and per batch 2 paired transposes, the
+      // signed counts and their accumulation (about 90 per lane).
+      // real_work counts the same operations without padding: the rows of
+      // each term's own factors and one batch epilogue per term (lane).
+      static const int kRowOps[kSlCodes] = {3, 4, 5, 4, 3, 3, 6};
+      constexpr uint64_t kBatchOps = 90;
+      uint64_t w32 = 32ull * 32 * (uint64_t)W;
+      uint64_t wreal = w32;
       uint32_t most = 0;
       auto parities_of = [](const SlTerm& t, std::vector<uint32_t>& out) {
         out.clear();
@@ -797,6 +805,7 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
           uint64_t pop = 0;
           for (uint64_t m : plist[q - 1]) pop += (uint64_t)__builtin_popcountll(m);
           w32 += 3 + 3 * pop;
+          wreal += 3 + 3 * pop;
         }
         w32 += 3 * (uint64_t)(nslot - ps.size());
         // rows hold byte offsets of the slots' words: 4 slot, or
@@ -825,7 +834,10 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
                   if (c == SL_XOR4AB) r = (4 * slot.at((uint32_t)v)) | ((4 * slot.at((uint32_t)(v >> 32))) << 16);
                   else r = 4 * slot.at((uint32_t)v);
                   const size_t ti = P.b0 + l;
-                  if (ti < P.b1 && k < lt[ti].ops[c].size()) ++real_ops;
+                  if (ti < P.b1 && k < lt[ti].ops[c].size()) {
+                    ++real_ops;
+                    wreal += (uint64_t)kRowOps[c];
+                  }
                   rows.push_back(r);
                 }
             ri += n;
@@ -833,7 +845,8 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
             nrows += (uint32_t)n;
             w32 += (uint64_t)n * 32 * (uint64_t)kRowOps[c];
           }
-          w32 += 32 * 110;
+          w32 += 32 * kBatchOps;
+          wreal += kBatchOps * (uint64_t)(P.b1 - P.b0);
           most = std::max(most, nrows);
           if (rows.size() > 0xFFFFFFFFull) throw PackError{TSIM_ERR_ARG, "sliced tables too large"};
           sbs.push_back(B);
@@ -850,6 +863,7 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
       dt.stage = stage_rows > 0 && most <= (uint32_t)stage_rows ? 1 : 0;
       if (dt.stage) L.sl_rows_max = std::max(L.sl_rows_max, most);
       sliced_work = w32;
+      real_work = wreal;
     } else {
       // few distinct parities: evaluate each once per shot and index them;
       // many: evaluate a GF(2) basis of their span and give every parity its
@@ -924,6 +938,7 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
     L.table_rows.push_back(padded_rows);
     L.table_ops.push_back(real_ops);
     L.table_work32.push_back(sliced_work);
+    L.table_work32_real.push_back(real_work);
     tabs.push_back(dt);
   }
   // tables whose value does not depend on the shot (only the zero parity):

@@ -46,7 +46,8 @@ struct DeviceLayout {
   // per table: layout (0 scalar, 1 basis, 2 bit-sliced), and for sliced
   // tables the batches of 32 terms, padded operation rows and real operations
   std::vector<uint64_t> table_mode, table_batches, table_rows, table_ops;
-  std::vector<uint64_t> table_work32;  // sliced: integer lane-operations of one warp (32 shots)
+  std::vector<uint64_t> table_work32;       // sliced: integer lane-operations of one warp (32 shots)
+  std::vector<uint64_t> table_work32_real;  // the same without row and lane padding
 };
 
 // Host-side packed tables of one program, built once when the program is

@@ -70,9 +70,11 @@ struct DSBatch { uint32_t row_off; uint16_t cnt[8]; int32_t d; uint32_t j0m[3]; 
 // parities (par_off, n_par masks) fit one shared buffer, and their batches.
 struct DSeg { uint32_t par_off, n_par, sb_off, n_sb; };
 
-// One group of the geometric-gap noise rule: Q, member count, offsets of
-// its member channel indices and of its table T_1..T_n.
-struct DGroup { uint32_t Q, n, m_off, t_off; };
+// One group of the geometric-gap noise rule: Q, member count n, the offset
+// of its member channel indices and of its table T_1..T_n (the same offset
+// into both arrays), and T_n (a word U < T_n leaves no candidate in the
+// group: the common case, decided without reading the table).
+struct DGroup { uint32_t Q, n, off, tn; };
 
 struct DevView {
   int W;

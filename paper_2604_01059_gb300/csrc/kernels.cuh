@@ -255,16 +255,19 @@ __device__ __forceinline__ void sl_init(const SlSmem& m) {
   }
 }
 
-// 32 x 32 bit-matrix transpose across the warp: on entry lane r holds row r
-// (bit c = column c), on exit lane c holds column c (bit r = row r).  Stage j
-// (16, 8, 4, 2, 1) swaps the off-diagonal j x j blocks between lanes r and
-// r ^ j: each lane sends the half its partner keeps, and rotates what it
-// receives into place (left by j in the lower lane, right by j in the upper
-// one; the received bits never wrap).
-struct Transposer {
+// Two 32 x 32 bit-matrix transposes across the warp at once: on entry lane
+// r holds row r of each matrix (bit c = column c), on exit lane c holds
+// column c (bit r = row r).  Stage j (16, 8, 4, 2, 1) swaps the off-diagonal
+// j x j blocks between lanes r and r ^ j.  Each lane keeps half of its bits
+// (mk) and sends the other half; one shuffle carries both matrices: the
+// half of B that leaves rides, rotated by j, in the positions of A that
+// stay.  The receiver rotates A's half into place; B's half arrives in
+// place.  (Rotations never wrap a kept bit: they move bits within a 2j
+// block.)
+struct Transposer2 {
   uint32_t mk[5];   // the bits a lane keeps at each stage
-  uint32_t rot[5];  // left-rotation of the received bits
-  __device__ __forceinline__ explicit Transposer(int lane) {
+  uint32_t rot[5];  // left-rotation that brings received bits of A into place
+  __device__ __forceinline__ explicit Transposer2(int lane) {
     const uint32_t keep[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
 #pragma unroll
     for (int st = 0; st < 5; ++st) {
@@ -274,36 +277,28 @@ struct Transposer {
       rot[st] = upper ? 32u - (uint32_t)j : (uint32_t)j;
     }
   }
-  __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
+  __device__ __forceinline__ void operator()(uint32_t& a, uint32_t& b) const {
 #pragma unroll
     for (int st = 0; st < 5; ++st) {
-      const uint32_t recv = __shfl_xor_sync(0xFFFFFFFFu, x & ~mk[st], 16 >> st);
-      x = (x & mk[st]) | __funnelshift_l(recv, recv, rot[st]);
+      const uint32_t bs = __funnelshift_r(b, b, rot[st]);
+      const uint32_t send = (a & ~mk[st]) | (bs & mk[st]);
+      const uint32_t r = __shfl_xor_sync(0xFFFFFFFFu, send, 16 >> st);
+      a = (a & mk[st]) | (__funnelshift_l(r, r, rot[st]) & ~mk[st]);
+      b = (b & mk[st]) | (r & ~mk[st]);
     }
-    return x;
   }
 };
 
-// Operation rows read from global memory (through L1) or from a shared
-// staging buffer.  A row holds the byte offset of a parity word (4q), or two
-// of them (4qa | 4qb << 16) for pi-pairs.  Rows come in groups of 4: group g
-// of a code is 32 lanes x 4 consecutive rows, so one 16-byte load per lane
-// fetches 4 rows and a warp's load is 512 contiguous bytes.
-struct RowsG {
+// Operation rows, read through a generic pointer: a shared staging buffer
+// or the rows in global memory (one code path for both).  A row holds the
+// byte offset of a parity word (4q), or two of them (4qa | 4qb << 16) for
+// pi-pairs.  Rows come in groups of 4: group g of a code is 32 lanes x 4
+// consecutive rows, so one 16-byte load per lane fetches 4 rows and a warp's
+// load is 512 contiguous bytes.
+struct Rows {
   const uint4* p;  // this lane's current group
-  __device__ __forceinline__ uint4 get4(int g) const { return __ldg(p + 32 * g); }
+  __device__ __forceinline__ uint4 get4(int g) const { return p[32 * g]; }
   __device__ __forceinline__ void adv4(int k) { p += 32 * k; }
-};
-struct RowsS {
-  uint32_t a;  // shared address of this lane's current group
-  __device__ __forceinline__ uint4 get4(int g) const {
-    uint4 v;
-    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "r"(a + 512u * (uint32_t)g));
-    return v;
-  }
-  __device__ __forceinline__ void adv4(int k) { a += 512u * (uint32_t)k; }
 };
 
 // Rows per chunk of sl_loop (a multiple of 4): every row and parity load of
@@ -324,7 +319,7 @@ static_assert(kSlChunk % 4 == 0 && kSlChunk >= 4, "rows per chunk must be a mult
 constexpr int kSlWays = TSIM_SL_WAYS;
 static_assert(kSlWays == 2 || kSlWays == 4, "2 or 4 accumulator ways");
 
-template <bool PAIR, class Rows, class F>
+template <bool PAIR, class F>
 __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
   int k = 0;
   for (; k + kSlChunk <= n; k += kSlChunk, R.adv4(kSlChunk / 4)) {
@@ -366,7 +361,6 @@ __device__ __forceinline__ void add2bit(uint32_t& x1, uint32_t& x2, uint32_t y1,
 }
 
 // All operation rows of one batch; returns the planes (J0, J1, J2, Z).
-template <class Rows>
 __device__ __forceinline__ void sl_batch(const DSBatch& B, Rows R, uint32_t par, int lane, uint32_t& J0, uint32_t& J1,
                                          uint32_t& J2, uint32_t& Z) {
   J0 = 0u - ((B.j0m[0] >> lane) & 1u);
@@ -422,13 +416,14 @@ __device__ __forceinline__ uint32_t sl_batch_rows(const DSBatch& B) {
 template <int W>
 __device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64_t (&X)[W], const SlSmem& S) {
   const int lane = threadIdx.x & 31;
-  const Transposer transpose32(lane);
+  const Transposer2 transpose2(lane);
   __syncwarp();
   uint32_t state = S.rb > 0 ? lds(S.state) : 4u;
   const bool staged = tb.stage && !(state & 4u);
 #pragma unroll
   for (int w = 0; w < W; ++w) {
-    const uint32_t lo = transpose32((uint32_t)X[w]), hi = transpose32((uint32_t)(X[w] >> 32));
+    uint32_t lo = (uint32_t)X[w], hi = (uint32_t)(X[w] >> 32);
+    transpose2(lo, hi);
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)(64 * w + lane)), "r"(lo) : "memory");
     asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)(64 * w + 32 + lane)), "r"(hi) : "memory");
   }
@@ -521,15 +516,18 @@ __device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64
           state |= 4u;
         } else {
           state ^= 1u << buf;
-          sl_batch(B, RowsS{(buf ? S.rb1 : S.rb0) + 16u * (uint32_t)lane}, S.par, lane, J0, J1, J2, Z);
         }
       }
-      if (!staged || !ok)
-        sl_batch(B, RowsG{reinterpret_cast<const uint4*>(V.rows + B.row_off) + lane}, S.par, lane, J0, J1, J2, Z);
+      // rows from this batch's staging buffer, or from global memory
+      const uint4* rp = (staged && ok)
+                            ? reinterpret_cast<const uint4*>(__cvta_shared_to_generic((bi & 1) ? S.rb1 : S.rb0))
+                            : reinterpret_cast<const uint4*>(V.rows + B.row_off);
+      sl_batch(B, Rows{rp + lane}, S.par, lane, J0, J1, J2, Z);
       if (staged) __syncwarp();  // the buffer just read is refilled next batch
       // lane s now needs, for each of the 32 terms, its phase and flag at shot s
-      const uint32_t T0 = transpose32(J0), T1 = transpose32(J1);
-      const uint32_t T2 = transpose32(J2), TZ = transpose32(Z);
+      uint32_t T0 = J0, T1 = J1, T2 = J2, TZ = Z;
+      transpose2(T0, T1);
+      transpose2(T2, TZ);
       const uint32_t nz = ~TZ;
       const uint32_t M[4] = {~T0 & ~T1 & nz, T0 & ~T1 & nz, ~T0 & T1 & nz, T0 & T1 & nz};
       if (B.d != d_cur) {
@@ -770,14 +768,16 @@ __device__ __forceinline__ void sample_noise(const DevView& V, uint32_t c0, uint
     ++j;
     return v;
   };
+  // the next group's descriptor is loaded while the current one is drawn
+  DGroup G = V.n_grp > 0 ? V.grp[0] : DGroup{};
   for (int g = 0; g < V.n_grp; ++g) {
-    const DGroup G = V.grp[g];
-    const uint32_t* T = V.gT + G.t_off;  // T_k at T[k - 1]
+    const DGroup Gn = g + 1 < V.n_grp ? V.grp[g + 1] : G;
+    const uint32_t* T = V.gT + G.off;  // T_k at T[k - 1]
     uint32_t pos = 0;
     while (pos < G.n) {
       const uint32_t U = word();
       const uint32_t rem = G.n - pos;
-      if (U < __ldg(T + rem - 1)) break;  // gap = rem: no candidate among the rest
+      if (U < (pos == 0 ? G.tn : __ldg(T + rem - 1))) break;  // gap = rem: no candidate among the rest
       uint32_t lo = 0, hi = rem;          // U < T_lo (T_0 = 2^32) and U >= T_hi
       while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
@@ -785,7 +785,7 @@ __device__ __forceinline__ void sample_noise(const DevView& V, uint32_t c0, uint
         else hi = mid;
       }
       pos += lo;
-      const DChan ch = V.ch[__ldg(V.gmem + G.m_off + pos)];
+      const DChan ch = V.ch[__ldg(V.gmem + G.off + pos)];
       const uint32_t Vw = word();
       const uint32_t Vp = G.Q + (uint32_t)(((uint64_t)Vw * ((1ull << 32) - G.Q)) >> 32);
       if (Vp >= ch.thr0) {
@@ -799,6 +799,7 @@ __device__ __forceinline__ void sample_noise(const DevView& V, uint32_t c0, uint
       }
       pos += 1;
     }
+    G = Gn;
   }
 }
 

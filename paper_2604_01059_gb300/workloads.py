@@ -387,3 +387,48 @@ def count_t(text):
         if parts and parts[0] in ("T", "T_DAG"):
             n += len(parts) - 1
     return n
+
+
+# --------------------------------------------------------------------------
+# learned cut order: circuits of the network's training family
+# --------------------------------------------------------------------------
+def layered_clifford_t(seed, q, t_count, p=1e-3, cx_density=0.4):
+    """A seeded random Clifford+T circuit of the family the cut-order network
+    is trained on: layers of CX pairs on random partners (cx_density of the
+    qubits) and single-qubit gates on the others (T or T_DAG with probability
+    1/4, else H, S, S_DAG or SQRT_X) until t_count T/T_DAG gates are placed,
+    DEPOLARIZE1(p) after every layer, Z measurement of every qubit.  No
+    detectors: it is sampled in measurement mode."""
+    rng = random.Random(seed)
+    one_q = ["H", "S", "S_DAG", "SQRT_X"]
+    L = ["R " + " ".join(map(str, range(q)))]
+    placed = 0
+    while placed < t_count:
+        qs = list(range(q))
+        rng.shuffle(qs)
+        pairs = int(cx_density * q / 2 + 0.5)
+        for k in range(pairs):
+            L.append(f"CX {qs[2 * k]} {qs[2 * k + 1]}")
+        for qb in qs[2 * pairs:]:
+            if rng.random() < 0.25 and placed < t_count:
+                L.append(f"{rng.choice(['T', 'T_DAG'])} {qb}")
+                placed += 1
+            else:
+                L.append(f"{rng.choice(one_q)} {qb}")
+        L.append(f"DEPOLARIZE1({p:.6g}) " + " ".join(map(str, range(q))))
+    L.append("M " + " ".join(map(str, range(q))))
+    return "\n".join(L) + "\n"
+
+
+def config5_pool(n, seed=1, q_range=(3, 10), t_range=(40, 60)):
+    """(circuit, shots) pairs for the learned-cut-order comparison: circuits
+    of the training family (layered_clifford_t) with config-3-sized T counts
+    (40-60 T/T_DAG), drawn from generator seeds the training set does not
+    use (seed * 1000003 + k + 7).  1e5 shots each."""
+    rng = random.Random(seed)
+    out = []
+    for k in range(n):
+        q = rng.randint(*q_range)
+        t = rng.randint(*t_range)
+        out.append((layered_clifford_t(seed * 1000003 + k + 7, q, t), 100_000))
+    return out

@@ -72,3 +72,15 @@ def test_config4_generator_is_seeded_and_in_range():
         assert 20 <= c.num_qubits <= 60 and 1_000 <= shots <= 1_000_000
         assert 4 <= Wk.count_t(txt) <= 40
         assert c.num_detectors == c.num_qubits and c.num_observables == 1
+
+
+def test_config5_generator_is_seeded_and_in_range():
+    from oracle import circuit as oc
+    from paper_2604_01059_gb300 import workloads as Wk
+    a = Wk.config5_pool(6, t_range=(34, 46))
+    assert a == Wk.config5_pool(6, t_range=(34, 46))
+    for txt, shots in a:
+        c = oc.parse(txt)
+        assert 3 <= c.num_qubits <= 10 and shots == 100_000
+        assert 34 <= Wk.count_t(txt) <= 46
+        assert c.num_detectors == 0 and c.num_measurements == c.num_qubits

@@ -21,14 +21,17 @@ def test_color_code_default_layout(color_code):
     # marginals of 4 terms or more (no two with equal factor lists here) are
     # sliced; each segment's batches hold 32 terms but its last one, so a
     # table has at least ceil(n / 32) batches
-    for (mode, nb, rows, ops, work), n in zip(_layouts(color_code), color_code.table_terms()):
+    for (mode, nb, rows, ops, work, real), n in zip(_layouts(color_code), color_code.table_terms()):
         assert mode == (T.TABLE_SLICED if n >= 4 else T.TABLE_SCALAR)
         if mode == T.TABLE_SLICED:
             assert (n + 31) // 32 <= nb <= (n + 31) // 32 + n // 32
             assert rows % 4 == 0 or rows >= ops / 32
             assert rows * 32 >= ops and work > rows * 32 * 3
+            # without padding: at least 3 lane-operations per real row,
+            # never more than the padded count
+            assert 3 * ops < real <= work
         else:
-            assert nb == rows == ops == work == 0
+            assert nb == rows == ops == work == real == 0
 
 
 @pytest.mark.parametrize("seg", [256, 1024, 2048, 16384])
@@ -57,7 +60,7 @@ def test_layout_switches(color_code):
 def test_worked_example_forced_sliced():
     prog = T.Program(WORKED_EXAMPLE)
     prog.set_table_layout(1, 128, 16)
-    for mode, nb, rows, ops, work in _layouts(prog):
+    for mode, nb, rows, ops, work, real in _layouts(prog):
         assert mode == T.TABLE_SLICED and nb >= 1
 
 
