@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=6.0, help="bound on each oracle baseline's CPU work")
     ap.add_argument("--only", default=None, choices=sorted(WORKLOADS), help="one workload (it becomes the value)")
     ap.add_argument("--profile", action="store_true", help="only two plain launches per program (for ncu)")
+    ap.add_argument("--profile-scale", type=float, default=1.0,
+                    help="--profile: each program's shots times this factor (at least 32)")
     return ap.parse_args()
 
 
@@ -487,17 +489,33 @@ def bench_config(wl, steps, args, dist, rank, world, flush, clocks_index):
         T.tsim_sync(stream)
         return max_over_ranks(total, dist, "cuda")
 
+    # where the learned order changed programs: the learned programs in the
+    # plain form too, to separate the two effects
+    differs = any(premerge_terms_per_shot(a) != premerge_terms_per_shot(b) for a, b in zip(progs, plain_progs))
+    lp_outs = _outputs(progs, shots) if differs else None
+
+    def learned_plain_step():
+        for k, (p, (d, o, a, m)) in enumerate(zip(progs, lp_outs)):
+            T.tsim_sample(p.h, shots[k], seeds[k], offsets[k], m, d, o, a, stream)
+
+    if differs:
+        for _ in range(max(args.warmup, 3)):
+            learned_plain_step()
     clocks = ClockSampler(clocks_index)
     clocks.start()
     batch_ms = timed(batch_step)
     plain_ms = timed(plain_step)
+    lp_ms = timed(learned_plain_step) if differs else None
     clk = clocks.stop()
     T.tsim_batch_free(batch)
-    identical = all(torch.equal(a[:, :p.info["det_words"]], b[:, :p.info["det_words"]]) and
-                    torch.equal(x[:, :p.info["obs_words"]], y[:, :p.info["obs_words"]]) and torch.equal(u, v) and
-                    (m1 is None or torch.equal(m1, m2))
-                    for p, (a, x, u, m1), (b, y, v, m2) in zip(progs, outs, plain_outs))
-    del outs, plain_outs
+    def same(set1, set2):
+        return all(torch.equal(a[:, :p.info["det_words"]], b[:, :p.info["det_words"]]) and
+                   torch.equal(x[:, :p.info["obs_words"]], y[:, :p.info["obs_words"]]) and torch.equal(u, v) and
+                   (m1 is None or torch.equal(m1, m2))
+                   for p, (a, x, u, m1), (b, y, v, m2) in zip(progs, set1, set2))
+
+    identical = same(outs, plain_outs) and (lp_outs is None or same(lp_outs, plain_outs))
+    del outs, plain_outs, lp_outs
     shots_step = sum(shots) * world
     value = shots_step * steps / (batch_ms / 1e3)
     plain = shots_step * steps / (plain_ms / 1e3)
@@ -575,6 +593,10 @@ def bench_config(wl, steps, args, dist, rank, world, flush, clocks_index):
                   "form": "heuristic cut order, one tsim_sample launch per program",
                   "gpu_launches": steps * sum(1 for s in shots if s > 0)},
         "speedup_vs_plain": value / plain,
+        "learned_plain": None if lp_ms is None else {
+            "value": shots_step * steps / (lp_ms / 1e3), "unit": "shots/s", "ms_per_step": lp_ms / steps,
+            "form": "learned cut order, one tsim_sample launch per program",
+            "speedup_vs_plain": plain_ms / lp_ms},
         "form": "learned cut order + batched launch (CUDA graph, autotuned)", "batch": binfo, "cut": wl.cut,
         "noise_sampling": {"geometric_programs": sum(1 for z in noise if z["mode"] == 1),
                            "words_per_shot": sum((z["words_geometric_mode"] if z["mode"] == 1 else
@@ -678,9 +700,13 @@ def run_profile(args):
 
     import paper_2604_01059_gb300 as T
     name = args.only or "cfg2"
+
+    def scaled(n):
+        return max(32, int(round(n * args.profile_scale)))
+
     if name == "cfg4":
         pr = config4_programs()
-        progs, shots = [p for p, _, _ in pr], [s for _, s, _ in pr]
+        progs, shots = [p for p, _, _ in pr], [scaled(s) for _, s, _ in pr]
         outs = _outputs(progs, shots)
         batch = T.tsim_batch_create([p.h for p in progs], shots, [SEED] * len(progs), None, None,
                                     [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs], autotune=0)
@@ -694,11 +720,11 @@ def run_profile(args):
         wl = Workload(name)
         progs = wl.plain
         for p, ns in zip(wl.plain, wl.shots):
-            p.sample_torch(ns, SEED, 0)
-            p.sample_torch(ns, SEED, 0)
+            p.sample_torch(scaled(ns), SEED, 0)
+            p.sample_torch(scaled(ns), SEED, 0)
         T.tsim_sync()
     torch.cuda.synchronize()
-    print(json.dumps({"profile": WORKLOADS[name], "programs": len(progs)}))
+    print(json.dumps({"profile": WORKLOADS[name], "programs": len(progs), "shots_scale": args.profile_scale}))
 
 
 def main():

@@ -301,56 +301,55 @@ struct Rows {
   __device__ __forceinline__ void adv4(int k) { p += 32 * k; }
 };
 
-// Rows per chunk of sl_loop (a multiple of 4): every row and parity load of
-// a chunk is issued before its updates.
-#ifndef TSIM_SL_CHUNK
-#define TSIM_SL_CHUNK 16
-#endif
-constexpr int kSlChunk = TSIM_SL_CHUNK;
-static_assert(kSlChunk % 4 == 0 && kSlChunk >= 4, "rows per chunk must be a multiple of 4");
+// Rows per chunk of sl_loop: every row and parity load of a chunk is issued
+// before its updates.
+constexpr int kSlChunk = 16;
 
-// The n rows (a multiple of 4) of one operation code, in chunks whose row
-// loads and parity loads are all issued before the updates; f(way, a, b)
-// spreads consecutive rows over kSlWays independent accumulators so that
-// the update chains overlap (2 ways: fewer registers, measured as fast as 4).
+// Consecutive rows of one code are spread over kSlWays independent
+// accumulators so that their update chains overlap (2 ways: fewer
+// registers, measured as fast as 4).
 #ifndef TSIM_SL_WAYS
 #define TSIM_SL_WAYS 2
 #endif
 constexpr int kSlWays = TSIM_SL_WAYS;
 static_assert(kSlWays == 2 || kSlWays == 4, "2 or 4 accumulator ways");
 
+// NR rows (a multiple of 4) of one code: all their row loads, then all
+// their parity loads, then the updates (one memory round trip).
+template <bool PAIR, int NR, class F>
+__device__ __forceinline__ void sl_chunk(Rows& R, uint32_t par, F&& f) {
+  uint32_t r[NR], a[NR], b[NR];
+#pragma unroll
+  for (int g = 0; g < NR / 4; ++g) {
+    const uint4 v = R.get4(g);
+    r[4 * g] = v.x;
+    r[4 * g + 1] = v.y;
+    r[4 * g + 2] = v.z;
+    r[4 * g + 3] = v.w;
+  }
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    a[i] = lds(par + (PAIR ? (r[i] & 0xFFFFu) : r[i]));
+    b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
+  }
+#pragma unroll
+  for (int i = 0; i < NR; ++i) f(i % kSlWays, a[i], b[i]);
+  R.adv4(NR / 4);
+}
+
+// The n rows (a multiple of 4) of one code: chunks of kSlChunk rows, then
+// the rest (4, 8 or 12 rows) as one chunk, so that a code costs one memory
+// round trip per started chunk (the rest taken 4 rows at a time cost 7.5 %
+// on the 256-program batch); f(way, a, b) applies one row's update.
 template <bool PAIR, class F>
 __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
   int k = 0;
-  for (; k + kSlChunk <= n; k += kSlChunk, R.adv4(kSlChunk / 4)) {
-    uint32_t r[kSlChunk], a[kSlChunk], b[kSlChunk];
-#pragma unroll
-    for (int g = 0; g < kSlChunk / 4; ++g) {
-      const uint4 v = R.get4(g);
-      r[4 * g] = v.x;
-      r[4 * g + 1] = v.y;
-      r[4 * g + 2] = v.z;
-      r[4 * g + 3] = v.w;
-    }
-#pragma unroll
-    for (int i = 0; i < kSlChunk; ++i) {
-      a[i] = lds(par + (PAIR ? (r[i] & 0xFFFFu) : r[i]));
-      b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
-    }
-#pragma unroll
-    for (int i = 0; i < kSlChunk; ++i) f(i % kSlWays, a[i], b[i]);
-  }
-  for (; k < n; k += 4, R.adv4(1)) {
-    const uint4 v = R.get4(0);
-    const uint32_t r[4] = {v.x, v.y, v.z, v.w};
-    uint32_t a[4], b[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      a[i] = lds(par + (PAIR ? (r[i] & 0xFFFFu) : r[i]));
-      b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) f(i % kSlWays, a[i], b[i]);
+  for (; k + kSlChunk <= n; k += kSlChunk) sl_chunk<PAIR, kSlChunk>(R, par, f);
+  switch (n - k) {
+    case 4: sl_chunk<PAIR, 4>(R, par, f); break;
+    case 8: sl_chunk<PAIR, 8>(R, par, f); break;
+    case 12: sl_chunk<PAIR, 12>(R, par, f); break;
+    default: break;
   }
 }
 
@@ -495,8 +494,11 @@ __device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64
     }
     __syncwarp();
     for (uint32_t b = 0; b < sg.n_sb; ++b, ++bi) {
-      const DSBatch B = next;
-      if (b + 1 < sg.n_sb) next = bt[b + 1];  // the next header's load overlaps this batch
+      // the header at use (keeping the next one in registers across the
+      // batch cost more in spills than it saved in latency); staging needs
+      // the next one to start its copy
+      const DSBatch B = bt[b];
+      if (staged && b + 1 < sg.n_sb) next = bt[b + 1];
       uint32_t J0, J1, J2, Z;
       if (staged && ok) {
         const uint32_t buf = bi & 1;
@@ -1018,24 +1020,26 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk
 extern __shared__ __align__(128) uint32_t g_warp_smem[];
 
 // Register bounds (resident blocks of up to 128 threads per SM) for X of up
-// to 4 words: kernels for programs with sliced tables at 80 registers (6
+// to 4 words: kernels for programs with sliced tables at 64 registers (8
 // blocks: occupancy hides the latency of the operation rows read through
-// L1), the others at 48 (10 blocks for the Philox-bound noise loop).  Wider X
-// needs 2W registers of its own, so the bounds relax with W.
+// L1; measured 15 % faster on the colour code than 80 registers and 6
+// blocks, with the rows' header read at use), the others at 48 (10 blocks
+// for the Philox-bound noise loop).  Wider X needs 2W registers of its own,
+// so the bounds relax with W.
 #ifndef TSIM_MINB_SL
-#define TSIM_MINB_SL 6
+#define TSIM_MINB_SL 8
 #endif
 #ifndef TSIM_BATCH_SEEDKEY
 #define TSIM_BATCH_SEEDKEY 1
 #endif
 #ifndef TSIM_MINB_SL_BATCH
-#define TSIM_MINB_SL_BATCH 5
+#define TSIM_MINB_SL_BATCH 6
 #endif
 constexpr int min_blocks(int W, bool sl) {
   return sl ? (W <= 4 ? TSIM_MINB_SL : W <= 8 ? 4 : 2) : (W <= 4 ? 10 : W <= 8 ? 6 : 2);
 }
 // the batched kernel keeps its work-item state live across the whole shot
-// loop: one block less for programs with sliced tables (96 registers)
+// loop: fewer blocks for programs with sliced tables (6: 80 registers)
 constexpr int min_blocks_batch(int W, bool sl) { return sl && W <= 4 ? TSIM_MINB_SL_BATCH : min_blocks(W, sl); }
 
 // One program's launch: thread s samples shot shot0 + s.  DBG: shots with
