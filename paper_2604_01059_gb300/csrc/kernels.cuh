@@ -94,6 +94,54 @@ __device__ __forceinline__ int sign_xy(__int128 X, __int128 Y, int* st) {
   return y2 > x2 ? 1 : -1;
 }
 
+// x as a 64-bit integer and its magnitude, when it fits
+__device__ __forceinline__ bool to64(__int128 x, long long& v, unsigned long long& mag) {
+  v = (long long)x;
+  mag = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  return (__int128)v == x;
+}
+
+// sign of X + Y sqrt2 for |X|, |Y| < 2^63 (exact: X^2 against 2 Y^2 in 128 bits
+// when the signs differ; sqrt2 is irrational, so the squares never tie)
+__device__ __forceinline__ int sign_xy64(long long X, long long Y) {
+  if (X >= 0 && Y >= 0) return (X | Y) != 0;
+  if (X <= 0 && Y <= 0) return -1;
+  const unsigned long long ax = X < 0 ? 0ull - (unsigned long long)X : (unsigned long long)X;
+  const unsigned long long ay = Y < 0 ? 0ull - (unsigned long long)Y : (unsigned long long)Y;
+  const unsigned __int128 x2 = (unsigned __int128)ax * ax, y2 = 2 * ((unsigned __int128)ay * ay);
+  if (X > 0) return x2 > y2 ? 1 : -1;
+  return y2 > x2 ? 1 : -1;
+}
+
+// Algorithm 1's decision U * P_prev < 2^32 * P_1 and the next P_prev (P_1 if
+// the bit is 1, P_prev - P_1 otherwise) in 64-bit integers, exactly as the
+// int128 path computes them, whenever no operand reaches 2^62: P_prev's
+// coefficients below 2^30 (they meet U < 2^32), P_1's below 2^(62 - s) for
+// its shift s, so that every difference stays below 2^63.  Returns the bit,
+// or -1 when the int128 path must decide.  *pos receives whether P_prev > 0.
+__device__ __forceinline__ int bern_fast(const RV& pv, const RV& p1, uint32_t U, RV& next, bool* pos) {
+  long long a, b, a1, b1;
+  unsigned long long ma, mb, ma1, mb1;
+  if (!(to64(pv.A, a, ma) && to64(pv.B, b, mb) && to64(p1.A, a1, ma1) && to64(p1.B, b1, mb1))) return -1;
+  const unsigned long long mp = ma | mb, m1 = ma1 | mb1;
+  const int s = p1.e + 32 - pv.e;  // P_1's shift against an unshifted U * P_prev
+  if ((mp >> 30) || s < 0 || s > 62 || (m1 >> (62 - s))) return -1;
+  *pos = sign_xy64(a, b) > 0;
+  const long long X = a * (long long)U - a1 * (1ll << s);
+  const long long Y = b * (long long)U - b1 * (1ll << s);
+  if (sign_xy64(X, Y) < 0) {
+    next = p1;
+    return 1;
+  }
+  const int e2 = min(pv.e, p1.e);
+  const int sp = pv.e - e2, s1 = p1.e - e2;  // one of them is 0
+  if (sp > 62 || s1 > 62 || (mp >> (62 - sp)) || (m1 >> (62 - s1))) return -1;
+  next.A = (__int128)(a * (1ll << sp) - a1 * (1ll << s1));
+  next.B = (__int128)(b * (1ll << sp) - b1 * (1ll << s1));
+  next.e = e2;
+  return 0;
+}
+
 // coefficient k (0..7) of w^k in Z[w] basis {1, w, w^2, w^3}: w^k = +-w^(k mod 4)
 __device__ __forceinline__ long long pick(const long long c[4], int k) {
   k &= 7;
@@ -333,14 +381,14 @@ __device__ __forceinline__ void sl_chunk(Rows& R, uint32_t par, F&& f) {
     b[i] = PAIR ? lds(par + (r[i] >> 16)) : 0u;
   }
 #pragma unroll
-  for (int i = 0; i < NR; ++i) f(i % kSlWays, a[i], b[i]);
+  for (int i = 0; i < NR; i += 2) f((i / 2) % kSlWays, a[i], b[i], a[i + 1], b[i + 1]);
   R.adv4(NR / 4);
 }
 
 // The n rows (a multiple of 4) of one code: chunks of kSlChunk rows, then
 // the rest (4, 8 or 12 rows) as one chunk, so that a code costs one memory
 // round trip per started chunk (the rest taken 4 rows at a time cost 7.5 %
-// on the 256-program batch); f(way, a, b) applies one row's update.
+// on the 256-program batch); f(way, a, b, a2, b2) applies two rows' updates.
 template <bool PAIR, class F>
 __device__ __forceinline__ void sl_loop(int n, Rows& R, uint32_t par, F&& f) {
   int k = 0;
@@ -369,20 +417,28 @@ __device__ __forceinline__ void sl_batch(const DSBatch& B, Rows R, uint32_t par,
   // per way: J2 flips k, vanishing flags z, and a 2-bit counter (c1, c2) of
   // the rows that add 2 to J (J2 flips and vanishing flags commute with it)
   uint32_t k[kSlWays] = {}, z[kSlWays] = {}, c1[kSlWays] = {}, c2[kSlWays] = {};
-  sl_loop<false>(B.cnt[SL_XOR4], R, par, [&](int w, uint32_t a, uint32_t) { k[w] ^= a; });
-  sl_loop<false>(B.cnt[SL_ADD2], R, par, [&](int w, uint32_t a, uint32_t) {
-    c2[w] ^= c1[w] & a;
-    c1[w] ^= a;
+  // two rows per update: 3-input word operations take both (a 2-bit
+  // counter adds two bits as c1 ^ a ^ b with carry maj(c1, a, b))
+  sl_loop<false>(B.cnt[SL_XOR4], R, par,
+                 [&](int w, uint32_t a, uint32_t, uint32_t a2, uint32_t) { k[w] ^= a ^ a2; });
+  sl_loop<false>(B.cnt[SL_ADD2], R, par, [&](int w, uint32_t a, uint32_t, uint32_t a2, uint32_t) {
+    const uint32_t c = c1[w];
+    c2[w] ^= (c & (a | a2)) | (a & a2);
+    c1[w] = c ^ a ^ a2;
   });
   // J += 6a = 2a + 4a
-  sl_loop<false>(B.cnt[SL_ADD6], R, par, [&](int w, uint32_t a, uint32_t) {
-    c2[w] ^= c1[w] & a;
-    c1[w] ^= a;
-    k[w] ^= a;
+  sl_loop<false>(B.cnt[SL_ADD6], R, par, [&](int w, uint32_t a, uint32_t, uint32_t a2, uint32_t) {
+    const uint32_t c = c1[w];
+    c2[w] ^= (c & (a | a2)) | (a & a2);
+    c1[w] = c ^ a ^ a2;
+    k[w] ^= a ^ a2;
   });
-  sl_loop<true>(B.cnt[SL_XOR4AB], R, par, [&](int w, uint32_t a, uint32_t b) { k[w] ^= a & b; });
-  sl_loop<false>(B.cnt[SL_ZERO], R, par, [&](int w, uint32_t a, uint32_t) { z[w] |= a; });
-  sl_loop<false>(B.cnt[SL_ZEROC], R, par, [&](int w, uint32_t a, uint32_t) { z[w] |= ~a; });
+  sl_loop<true>(B.cnt[SL_XOR4AB], R, par,
+                [&](int w, uint32_t a, uint32_t b, uint32_t a2, uint32_t b2) { k[w] ^= (a & b) ^ (a2 & b2); });
+  sl_loop<false>(B.cnt[SL_ZERO], R, par,
+                 [&](int w, uint32_t a, uint32_t, uint32_t a2, uint32_t) { z[w] |= a | a2; });
+  sl_loop<false>(B.cnt[SL_ZEROC], R, par,
+                 [&](int w, uint32_t a, uint32_t, uint32_t a2, uint32_t) { z[w] |= ~(a & a2); });
   add2bit(c1[0], c2[0], c1[1], c2[1]);
   if constexpr (kSlWays == 4) {
     add2bit(c1[2], c2[2], c1[3], c2[3]);
@@ -395,11 +451,15 @@ __device__ __forceinline__ void sl_batch(const DSBatch& B, Rows R, uint32_t par,
   }
   add2bit(J1, J2, c1[0], c2[0]);
   // J += a (odd phases; rare): a three-plane increment
-  sl_loop<false>(B.cnt[SL_ADD1], R, par, [&](int, uint32_t a, uint32_t) {
+  sl_loop<false>(B.cnt[SL_ADD1], R, par, [&](int, uint32_t a, uint32_t, uint32_t a2, uint32_t) {
     const uint32_t cy = J0 & a;
     J0 ^= a;
     J2 ^= J1 & cy;
     J1 ^= cy;
+    const uint32_t cy2 = J0 & a2;
+    J0 ^= a2;
+    J2 ^= J1 & cy2;
+    J1 ^= cy2;
   });
 }
 
@@ -950,28 +1010,39 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk
       if (DBG && dump) dump_eval<W>(dump + (size_t)drow * nd++, o.table, z1, X, V.W);
       const RV p1 = to_real_rot(z1, rot[o.chain], &st);
       const RV pv = pp[o.chain];
-      if (sign_xy(pv.A, pv.B, &st) <= 0) st |= ST_ZERO_PROB;
       uint32_t u[4];
       philox4x32_10(c0, c1, 1u, (uint32_t)(i >> 2), rk, u);
       const uint32_t q4 = (uint32_t)i & 3;
       const uint32_t U = q4 == 0 ? u[0] : q4 == 1 ? u[1] : q4 == 2 ? u[2] : u[3];
-      // bit = 1 iff U * P_prev < 2^32 * P_1
-      const int e = min(pv.e, p1.e + 32);
-      const __int128 LA = shl_chk(pv.A * (__int128)U, pv.e - e, &st);
-      const __int128 LB = shl_chk(pv.B * (__int128)U, pv.e - e, &st);
-      const __int128 RA = shl_chk(p1.A, p1.e + 32 - e, &st);
-      const __int128 RB = shl_chk(p1.B, p1.e + 32 - e, &st);
-      bit = sign_xy(LA - RA, LB - RB, &st) < 0;
-      if (bit) {
-        pp[o.chain] = p1;
+      // bit = 1 iff U * P_prev < 2^32 * P_1: in 64-bit integers when the
+      // values are small (the common case), else in int128
+      RV nx;
+      bool pos = true;
+      const int fb = bern_fast(pv, p1, U, nx, &pos);
+      if (fb >= 0) {
+        if (!pos) st |= ST_ZERO_PROB;
+        bit = fb;
+        pp[o.chain] = nx;
+        if (!bit) set_xbit<W>(X, o.a, false);
       } else {
-        const int e2 = min(pv.e, p1.e);
-        RV d;
-        d.A = shl_chk(pv.A, pv.e - e2, &st) - shl_chk(p1.A, p1.e - e2, &st);
-        d.B = shl_chk(pv.B, pv.e - e2, &st) - shl_chk(p1.B, p1.e - e2, &st);
-        d.e = e2;
-        pp[o.chain] = d;
-        set_xbit<W>(X, o.a, false);
+        if (sign_xy(pv.A, pv.B, &st) <= 0) st |= ST_ZERO_PROB;
+        const int e = min(pv.e, p1.e + 32);
+        const __int128 LA = shl_chk(pv.A * (__int128)U, pv.e - e, &st);
+        const __int128 LB = shl_chk(pv.B * (__int128)U, pv.e - e, &st);
+        const __int128 RA = shl_chk(p1.A, p1.e + 32 - e, &st);
+        const __int128 RB = shl_chk(p1.B, p1.e + 32 - e, &st);
+        bit = sign_xy(LA - RA, LB - RB, &st) < 0;
+        if (bit) {
+          pp[o.chain] = p1;
+        } else {
+          const int e2 = min(pv.e, p1.e);
+          RV d;
+          d.A = shl_chk(pv.A, pv.e - e2, &st) - shl_chk(p1.A, p1.e - e2, &st);
+          d.B = shl_chk(pv.B, pv.e - e2, &st) - shl_chk(p1.B, p1.e - e2, &st);
+          d.e = e2;
+          pp[o.chain] = d;
+          set_xbit<W>(X, o.a, false);
+        }
       }
     }
     if (V.mode == 0) {
