@@ -909,29 +909,46 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
 
 namespace {
 
-// Groups for the geometric-gap noise rule: channels sorted by their
-// probability of firing (2^32 - thr[0], in units of 2^-32), largest first;
-// a group starts at the most likely channel left and takes every further
-// channel at least half as likely, so a candidate is accepted with
-// probability >= 1/2.  Q is the leader's outcome-0 threshold; members keep
-// program order.  Channels that cannot fire (one outcome) join no group.
+// Groups for the geometric-gap noise rule.  Channels that can fire are sorted
+// by their probability of firing f (2^32 - thr[0], in units of 2^-32),
+// largest first, and cut into consecutive runs; a run's leader (its most
+// likely channel) gives Q, so every member's outcome-0 threshold is >= Q and
+// the rule is exact for any cut.  A run of n channels led by f costs about
+// 1 + 2 n f random words per shot (a gap word, and per candidate its word and
+// the next gap word); the cuts minimise the total by dynamic programming over
+// the sorted list (O(channels^2)).  Members keep program order.  Channels
+// that cannot fire (one outcome) join no group.
 std::vector<NoiseGroup> noise_groups(const Program& p) {
   std::vector<int> order;
   for (size_t c = 0; c < p.channels.size(); ++c)
     if (!p.channels[c].thr.empty()) order.push_back((int)c);
   auto fire = [&](int c) { return (uint64_t(1) << 32) - p.channels[(size_t)c].thr[0]; };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return fire(a) > fire(b); });
+  const size_t n = order.size();
+  // best[j]: fewest expected words for the first j channels; cut[j]: where
+  // the last run of that optimum starts
+  std::vector<double> best(n + 1, 0.0);
+  std::vector<size_t> cut(n + 1, 0);
+  for (size_t j = 1; j <= n; ++j) {
+    best[j] = 1e300;
+    for (size_t i = 0; i < j; ++i) {
+      const double f = (double)fire(order[i]) / 4294967296.0;
+      const double c = best[i] + 1.0 + 2.0 * (double)(j - i) * f;
+      if (c < best[j]) {
+        best[j] = c;
+        cut[j] = i;
+      }
+    }
+  }
   std::vector<NoiseGroup> out;
-  for (size_t i = 0; i < order.size();) {
-    const uint64_t lead = fire(order[i]);
+  for (size_t j = n; j > 0; j = cut[j]) {
     NoiseGroup g;
-    g.Q = p.channels[(size_t)order[i]].thr[0];
-    size_t j = i;
-    while (j < order.size() && 2 * fire(order[j]) >= lead) g.member.push_back(order[j++]);
+    g.Q = p.channels[(size_t)order[cut[j]]].thr[0];
+    for (size_t k = cut[j]; k < j; ++k) g.member.push_back(order[k]);
     std::sort(g.member.begin(), g.member.end());
     out.push_back(std::move(g));
-    i = j;
   }
+  std::reverse(out.begin(), out.end());
   return out;
 }
 

@@ -840,12 +840,19 @@ __device__ __forceinline__ void sample_noise(const DevView& V, uint32_t c0, uint
       const uint32_t U = word();
       const uint32_t rem = G.n - pos;
       if (U < (pos == 0 ? G.tn : __ldg(T + rem - 1))) break;  // gap = rem: no candidate among the rest
-      uint32_t lo = 0, hi = rem;          // U < T_lo (T_0 = 2^32) and U >= T_hi
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (U < __ldg(T + mid - 1)) lo = mid;
-        else hi = mid;
-      }
+      // the gap: the largest k < rem with U < T_k (T_0 = 2^32 > U, U >= T_rem).
+      // T_k is close to 2^32 q^k (q = Q / 2^32), so k is about
+      // ln(U / 2^32) / ln q: a float estimate from log1p (accurate where U
+      // and Q are close to 2^32), then exact steps on the table (usually one
+      // or two loads instead of a binary search's log2(rem) dependent ones)
+      float x = log1pf(-(float)((1ull << 32) - U) * 2.3283064365386963e-10f) /
+                log1pf(-(float)((1ull << 32) - G.Q) * 2.3283064365386963e-10f);
+      if (!(x < (float)rem)) x = (float)rem;  // also NaN and infinity
+      int k = (int)ceilf(x) - 1;
+      k = k < 0 ? 0 : (k >= (int)rem ? (int)rem - 1 : k);
+      while (k + 1 < (int)rem && U < __ldg(T + k)) ++k;  // T_{k+1} is T[k]
+      while (k > 0 && U >= __ldg(T + k - 1)) --k;
+      const uint32_t lo = (uint32_t)k;
       pos += lo;
       const DChan ch = V.ch[__ldg(V.gmem + G.off + pos)];
       const uint32_t Vw = word();
