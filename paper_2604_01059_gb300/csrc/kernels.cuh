@@ -476,16 +476,9 @@ template <int W>
 __device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64_t (&X)[W], const SlSmem& S) {
   const int lane = threadIdx.x & 31;
   const Transposer2 transpose2(lane);
-  __syncwarp();
+  __syncwarp();  // the transposed X (kept current by the caller) is visible
   uint32_t state = S.rb > 0 ? lds(S.state) : 4u;
   const bool staged = tb.stage && !(state & 4u);
-#pragma unroll
-  for (int w = 0; w < W; ++w) {
-    uint32_t lo = (uint32_t)X[w], hi = (uint32_t)(X[w] >> 32);
-    transpose2(lo, hi);
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)(64 * w + lane)), "r"(lo) : "memory");
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)(64 * w + 32 + lane)), "r"(hi) : "memory");
-  }
   ZC z{{0, 0, 0, 0}, tb.base};
   long long (&c)[4] = z.c;
   bool ok = true;
@@ -608,6 +601,27 @@ __device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64
     __syncwarp();
   }
   return z;
+}
+
+// The warp's transposed X in shared memory: word b holds bit b of X of the
+// warp's 32 shots (bit s = lane s).  Written whole after the noise, then one
+// word per change of X (the random outputs' bits), so that table
+// evaluations read it without transposing X again.
+template <int W>
+__device__ __forceinline__ void xs_store_all(const SlSmem& S, const uint64_t (&X)[W]) {
+  const int lane = threadIdx.x & 31;
+  const Transposer2 transpose2(lane);
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    uint32_t lo = (uint32_t)X[w], hi = (uint32_t)(X[w] >> 32);
+    transpose2(lo, hi);
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)(64 * w + lane)), "r"(lo) : "memory");
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)(64 * w + 32 + lane)), "r"(hi) : "memory");
+  }
+}
+__device__ __forceinline__ void xs_store_bit(const SlSmem& S, int b, uint32_t word) {
+  if ((threadIdx.x & 31) == 0)
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.xs + 4u * (uint32_t)b), "r"(word) : "memory");
 }
 
 // SL: the program has sliced tables (kernels without them never contain the
@@ -918,6 +932,7 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk
 #pragma unroll
   for (int w = 0; w < W; ++w) X[w] = 0;
   sample_noise<W, K>(V, c0, c1, rk, X);
+  if constexpr (SL) xs_store_all<W>(sm, X);
 
   // 2-3. outputs in autoregressive order (Algorithm 1 per chain)
   RV pp[kMaxChains];
@@ -995,6 +1010,7 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk
       // the comparison with U / 2^32
       const int c = o.chain;
       set_xbit<W>(X, o.a, true);
+      if constexpr (SL) xs_store_bit(sm, o.a, 0xFFFFFFFFu);
       const ZF z1 = eval_table_f<W>(V, o.table, X);
       if (DBG && dump) dump_eval_f<W>(dump + (size_t)drow * nd++, o.table, z1, X, V.W);
       const double p1 = (z1.re * fnre[c] + z1.im * fnim[c]) / fnmag[c];
@@ -1013,6 +1029,7 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk
       }
     } else {
       set_xbit<W>(X, o.a, true);
+      if constexpr (SL) xs_store_bit(sm, o.a, 0xFFFFFFFFu);
       const ZC z1 = eval_table<W, SL>(V, o.table, X, sm);
       if (DBG && dump) dump_eval<W>(dump + (size_t)drow * nd++, o.table, z1, X, V.W);
       const RV p1 = to_real_rot(z1, rot[o.chain], &st);
@@ -1052,6 +1069,9 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk
         }
       }
     }
+    // every lane walks the same outputs, so the warp is converged here
+    if constexpr (SL)
+      if (o.kind == OUT_RANDOM) xs_store_bit(sm, o.a, __ballot_sync(0xFFFFFFFFu, bit != 0));
     if (V.mode == 0) {
       put(i, (uint64_t)bit);  // detectors are outputs [0, ndet), observables [ndet, ndet + nobs)
     } else {
