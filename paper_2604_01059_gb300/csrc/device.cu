@@ -332,6 +332,109 @@ bool sliced_term(const std::vector<FacKey>& f, int j, int d, LutFn& lut, SlTerm&
   return true;
 }
 
+// Local search after the greedy bank assignment of a segment's parity words.
+// Each warp-wide parity load reads one word per lane; distinct words in one
+// bank are served one after another, so a load costs the largest number of
+// distinct words any bank holds for it.  Every load of the segment (a row's
+// words, or for pi-pairs each half) is one group; a parity moves to a bank
+// with a free slot when that lowers the summed cost of the groups it is in.
+// A few passes; the moves never change which parity a row reads.
+void refine_banks(const std::vector<std::array<uint64_t, 32>>& prow, const std::vector<int>& prow_code,
+                  std::unordered_map<uint32_t, uint32_t>& slot, uint32_t fill[32], uint32_t cap) {
+  // groups: distinct movable parities of one load
+  std::vector<std::vector<uint32_t>> groups;
+  groups.reserve(prow.size() * 2);
+  for (size_t ri = 0; ri < prow.size(); ++ri) {
+    for (int half = 0; half < (prow_code[ri] == SL_XOR4AB ? 2 : 1); ++half) {
+      std::vector<uint32_t> g;
+      for (uint64_t v : prow[ri]) {
+        const uint32_t q = half ? (uint32_t)(v >> 32) : (uint32_t)v;
+        if (q > kSlOnes) g.push_back(q);
+      }
+      std::sort(g.begin(), g.end());
+      g.erase(std::unique(g.begin(), g.end()), g.end());
+      if (g.size() > 1) groups.push_back(std::move(g));
+    }
+  }
+  if (groups.empty()) return;
+  std::unordered_map<uint32_t, std::vector<uint32_t>> member;  // parity -> its groups
+  for (uint32_t gi = 0; gi < groups.size(); ++gi)
+    for (uint32_t q : groups[gi]) member[q].push_back(gi);
+  // per group: distinct words per bank, the largest count and how many banks reach it
+  std::vector<std::array<uint8_t, 32>> cnt(groups.size());
+  std::vector<uint8_t> mx(groups.size(), 0), nmx(groups.size(), 0);
+  auto recount = [&](uint32_t gi) {
+    uint8_t m = 0, n = 0;
+    for (int b = 0; b < 32; ++b) {
+      if (cnt[gi][(size_t)b] > m) {
+        m = cnt[gi][(size_t)b];
+        n = 1;
+      } else if (cnt[gi][(size_t)b] == m) {
+        ++n;
+      }
+    }
+    mx[gi] = m;
+    nmx[gi] = n;
+  };
+  for (uint32_t gi = 0; gi < groups.size(); ++gi) {
+    cnt[gi].fill(0);
+    for (uint32_t q : groups[gi]) cnt[gi][slot.at(q) & 31]++;
+    recount(gi);
+  }
+  // free slots per bank (slot = bank + 32 x row, rows below cap)
+  std::vector<std::vector<uint32_t>> freeslots(32);
+  {
+    std::vector<char> taken((size_t)32 * cap, 0);
+    for (const auto& kv : slot)
+      if (kv.second < 32u * cap) taken[kv.second] = 1;
+    for (uint32_t sl = 2; sl < 32u * cap; ++sl)
+      if (!taken[sl]) freeslots[sl & 31].push_back(sl);
+  }
+  std::vector<uint32_t> order;
+  for (const auto& kv : member) order.push_back(kv.first);
+  std::sort(order.begin(), order.end());
+  for (int pass = 0; pass < 4; ++pass) {
+    int moved = 0;
+    for (uint32_t q : order) {
+      const uint32_t a = slot.at(q) & 31;
+      const std::vector<uint32_t>& gs = member.at(q);
+      // cost change of leaving bank a, per group
+      long base = 0;
+      for (uint32_t gi : gs) base -= (cnt[gi][a] == mx[gi] && nmx[gi] == 1) ? 1 : 0;
+      long best = 0;
+      int bb = -1;
+      for (int b = 0; b < 32; ++b) {
+        if ((uint32_t)b == a || freeslots[(size_t)b].empty()) continue;
+        long d = base;
+        for (uint32_t gi : gs) {
+          // after leaving a, the group's largest count is mx or mx - 1
+          const int m0 = (cnt[gi][a] == mx[gi] && nmx[gi] == 1) ? mx[gi] - 1 : mx[gi];
+          d += (cnt[gi][(size_t)b] + 1 > m0) ? 1 : 0;
+        }
+        if (d < best) {
+          best = d;
+          bb = b;
+        }
+      }
+      if (bb < 0) continue;
+      const uint32_t ns = freeslots[(size_t)bb].back();
+      freeslots[(size_t)bb].pop_back();
+      freeslots[a].push_back(slot.at(q));
+      slot[q] = ns;
+      for (uint32_t gi : gs) {
+        cnt[gi][a]--;
+        cnt[gi][(size_t)bb]++;
+        recount(gi);
+      }
+      ++moved;
+    }
+    if (!moved) break;
+  }
+  // the fill of each bank: one past its highest taken row
+  for (int b = 0; b < 32; ++b) fill[b] = 0;
+  for (const auto& kv : slot) fill[kv.second & 31] = std::max(fill[kv.second & 31], kv.second / 32 + 1);
+}
+
 void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_rows, int seg_par) {
   std::map<std::tuple<int, int, int>, Lut> lut_cache;
   auto lut = [&](int kind, int alpha, int beta) -> const Lut& {
@@ -784,6 +887,7 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
             used[best]++;
           }
         }
+        refine_banks(prow, prow_code, slot, fill, cap);
         uint32_t nslot = 2;
         for (const auto& kv : slot) nslot = std::max(nslot, kv.second + 1);
         if (nslot > (uint32_t)kSlMaxPar) throw PackError{TSIM_ERR_ARG, "a sliced term has too many parities"};
@@ -989,6 +1093,38 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
   if (!tabs.empty()) s.put(tabs.data(), tabs.size() * sizeof(DTable));
   L.o_par = s.section();
   if (!par.empty()) s.put(par.data(), par.size() * 8);
+  // per parity slot, its X bits as eight 8-bit indices when it has at most
+  // eight (X of at most 4 words; unused entries name an X bit that is always
+  // 0, past the program's n_x), else .x = kSlWalk: the kernel then walks the
+  // slot's mask.  Bit-sliced segments form their parity words from these
+  // with four (k8 = 0) or eight shared loads instead of a loop over the mask.
+  {
+    std::vector<uint2> pidx(par.size() / (size_t)W, make_uint2(kSlWalk, kSlWalk));
+    std::vector<uint8_t> wide(pidx.size(), 0);
+    const int zb = p.nx < 64 * W ? 64 * W - 1 : -1;
+    if (W <= 4 && zb >= 0)
+      for (size_t q = 0; q < pidx.size(); ++q) {
+        int bits[8], nb = 0;
+        bool ok = true;
+        for (int w = 0; w < W && ok; ++w)
+          for (uint64_t m = par[q * (size_t)W + (size_t)w]; m && ok; m &= m - 1) {
+            if (nb == 8) ok = false;
+            else bits[nb++] = 64 * w + __builtin_ctzll(m);
+          }
+        if (!ok) continue;
+        uint32_t v[2] = {0, 0};
+        for (int k = 0; k < 8; ++k) v[k >> 2] |= (uint32_t)(k < nb ? bits[k] : zb) << (8 * (k & 3));
+        if (v[0] == kSlWalk) continue;  // only when zb is 255 and no bit is named: walk the (zero) mask
+        pidx[q] = make_uint2(v[0], v[1]);
+        wide[q] = nb > 4;
+      }
+    for (DSeg& g : segs) {
+      g.k8 = 0;
+      for (uint32_t q = 0; q < g.n_par; ++q) g.k8 |= wide[(size_t)g.par_off + q];
+    }
+    L.o_pidx = s.section();
+    if (!pidx.empty()) s.put(pidx.data(), pidx.size() * sizeof(uint2));
+  }
   L.o_cls = s.section();
   if (!cls.empty()) s.put(cls.data(), cls.size() * sizeof(DClass));
   L.o_fidx = s.section();
@@ -1087,6 +1223,7 @@ DevView make_view(const unsigned char* base, const DeviceLayout& L, const Progra
   v.chain_norm = (const int32_t*)(base + L.o_cn);
   v.tab = (const DTable*)(base + L.o_tab);
   v.par = (const uint64_t*)(base + L.o_par);
+  v.pidx = (const uint2*)(base + L.o_pidx);
   v.cls = (const DClass*)(base + L.o_cls);
   v.fidx = (const uint32_t*)(base + L.o_fidx);
   v.finc = (const uint32_t*)(base + L.o_finc);
@@ -1193,6 +1330,7 @@ std::vector<ZW> emulate_sliced_table(const Program& p, const DeviceTables& T, in
   const DSBatch* sbv = (const DSBatch*)(b + L.o_sb);
   const uint32_t* rows = (const uint32_t*)(b + L.o_row);
   const uint64_t* par = (const uint64_t*)(b + L.o_par);
+  const uint2* pidx = (const uint2*)(b + L.o_pidx);
   const int W = L.W;
   std::vector<ZW> val(32);
   std::vector<uint32_t> Xs((size_t)64 * W, 0);
@@ -1207,6 +1345,13 @@ std::vector<ZW> emulate_sliced_table(const Program& p, const DeviceTables& T, in
       for (int w = 0; w < W; ++w)
         for (int bit = 0; bit < 64; ++bit)
           if ((par[((size_t)sg.par_off + q) * W + (size_t)w] >> bit) & 1) acc ^= Xs[(size_t)(64 * w + bit)];
+      // the kernel's form: four or eight named X bits, or the mask
+      const uint2 ix = pidx[(size_t)sg.par_off + q];
+      if (ix.x != kSlWalk) {
+        uint32_t acc8 = 0;
+        for (int k = 0; k < (sg.k8 ? 8 : 4); ++k) acc8 ^= Xs[(size_t)((((k < 4) ? ix.x : ix.y) >> (8 * (k & 3))) & 0xFF)];
+        if (acc8 != acc) fail(TSIM_ERR_INTERNAL, "a parity's bit indices differ from its mask");
+      }
       Par[q] = q == kSlOnes ? 0xFFFFFFFFu : acc;
     }
     auto word = [&](uint32_t off) {

@@ -28,7 +28,7 @@ struct DeviceLayout {
   size_t o_cf = 0, o_ffi = 0, o_ffa = 0;   // chain float flags; arbitrary-angle factors (parity, angle)
   size_t o_tc = 0;                          // per table: the precomputed value of a constant table
   size_t o_dmk = 0, o_omk = 0, o_dcs = 0, o_ocs = 0;  // measurement mode: detector / observable X-masks, constants
-  size_t o_ch = 0, o_t0 = 0, o_thr = 0, o_sig = 0, o_out = 0, o_om = 0, o_cn = 0, o_tab = 0, o_par = 0,
+  size_t o_ch = 0, o_t0 = 0, o_thr = 0, o_sig = 0, o_out = 0, o_om = 0, o_cn = 0, o_tab = 0, o_par = 0, o_pidx = 0,
          o_cls = 0, o_fidx = 0, o_finc = 0, o_fco = 0, o_seg = 0, o_sb = 0, o_row = 0, o_dmo = 0, o_dmi = 0, o_omo = 0,
          o_omi = 0, total = 0;
   int W = 1;

@@ -59,6 +59,7 @@ enum : int {
   kSlCodes = 7
 };
 constexpr uint32_t kSlOnes = 1;        // parity index whose word is all ones
+constexpr uint32_t kSlWalk = 0xFFFFFFFFu;  // parity bit indices absent (> 8 bits): walk the mask
 constexpr int kSlMaxPar = 16384;       // parity words of one segment (4q fits 16 bits)
 // One batch of 32 terms: rows of operation code c are cnt[c] (a multiple of
 // 4) x 32 parity offsets, padded with no-op offsets and stored in groups of 4
@@ -68,7 +69,9 @@ constexpr int kSlMaxPar = 16384;       // parity words of one segment (4q fits 1
 struct DSBatch { uint32_t row_off; uint16_t cnt[8]; int32_t d; uint32_t j0m[3]; uint32_t valid; };
 // A sliced table is a list of segments: consecutive terms whose distinct
 // parities (par_off, n_par masks) fit one shared buffer, and their batches.
-struct DSeg { uint32_t par_off, n_par, sb_off, n_sb; };
+// k8 = 1 when some parity of the segment names more than four X bits (its
+// words are then formed from eight bit indices, else from four).
+struct DSeg { uint32_t par_off, n_par, sb_off, n_sb, k8; };
 
 // One group of the geometric-gap noise rule: Q, member count n, the offset
 // of its member channel indices and of its table T_1..T_n (the same offset
@@ -94,6 +97,7 @@ struct DevView {
   const int32_t* chain_norm;
   const DTable* tab;
   const uint64_t* par;    // per table: n_par masks of W words (mask 0 = zero)
+  const uint2* pidx;      // per parity slot: eight 8-bit X bit indices, or .x = kSlWalk
   const DClass* cls;
   const uint32_t* fidx;   // per factor: parity index of a | parity index of b << 8
   const uint32_t* finc;   // per factor: 4 packed increments

@@ -520,29 +520,52 @@ __device__ ZC eval_table_sliced(const DevView& V, const DTable& tb, const uint64
     // the segment's parities as XORs of the X bits in their masks, 32 shots
     // at once; four per lane at a time so that their mask loads overlap
     const uint64_t* pm = V.par + (size_t)sg.par_off * ws;
-    for (uint32_t q0 = lane; q0 < sg.n_par; q0 += 128) {
-      uint64_t m[4][W];
+    // a parity's word from its mask (one shared load per X bit)
+    auto walk = [&](uint32_t q) {
+      uint32_t acc = 0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t q = q0 + 32u * (uint32_t)u;
-#pragma unroll
-        for (int w = 0; w < W; ++w) m[u][w] = (w < ws && q < sg.n_par) ? __ldg(pm + (size_t)q * ws + w) : 0ull;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const uint32_t q = q0 + 32u * (uint32_t)u;
-        uint32_t acc = 0;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-          uint64_t x = m[u][w];
-          while (x) {
-            acc ^= lds(S.xs + 4u * (uint32_t)(64 * w + __ffsll((long long)x) - 1));
-            x &= x - 1;
-          }
+      for (int w = 0; w < W; ++w) {
+        uint64_t x = w < ws ? __ldg(pm + (size_t)q * ws + w) : 0ull;
+        while (x) {
+          acc ^= lds(S.xs + 4u * (uint32_t)(64 * w + __ffsll((long long)x) - 1));
+          x &= x - 1;
         }
-        if (q < sg.n_par)
+      }
+      return acc;
+    };
+    for (uint32_t q0 = lane; q0 < sg.n_par; q0 += 128) {
+      if constexpr (W <= 4) {
+        // parities name at most four (k8 = 0) or eight X bits: as many
+        // shared loads, the same number in every lane (no loop over mask bits)
+        const uint2* pi = V.pidx + sg.par_off;
+        uint2 ix[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t q = q0 + 32u * (uint32_t)u;
+          ix[u] = q < sg.n_par ? __ldg(pi + q) : make_uint2(0u, 0u);
+        }
+        auto four = [&](uint32_t v) {
+          return lds(S.xs + 4u * (v & 0xFFu)) ^ lds(S.xs + 4u * ((v >> 8) & 0xFFu)) ^
+                 lds(S.xs + 4u * ((v >> 16) & 0xFFu)) ^ lds(S.xs + 4u * (v >> 24));
+        };
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t q = q0 + 32u * (uint32_t)u;
+          if (q >= sg.n_par) continue;
+          const uint2 v = ix[u];
+          const uint32_t acc = v.x == kSlWalk ? walk(q) : (sg.k8 ? four(v.x) ^ four(v.y) : four(v.x));
           asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.par + 4u * q), "r"(q == kSlOnes ? 0xFFFFFFFFu : acc)
                        : "memory");
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t q = q0 + 32u * (uint32_t)u;
+          if (q >= sg.n_par) continue;
+          const uint32_t acc = walk(q);
+          asm volatile("st.shared.u32 [%0], %1;" ::"r"(S.par + 4u * q), "r"(q == kSlOnes ? 0xFFFFFFFFu : acc)
+                       : "memory");
+        }
       }
     }
     __syncwarp();
