@@ -19,6 +19,10 @@
 //  4. GF(2) elimination picks a minimal set of f_i (Eq. detector_sampling) and
 //     the noise channels are reduced (Appendix "Channel reduction").
 #include <algorithm>
+#include <thread>
+#include <mutex>
+#include <exception>
+#include <atomic>
 #include <array>
 #include <cmath>
 #include <functional>
@@ -26,6 +30,8 @@
 #include <memory>
 #include <numeric>
 #include <unordered_map>
+
+#include <cuda_runtime.h>
 
 #include "circuit.h"
 #include "device.h"
@@ -348,6 +354,28 @@ std::vector<uint64_t> to_words(const Bits& b, int W) {
 }  // namespace
 
 std::atomic<CutScorer> g_cut_scorer{nullptr};
+
+// Spare host threads for decomposing marginals: the process shares
+// hardware_concurrency - 1 helpers among concurrent compilations, so that
+// compiling many programs on many threads does not oversubscribe the cores.
+std::atomic<int> g_helpers_free{-1};
+int acquire_helpers(int want) {
+  if (want <= 0) return 0;
+  int cur = g_helpers_free.load();
+  if (cur < 0) {
+    const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+    g_helpers_free.compare_exchange_strong(cur, hw - 1);
+    cur = g_helpers_free.load();
+  }
+  for (;;) {
+    if (cur <= 0) return 0;
+    const int take = std::min(cur, want);
+    if (g_helpers_free.compare_exchange_weak(cur, cur - take)) return take;
+  }
+}
+void release_helpers(int n) {
+  if (n > 0) g_helpers_free.fetch_add(n);
+}
 std::atomic<uint64_t> g_cut_stats[4];
 
 // Decompose one marginal diagram.  LEARNED: the spiders of the simplified
@@ -362,7 +390,7 @@ thread_local std::vector<Graph>* g_marginal_capture = nullptr;
 struct CaptureDone {};
 
 void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget, uint64_t* total,
-                        std::vector<Term>& out) {
+                        std::vector<Term>& out, std::atomic<uint64_t>* shared_total) {
   if (g_marginal_capture) {
     M.simplify();
     M.compact();
@@ -375,6 +403,9 @@ void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget,
   st.total_budget = opts.total_budget;
   const CutScorer scorer = g_cut_scorer.load();
   if (opts.decomp != TSIM_DECOMP_LEARNED || !scorer) {
+    // one decomposition per marginal: its terms count toward the program's
+    // budget as they are made (LEARNED tries several and counts the kept one)
+    st.shared_total = shared_total;
     decompose(M, opts.decomp == TSIM_DECOMP_LEARNED ? TSIM_DECOMP_HEURISTIC : opts.decomp, out, st);
     return;
   }
@@ -586,6 +617,7 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
   // ---- 3: marginal diagrams per chain, decomposed into Clifford terms
   struct RawTable { std::vector<Term> terms; };
   std::vector<RawTable> rtabs;
+  std::vector<Graph> marg;  // marginal diagrams, decomposed after all are built
   // Parities of the chain sub-diagrams before decomposition: every parity a
   // decomposition produces is a sum of these (rewriting only adds parameter
   // sets), so an f basis built from them does not depend on the cut order.
@@ -667,12 +699,59 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
           }
         }
       }
-      RawTable rt;
-      decompose_marginal(M, opts, budget, &total_terms, rt.terms);
-      if (i < 0) P.chain_norm.push_back((int)rtabs.size());
-      else { out_table[(size_t)outs[(size_t)i]] = (int)rtabs.size(); out_chain[(size_t)outs[(size_t)i]] = c; }
-      rtabs.push_back(std::move(rt));
+      if (i < 0) P.chain_norm.push_back((int)(rtabs.size() + marg.size()));
+      else {
+        out_table[(size_t)outs[(size_t)i]] = (int)(rtabs.size() + marg.size());
+        out_chain[(size_t)outs[(size_t)i]] = c;
+      }
+      marg.push_back(std::move(M));
     }
+  }
+  // ---- 3b: decompose the marginals (independent of one another), on spare
+  // host cores when there are any
+  {
+    std::vector<RawTable> done(marg.size());
+    std::vector<uint64_t> totals(marg.size(), 0);
+    std::atomic<uint64_t> shared_total{0};
+    std::atomic<size_t> next{0};
+    std::exception_ptr err;
+    std::mutex err_mu;
+    auto work = [&]() {
+      for (;;) {
+        const size_t k = next.fetch_add(1);
+        if (k >= marg.size()) return;
+        try {
+          decompose_marginal(std::move(marg[k]), opts, budget, &totals[k], done[k].terms, &shared_total);
+        } catch (...) {
+          std::lock_guard<std::mutex> lk(err_mu);
+          if (!err) err = std::current_exception();
+          next.store(marg.size());
+        }
+      }
+    };
+    // the capture mode records into a thread-local list: no helpers then.
+    // Helpers score cuts (LEARNED) on the caller's CUDA device.
+    const int helpers = g_marginal_capture ? 0 : acquire_helpers((int)marg.size() - 1);
+    int dev = -1;
+    if (helpers && opts.decomp == TSIM_DECOMP_LEARNED && g_cut_scorer.load() && cudaGetDevice(&dev) != cudaSuccess)
+      dev = -1;
+    std::vector<std::thread> pool;
+    for (int h = 0; h < helpers; ++h)
+      pool.emplace_back([&work, dev]() {
+        if (dev >= 0) cudaSetDevice(dev);
+        work();
+      });
+    work();
+    for (std::thread& t : pool) t.join();
+    release_helpers(helpers);
+    if (err) std::rethrow_exception(err);
+    for (size_t k = 0; k < marg.size(); ++k) {
+      total_terms += totals[k];
+      rtabs.push_back(std::move(done[k]));
+    }
+    if (opts.total_budget && total_terms > opts.total_budget)
+      fail(TSIM_ERR_CHI_BUDGET, "stabilizer terms of the program exceed the budget (" +
+                                    std::to_string(opts.total_budget) + ")");
   }
 
   if (g_marginal_capture) throw CaptureDone{};

@@ -170,7 +170,7 @@ void make_graph(uint64_t seed, int gi, int t_min, int t_max, uint64_t budget, in
 // compile.cpp: one marginal decomposed by the policy of opts (LEARNED: the
 // heuristic against the network's orders)
 void decompose_marginal(Graph M, const tsim_compile_opts& opts, uint64_t budget, uint64_t* total,
-                        std::vector<Term>& out);
+                        std::vector<Term>& out, std::atomic<uint64_t>* shared_total = nullptr);
 
 }  // namespace tsim
 

@@ -557,6 +557,9 @@ struct Decomposer {
     if (st->total && st->total_budget && ++*st->total > st->total_budget)
       fail(TSIM_ERR_CHI_BUDGET, "stabilizer terms of the program exceed the budget (" +
                                     std::to_string(st->total_budget) + ")");
+    if (st->shared_total && st->total_budget && st->shared_total->fetch_add(1) + 1 > st->total_budget)
+      fail(TSIM_ERR_CHI_BUDGET, "stabilizer terms of the program exceed the budget (" +
+                                    std::to_string(st->total_budget) + ")");
     out->push_back(g.as_term());
   }
 

@@ -17,6 +17,7 @@
 // variable at a time; stabilizer decomposition (Appendix "Stabilizer
 // decompositions") as splitting a sum into Clifford branches.
 #pragma once
+#include <atomic>
 #include <complex>
 #include <vector>
 
@@ -134,6 +135,9 @@ struct DecompStats {
   uint64_t nodes = 0;          // branches explored
   uint64_t* total = nullptr;   // running count over all decompositions of a program
   uint64_t total_budget = 0;
+  // the same count shared by marginals decomposed on several threads (the
+  // program-wide budget then stops every thread early)
+  std::atomic<uint64_t>* shared_total = nullptr;
 };
 
 // Decompose into Clifford terms (Appendix "Stabilizer decompositions").
