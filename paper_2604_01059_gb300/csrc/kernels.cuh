@@ -882,8 +882,7 @@ __device__ __forceinline__ void sample_noise(const DevView& V, uint32_t c0, uint
       // ln(U / 2^32) / ln q: a float estimate from log1p (accurate where U
       // and Q are close to 2^32), then exact steps on the table (usually one
       // or two loads instead of a binary search's log2(rem) dependent ones)
-      float x = log1pf(-(float)((1ull << 32) - U) * 2.3283064365386963e-10f) /
-                log1pf(-(float)((1ull << 32) - G.Q) * 2.3283064365386963e-10f);
+      float x = log1pf(-(float)((1ull << 32) - U) * 2.3283064365386963e-10f) / G.lnq;
       if (!(x < (float)rem)) x = (float)rem;  // also NaN and infinity
       int k = (int)ceilf(x) - 1;
       k = k < 0 ? 0 : (k >= (int)rem ? (int)rem - 1 : k);
