@@ -1140,14 +1140,14 @@ __device__ void sample_one(const DevView& V, uint64_t s, bool valid, const K& rk
 extern __shared__ __align__(128) uint32_t g_warp_smem[];
 
 // Register bounds (resident blocks of up to 128 threads per SM) for X of up
-// to 4 words: kernels for programs with sliced tables at 64 registers (8
+// to 4 words: kernels for programs with sliced tables at 72 registers (7
 // blocks: occupancy hides the latency of the operation rows read through
-// L1; measured 15 % faster on the colour code than 80 registers and 6
-// blocks, with the rows' header read at use), the others at 48 (10 blocks
-// for the Philox-bound noise loop).  Wider X needs 2W registers of its own,
-// so the bounds relax with W.
+// L1; on the colour code 7 blocks were 4.5 % faster than 8 at 64 registers,
+// which spill more, and 15 % faster than 6 at 80), the others at 48 (10
+// blocks for the Philox-bound noise loop).  Wider X needs 2W registers of
+// its own, so the bounds relax with W.
 #ifndef TSIM_MINB_SL
-#define TSIM_MINB_SL 8
+#define TSIM_MINB_SL 7
 #endif
 #ifndef TSIM_BATCH_SEEDKEY
 #define TSIM_BATCH_SEEDKEY 1
