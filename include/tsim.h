@@ -226,9 +226,11 @@ tsim_status tsim_debug_sample(const tsim_program* prog, uint64_t shots, uint64_t
 
 /* How the error mechanisms of a shot are drawn (Sec. "Detectors"):
  *   0  one Philox word per reduced channel (stream 0, word c of the shot);
- *   1  geometric gaps: the channels are split into groups of channels whose
- *      firing probabilities lie within a factor 2 of the group's largest,
- *      1 - Q/2^32; candidates are Bernoulli(1 - Q/2^32) trials along a
+ *   1  geometric gaps: the channels, sorted by firing probability, are cut
+ *      into groups (runs chosen to minimise the expected words per shot);
+ *      a group's Q is its most likely channel's outcome-0 threshold, so its
+ *      largest firing probability is 1 - Q/2^32; candidates are
+ *      Bernoulli(1 - Q/2^32) trials along a
  *      group, each gap drawn from one word U as the largest k (up to the
  *      channels left) with U < T_k, T_0 = 2^32, T_k = floor(T_{k-1} Q / 2^32);
  *      a candidate's word V, mapped onto [Q, 2^32) by Q + floor(V (2^32 - Q)

@@ -479,7 +479,7 @@ void pack(const Program& p, DeviceTables& out, int64_t sliced_min, int stage_row
       uint64_t tn = 1ull << 32;
       for (size_t k = 0; k < g.member.size(); ++k) tn = (tn * (uint64_t)g.Q) >> 32;
       DGroup d{g.Q, (uint32_t)g.member.size(), moff, (uint32_t)tn,
-               (float)std::log1p(-(double)((1ull << 32) - g.Q) / 4294967296.0)};
+               (float)(1.0 / std::log2((double)g.Q / 4294967296.0))};
       moff += (uint32_t)g.member.size();
       s.put(&d, sizeof d);
     }

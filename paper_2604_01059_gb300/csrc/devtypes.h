@@ -76,9 +76,9 @@ struct DSeg { uint32_t par_off, n_par, sb_off, n_sb, k8; };
 // One group of the geometric-gap noise rule: Q, member count n, the offset
 // of its member channel indices and of its table T_1..T_n (the same offset
 // into both arrays), T_n (a word U < T_n leaves no candidate in the group:
-// the common case, decided without reading the table), and ln(Q / 2^32)
+// the common case, decided without reading the table), and 1 / log2(Q / 2^32)
 // (the slope of the gap estimate; the gap itself is decided on the table).
-struct DGroup { uint32_t Q, n, off, tn; float lnq; };
+struct DGroup { uint32_t Q, n, off, tn; float rlq; };
 
 struct DevView {
   int W;

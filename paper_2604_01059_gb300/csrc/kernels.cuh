@@ -879,10 +879,11 @@ __device__ __forceinline__ void sample_noise(const DevView& V, uint32_t c0, uint
       if (U < (pos == 0 ? G.tn : __ldg(T + rem - 1))) break;  // gap = rem: no candidate among the rest
       // the gap: the largest k < rem with U < T_k (T_0 = 2^32 > U, U >= T_rem).
       // T_k is close to 2^32 q^k (q = Q / 2^32), so k is about
-      // ln(U / 2^32) / ln q: a float estimate from log1p (accurate where U
-      // and Q are close to 2^32), then exact steps on the table (usually one
-      // or two loads instead of a binary search's log2(rem) dependent ones)
-      float x = log1pf(-(float)((1ull << 32) - U) * 2.3283064365386963e-10f) / G.lnq;
+      // log2(U / 2^32) / log2 q: a float estimate (the hardware log2; the
+      // group's 1 / log2 q from the host), then exact steps on the table
+      // (usually one or two loads instead of a binary search's log2(rem)
+      // dependent ones)
+      float x = __log2f((float)U * 2.3283064365386963e-10f) * G.rlq;
       if (!(x < (float)rem)) x = (float)rem;  // also NaN and infinity
       int k = (int)ceilf(x) - 1;
       k = k < 0 ? 0 : (k >= (int)rem ? (int)rem - 1 : k);
