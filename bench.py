@@ -320,12 +320,13 @@ def measured_peaks():
 def launches_per_step(progs, shots, binfo):
     """Kernel launches one replay of the batch graph makes: one per program in
     the one-launch-per-program form; otherwise one persistent launch per group
-    (programs without and with bit-sliced tables)."""
+    (programs without and with bit-sliced tables, by X width)."""
     live = [p for p, n in zip(progs, shots) if n > 0]
     if binfo.get("form", 0) == 1:
         return len(live)
-    sliced = [any(p.device_table_layout(t)[0] == 2 for t in range(p.info["num_tables"])) for p in live]
-    return int(any(sliced)) + int(not all(sliced))
+    groups = {(any(p.device_table_layout(t)[0] == 2 for t in range(p.info["num_tables"])),
+               next(w for w in (1, 2, 4, 8, 16, 32) if p.info["x_words"] <= w)) for p in live}
+    return len(groups)
 
 
 class ClockSampler:

@@ -1466,9 +1466,11 @@ void device_sample(const Program& p, const SampleArgs& a, void* stream) {
 }
 
 // ----------------------------------------------------------- batch plans
-// Programs of a batch fall in two groups, without and with sliced tables:
-// each group is one persistent launch with its own register budget (the
-// kernels with sliced tables keep fewer warps resident).
+// Programs of a batch fall in groups by whether they have sliced tables and
+// by their X width: each group is one persistent launch with its own
+// register budget (the kernels with sliced tables keep fewer warps
+// resident) and its own width (a narrow program does not pay for the
+// widest one's X).
 struct BatchGroup {
   int off = 0, n = 0;       // programs [off, off + n) of the plan's (reordered) list
   int wmax = 1, sl_par = 0, sl_rb = 0;
@@ -1481,16 +1483,26 @@ struct BatchPlan {
   int device = -1, n = 0, sms = 1;
   uint32_t sb = 128;        // shots per work item
   int blocks_per_sm = 8;
-  BatchGroup grp[2];
-  std::vector<BatchProg> h_progs;  // group 0 first, then group 1
+  static constexpr int kGroups = 12;  // (sliced tables or not) x (X width 1, 2, 4, ..., 32)
+  BatchGroup grp[kGroups];
+  std::vector<BatchProg> h_progs;  // group 0 first, then group 1, ...
   unsigned char* dmem = nullptr;
   BatchProg* d_progs = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   float tuned_ms = 0;
   int form = 0;  // 0: persistent launches over the work items; 1: each program's own launch
-  uint64_t total_items() const { return grp[0].total_items + grp[1].total_items; }
-  int wmax() const { return std::max(grp[0].wmax, grp[1].wmax); }
+  uint64_t total_items() const {
+    uint64_t t = 0;
+    for (const BatchGroup& g : grp) t += g.total_items;
+    return t;
+  }
+  int wmax() const {
+    int w = 1;
+    for (const BatchGroup& g : grp)
+      if (g.n) w = std::max(w, g.wmax);
+    return w;
+  }
 };
 
 namespace {
@@ -1553,7 +1565,7 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
   b->n = n;
   TSIM_CUDA(cudaGetDevice(&b->device));
   TSIM_CUDA(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device));
-  std::vector<BatchProg> per_group[2];
+  std::vector<BatchProg> per_group[BatchPlan::kGroups];
   for (int i = 0; i < n; ++i) {
     const Program& p = *progs[i];
     if (p.mode == TSIM_MODE_DETECTORS && args[i].meas)
@@ -1568,29 +1580,37 @@ BatchPlan* batch_create(const Program* const* progs, int n, const SampleArgs* ar
     bp.det = args[i].det;
     bp.obs = args[i].obs;
     bp.accept = args[i].accept;
-    const int gi = bp.v.sl_par > 0 ? 1 : 0;
+    int wl = 0;
+    while ((1 << wl) < bp.v.W) ++wl;
+    if (wl > 5) fail(TSIM_ERR_ARG, "X wider than 32 words");
+    const int gi = (bp.v.sl_par > 0 ? 6 : 0) + wl;
     BatchGroup& g = b->grp[gi];
     g.wmax = std::max(g.wmax, bp.v.W);
     g.sl_par = std::max(g.sl_par, bp.v.sl_par);
     g.sl_rb = std::max(g.sl_rb, bp.v.sl_rb);
     per_group[gi].push_back(bp);
   }
-  b->grp[0].off = 0;
-  b->grp[0].n = (int)per_group[0].size();
-  b->grp[1].off = b->grp[0].n;
-  b->grp[1].n = (int)per_group[1].size();
+  {
+    int off = 0;
+    for (int gi = 0; gi < BatchPlan::kGroups; ++gi) {
+      b->grp[gi].off = off;
+      b->grp[gi].n = (int)per_group[gi].size();
+      off += b->grp[gi].n;
+    }
+  }
   for (const auto& v : per_group) b->h_progs.insert(b->h_progs.end(), v.begin(), v.end());
-  const size_t bytes = (size_t)n * sizeof(BatchProg) + ((size_t)n + 2) * 8 + 2 * 64;
+  const size_t bytes = (size_t)n * sizeof(BatchProg) + ((size_t)n + BatchPlan::kGroups) * 8 +
+                       (size_t)BatchPlan::kGroups * 64;
   cudaError_t e = cudaMalloc(&b->dmem, bytes);
   if (e != cudaSuccess) fail(TSIM_ERR_OOM, std::string("cudaMalloc of the batch plan: ") + cudaGetErrorString(e));
   b->d_progs = (BatchProg*)b->dmem;
   {
     uint64_t* starts = (uint64_t*)(b->dmem + (size_t)n * sizeof(BatchProg));
-    b->grp[0].d_item_start = starts;
-    b->grp[1].d_item_start = starts + b->grp[0].n + 1;
-    unsigned char* ctr = b->dmem + (size_t)n * sizeof(BatchProg) + ((size_t)n + 2) * 8;
-    b->grp[0].d_counter = (unsigned long long*)ctr;
-    b->grp[1].d_counter = (unsigned long long*)(ctr + 64);
+    unsigned char* ctr = b->dmem + (size_t)n * sizeof(BatchProg) + ((size_t)n + BatchPlan::kGroups) * 8;
+    for (int gi = 0; gi < BatchPlan::kGroups; ++gi) {
+      b->grp[gi].d_item_start = starts + b->grp[gi].off + gi;  // n + 1 entries per group
+      b->grp[gi].d_counter = (unsigned long long*)(ctr + 64 * gi);
+    }
   }
   cudaStream_t s = nullptr;
   TSIM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
