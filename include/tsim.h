@@ -264,14 +264,16 @@ tsim_status tsim_program_noise_info(const tsim_program* prog, double out[4]);
  * blocks per SM (4, 8, 16) by timing each candidate on the real batch,
  * then times the other launch form (each program's own sampling kernel, one
  * after another) and keeps the faster form, and captures the launch
- * ("reset the work counter + persistent launch", or the programs' launches)
- * in a CUDA graph.  Both forms write the same records.  tsim_batch_launch
+ * ("reset the work counter + persistent launch" for each group of programs
+ * with equal padded X width and with or without bit-sliced tables, or the
+ * programs' launches) in a CUDA graph.  Both forms write the same records.  tsim_batch_launch
  * replays that graph on cuda_stream (asynchronous); the output pointers
  * given at creation are written on every launch.  The batch owns a small
  * device allocation (descriptors, work counter) freed by tsim_batch_free,
  * which must not be called while a launch is in flight.
  * tsim_batch_info: out[0] shots per work item, out[1] blocks per SM,
- * out[2] work items, out[3] 1 if a graph is captured, out[4] words of X,
+ * out[2] work items, out[3] 1 if a graph is captured, out[4] words of the
+ * widest X,
  * out[5] autotuned launch time in microseconds (0 without autotuning),
  * out[6] launch form (0 persistent, 1 one launch per program).
  * autotune = 0 keeps the persistent form with its defaults; autotune = 2
