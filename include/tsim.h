@@ -191,9 +191,9 @@ tsim_status tsim_sample_batch(const tsim_program* const* progs, int n, const uin
  *     TSIM_ERR_ARG before anything is written; tsim_sample has no such limit.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture.  Later calls look the address up again, so
- *     a cudaDeviceReset of the device (which moves the array) is picked up
- *     by the next call.
+ *     before any stream capture.  Every later call outside a stream capture
+ *     looks the address up again, so a cudaDeviceReset of the device (which
+ *     moves the array) is picked up by the next such call.
  *   - Every call reuses the same array and rewrites all of it that the kernel
  *     reads.  Calls whose work overlaps on the GPU (different streams without
  *     ordering between them) race on the array and must not be issued; calls
