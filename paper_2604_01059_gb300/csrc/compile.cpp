@@ -736,11 +736,17 @@ Program* compile_program(const std::string& text, const tsim_compile_opts& opts)
     if (helpers && opts.decomp == TSIM_DECOMP_LEARNED && g_cut_scorer.load() && cudaGetDevice(&dev) != cudaSuccess)
       dev = -1;
     std::vector<std::thread> pool;
-    for (int h = 0; h < helpers; ++h)
-      pool.emplace_back([&work, dev]() {
-        if (dev >= 0) cudaSetDevice(dev);
-        work();
-      });
+    pool.reserve((size_t)helpers);
+    for (int h = 0; h < helpers; ++h) {
+      try {
+        pool.emplace_back([&work, dev]() {
+          if (dev >= 0) cudaSetDevice(dev);
+          work();
+        });
+      } catch (...) {
+        break;  // no more threads to be had: the ones started and this one share the work
+      }
+    }
     work();
     for (std::thread& t : pool) t.join();
     release_helpers(helpers);
