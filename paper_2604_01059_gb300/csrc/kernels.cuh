@@ -23,12 +23,14 @@
 //          the warp's 32 shots share every 32-bit word, lane l carries term l
 //          of a batch of 32, and each factor is one or two word operations on
 //          the term's phase exponent mod 8 and vanishing flag (below);
-//   3. the Bernoulli draw compares U * P_prev < 2^32 * P_1 exactly (int128);
+//   3. the Bernoulli draw compares U * P_prev < 2^32 * P_1 exactly (64-bit
+//      integers when bounds on the operands rule out overflow, else int128);
 //   4. bit-packed records (runs of single-bit detectors copied by word shifts).
 // The program tables are read-only; per-thread table loads are uniform
 // (broadcast) loads, the bit-sliced rows are lane-coalesced 16-byte loads.
 // k_sample launches one program; k_batch runs persistent warps over the
-// (program, shot-block) work items of many programs.  Conditions that make a
+// (program, shot-block) work items of many programs (one launch per group of
+// programs with equal X width, with or without sliced tables).  Conditions that make a
 // result untrustworthy (overflow, a non-real marginal, P_prev <= 0, a staging
 // wait that gave up) set bits of the launch's status word, read by tsim_sync.
 #pragma once
